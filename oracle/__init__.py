@@ -1,0 +1,161 @@
+"""FP64 CPU oracle of DeGraF detection and RLOF tracking (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the benchmark's
+CPU-baseline leg may use this module; the CUDA product path never imports it.
+The arithmetic lives in ``degraf_oracle.c``; this wrapper only marshals arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "degraf_oracle.c")
+_LIBDIR = os.path.join(_HERE, "lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+
+TRACKED, OOB, SMALL_EIG, SINGULAR, MAXITER = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, no fast-math, no FMA contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(_LIBDIR, exist_ok=True)
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                    "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"], check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _RlofParams(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("radius", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("model", ctypes.c_int), ("eps", ctypes.c_double), ("hampel_a", ctypes.c_double),
+                ("hampel_b", ctypes.c_double), ("hampel_c", ctypes.c_double),
+                ("min_eig", ctypes.c_double)]
+
+
+@dataclasses.dataclass
+class RlofParams:
+    levels: int = 3
+    radius: int = 4
+    max_iter: int = 30
+    model: int = 4
+    eps: float = 1e-3
+    hampel_a: float = 8.0
+    hampel_b: float = 16.0
+    hampel_c: float = 32.0
+    min_eig: float = 1e-3
+
+    def _c(self) -> _RlofParams:
+        return _RlofParams(self.levels, self.radius, self.max_iter, self.model, self.eps,
+                           self.hampel_a, self.hampel_b, self.hampel_c, self.min_eig)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P, I, L, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double
+        _lib.oracle_degraf_count.argtypes = [I, I, I, I, I]
+        _lib.oracle_degraf_count.restype = L
+        _lib.oracle_degraf_detect.argtypes = [P, I, I, I, I, I, I, P, P, P]
+        _lib.oracle_degraf_detect.restype = I
+        _lib.oracle_pyramid_size.argtypes = [I, I, I]
+        _lib.oracle_pyramid_size.restype = L
+        _lib.oracle_pyramid.argtypes = [P, I, I, I, P]
+        _lib.oracle_pyramid.restype = I
+        _lib.oracle_hampel_psi.argtypes = [D, D, D, D]
+        _lib.oracle_hampel_psi.restype = D
+        _lib.oracle_rlof_track.argtypes = [P, P, I, I, P, I, ctypes.POINTER(_RlofParams), P, P, P,
+                                           P, I]
+        _lib.oracle_rlof_track.restype = I
+        _lib.oracle_max_threads.argtypes = []
+        _lib.oracle_max_threads.restype = I
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def degraf_count(W: int, H: int, win_w: int, win_h: int, step: int) -> int:
+    return int(lib().oracle_degraf_count(W, H, win_w, win_h, step))
+
+
+def degraf_detect(img: np.ndarray, win_w: int, win_h: int | None = None, step: int = 1):
+    """Key-points of a uint8 frame: (pts [N,2] f64, sums [N,7] i64, neg [N] bool).
+
+    sums columns: S_pos, sum j I, sum i I, m, S_neg, sum j (1+m-I), sum i (1+m-I).
+    """
+    win_h = win_w if win_h is None else win_h
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    n = degraf_count(W, H, win_w, win_h, step)
+    pts = np.zeros((n, 2), np.float64)
+    sums = np.zeros((n, 7), np.int64)
+    neg = np.zeros(n, np.uint8)
+    rc = lib().oracle_degraf_detect(_ptr(img), W, H, W, win_w, win_h, step, _ptr(pts), _ptr(sums),
+                                    _ptr(neg))
+    if rc:
+        raise ValueError("oracle_degraf_detect: bad arguments")
+    return pts, sums, neg.astype(bool)
+
+
+def level_sizes(W: int, H: int, levels: int):
+    out = []
+    for _ in range(levels):
+        out.append((W, H))
+        W, H = W // 2, H // 2
+    return out
+
+
+def pyramid(img: np.ndarray, levels: int):
+    """[(I_l, Ix_l, Iy_l)] per level, float64 arrays [H_l, W_l]."""
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    H, W = img.shape
+    buf = np.zeros(int(lib().oracle_pyramid_size(W, H, levels)), np.float64)
+    if lib().oracle_pyramid(_ptr(img), W, H, levels, _ptr(buf)):
+        raise ValueError("oracle_pyramid: bad arguments")
+    out, off = [], 0
+    for (Wl, Hl) in level_sizes(W, H, levels):
+        n = Wl * Hl
+        out.append(tuple(buf[off + i * n: off + (i + 1) * n].reshape(Hl, Wl) for i in range(3)))
+        off += 3 * n
+    return out
+
+
+def hampel_psi(r: float, a: float, b: float, c: float) -> float:
+    return float(lib().oracle_hampel_psi(r, a, b, c))
+
+
+def rlof_track(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofParams,
+               nthreads: int = 0):
+    """Track pts [n,2] from I1 to I2: (flow [n,2], status [n] u8, iters [n] i32, illum [n,2])."""
+    I1 = np.ascontiguousarray(I1, dtype=np.float64)
+    I2 = np.ascontiguousarray(I2, dtype=np.float64)
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+    H, W = I1.shape
+    n = pts.shape[0]
+    flow = np.zeros((n, 2), np.float64)
+    status = np.zeros(n, np.uint8)
+    iters = np.zeros(n, np.int32)
+    illum = np.zeros((n, 2), np.float64)
+    prm = params._c()
+    rc = lib().oracle_rlof_track(_ptr(I1), _ptr(I2), W, H, _ptr(pts), n, ctypes.byref(prm),
+                                 _ptr(flow), _ptr(status), _ptr(iters), _ptr(illum), int(nthreads))
+    if rc:
+        raise ValueError("oracle_rlof_track: bad arguments")
+    return flow, status, iters, illum
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())

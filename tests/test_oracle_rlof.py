@@ -1,0 +1,194 @@
+"""Pins of the oracle's RLOF tracker (Section 2 "Sparse point tracking", Section 3
+"Parameters"). The paper gives no RLOF formulas, so the pins are facts any correct
+robust pyramidal Lucas-Kanade with a gain/offset illumination model must satisfy:
+exact recovery of integer translations and of gain/offset changes, equality with an
+independently written textbook Lucas-Kanade in the non-robust special case,
+rejection of gross outliers by the Hampel norm, and the lost-point rules. CPU only."""
+import numpy as np
+import pytest
+from scipy import ndimage
+
+import oracle
+import synth
+
+W, H = 160, 96
+HUGE = dict(hampel_a=1e30, hampel_b=1e30, hampel_c=2e30)
+
+
+@pytest.fixture(scope="module")
+def frame1():
+    return synth.render(W, H, 5)
+
+
+def shifted(I1, t, gain=1.0, offset=0.0, fill_seed=77):
+    """I2(x) = gain * I1(x - t) + offset for integer t; uncovered pixels get fresh texture."""
+    I2 = synth.render(W, H, fill_seed)
+    tx, ty = t
+    y, x = np.mgrid[0:H, 0:W]
+    ok = (x - tx >= 0) & (x - tx < W) & (y - ty >= 0) & (y - ty < H)
+    I2[ok] = I1[(y - ty)[ok], (x - tx)[ok]]
+    return gain * I2 + offset
+
+
+def interior_points(n=200, margin=30, seed=0):
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(margin, W - margin, n), rng.uniform(margin, H - margin, n)], 1)
+
+
+def test_hampel_psi_knots():
+    a, b, c = 8.0, 16.0, 32.0
+    psi = lambda r: oracle.hampel_psi(r, a, b, c)  # noqa: E731
+    assert psi(0.0) == 0.0 and psi(3.0) == 3.0 and psi(-a) == -a
+    assert psi(b) == a and psi(12.0) == a and psi(-12.0) == -a
+    assert psi((b + c) / 2) == a / 2 and psi(c) == 0.0 and psi(c + 1e-9) == 0.0
+    assert psi(-1e6) == 0.0
+    # continuous at every knot
+    for k in (a, b, c):
+        assert abs(psi(k - 1e-9) - psi(k + 1e-9)) < 1e-6
+
+
+@pytest.mark.parametrize("t", [(5, -3), (9, -7), (-12, 4)])
+def test_integer_translation_is_exact(frame1, t):
+    """Bilinear sampling is exact at an integer shift, so d = t is a fixed point
+    with zero residual; coarse-to-fine must reach it from |t| beyond the level-0
+    support radius."""
+    pts = interior_points()
+    prm = oracle.RlofParams(levels=3, radius=4, model=2, eps=1e-10, max_iter=100)
+    flow, st, _, _ = oracle.rlof_track(frame1, shifted(frame1, t), pts, prm)
+    assert np.all(st == oracle.TRACKED)
+    assert np.abs(flow - np.array(t)).max() < 1e-9
+
+
+def test_single_level_cannot_reach_large_translation(frame1):
+    """Without the pyramid a shift far beyond the support is not recovered."""
+    pts = interior_points()
+    prm = oracle.RlofParams(levels=1, radius=4, model=2, eps=1e-10, max_iter=100)
+    flow, st, _, _ = oracle.rlof_track(frame1, shifted(frame1, (9, -7)), pts, prm)
+    ok = (st == oracle.TRACKED) & (np.abs(flow - [9, -7]).max(1) < 1e-6)
+    assert ok.mean() < 0.8
+
+
+@pytest.mark.parametrize("t", [(4, -4), (5, -3)])
+def test_gain_offset_is_exact(frame1, t):
+    """Model 4: I2 = 1.2 I1(x - t) - 10 gives the fixed point d = t, m = 0.2, c = -10."""
+    pts = interior_points()
+    prm = oracle.RlofParams(levels=3, radius=4, model=4, eps=1e-10, max_iter=100)
+    flow, st, _, illum = oracle.rlof_track(frame1, shifted(frame1, t, 1.2, -10.0), pts, prm)
+    assert np.all(st == oracle.TRACKED)
+    assert np.abs(flow - np.array(t)).max() < 1e-9
+    assert np.abs(illum - [0.2, -10.0]).max() < 1e-8
+
+
+def test_translation_model_is_biased_by_gain(frame1):
+    """Model 2 has no illumination terms, so the same gain change moves its answer."""
+    pts = interior_points()
+    prm = oracle.RlofParams(levels=3, radius=4, model=2, eps=1e-10, max_iter=100, **HUGE)
+    flow, st, _, _ = oracle.rlof_track(frame1, shifted(frame1, (4, -4), 1.2, -10.0), pts, prm)
+    ok = st == oracle.TRACKED
+    assert np.median(np.abs(flow[ok] - [4, -4]).max(1)) > 1e-3
+
+
+def textbook_lk(I1, I2, p, radius, eps, max_iter):
+    """One-level Lucas-Kanade, written independently with SciPy primitives:
+    d <- d + G^-1 sum grad T (T - J(p + d)), G = sum grad T grad T^T, with Sobel/8
+    template gradients and clamp-to-edge bilinear sampling."""
+    gx = ndimage.sobel(I1, axis=1, mode="nearest") / 8.0
+    gy = ndimage.sobel(I1, axis=0, mode="nearest") / 8.0
+    k = np.arange(-radius, radius + 1, dtype=np.float64)
+    ky, kx = np.meshgrid(k, k, indexing="ij")
+    cy, cx = p[1] + ky.ravel(), p[0] + kx.ravel()
+
+    def sample(img, yy, xx):
+        return ndimage.map_coordinates(img, [yy, xx], order=1, mode="nearest")
+
+    T, Tx, Ty = sample(I1, cy, cx), sample(gx, cy, cx), sample(gy, cy, cx)
+    A = np.stack([Tx, Ty], 1)
+    G = A.T @ A
+    d = np.zeros(2)
+    for _ in range(max_iter):
+        J = sample(I2, cy + d[1], cx + d[0])
+        step = np.linalg.solve(G, A.T @ (T - J))
+        d += step
+        if np.hypot(*step) < eps:
+            break
+    return d
+
+
+def test_non_robust_single_level_equals_textbook_lk(frame1):
+    I2 = synth.render(W, H, 5, shift=(1.3, -0.6))
+    pts = interior_points(40, seed=3)
+    prm = oracle.RlofParams(levels=1, radius=5, model=2, eps=1e-12, max_iter=60, **HUGE)
+    flow, st, _, _ = oracle.rlof_track(frame1, I2, pts, prm)
+    for k in range(pts.shape[0]):
+        ref = textbook_lk(frame1, I2, pts[k], 5, 1e-12, 60)
+        assert st[k] in (oracle.TRACKED, oracle.MAXITER)
+        assert np.abs(flow[k] - ref).max() < 1e-9
+
+
+def test_subpixel_translation_recovered(frame1):
+    """Analytic sub-pixel shift: the error left is the bilinear model error of a
+    smooth texture (bound measured once: max 0.05 px for model 2, 0.10 px for 4)."""
+    pts = interior_points()
+    for t in [(0.4, -0.7), (2.3, 1.6)]:
+        I2 = synth.render(W, H, 5, shift=t)
+        for model, bound in ((2, 0.07), (4, 0.12)):
+            prm = oracle.RlofParams(levels=3, radius=4, model=model, eps=1e-6, max_iter=100)
+            flow, st, _, _ = oracle.rlof_track(frame1, I2, pts, prm)
+            e = np.hypot(*(flow - np.array(t)).T)
+            assert np.all(st == oracle.TRACKED)
+            assert np.median(e) < 0.02 and e.max() < bound
+
+
+@pytest.mark.parametrize("p", [(80.0, 48.0), (70.0, 40.0), (100.0, 50.0), (60.0, 60.0)])
+def test_hampel_rejects_gross_outliers(p):
+    """A 2x2 block of +120 corruption inside the support: at an integer point and an
+    integer shift every sample hits one pixel, the corrupted residuals lie beyond c
+    so their weights are 0, and d = t stays an exact fixed point that coarse-to-fine
+    reaches. The L2 norm (all weights 1) is pulled away from t."""
+    rng = np.random.default_rng(1)
+
+    def texture():
+        v = ndimage.gaussian_filter(rng.uniform(0, 255, (H, W)), 1.5)
+        return 16 + 224 * (v - v.min()) / (v.max() - v.min())
+
+    I1 = texture()
+    t = (5, -3)
+    I2 = texture()
+    y, x = np.mgrid[0:H, 0:W]
+    ok = (x - t[0] >= 0) & (x - t[0] < W) & (y - t[1] >= 0) & (y - t[1] < H)
+    I2[ok] = I1[(y - t[1])[ok], (x - t[0])[ok]]
+    cy, cx = int(p[1]) + t[1], int(p[0]) + t[0]
+    I2[cy - 1: cy + 1, cx + 1: cx + 3] += 120.0
+    pts = np.array([p])
+    robust = oracle.RlofParams(levels=3, radius=4, model=2, eps=1e-10, max_iter=100)
+    flow, st, _, _ = oracle.rlof_track(I1, I2, pts, robust)
+    assert st[0] == oracle.TRACKED and np.abs(flow[0] - t).max() < 1e-9
+    plain = oracle.RlofParams(levels=3, radius=4, model=2, eps=1e-10, max_iter=100, **HUGE)
+    flow2, _, _, _ = oracle.rlof_track(I1, I2, pts, plain)
+    assert np.abs(flow2[0] - t).max() > 5e-2
+
+
+def test_lost_point_rules(frame1):
+    prm = oracle.RlofParams(levels=2, radius=4, model=4)
+    # flat frames: the gradient matrix is zero
+    flat = np.full((H, W), 100.0)
+    _, st, it, _ = oracle.rlof_track(flat, flat, np.array([[50.0, 40.0]]), prm)
+    assert st[0] == oracle.SMALL_EIG and it[0] == 0
+    # a point pushed out of the frame by a large shift
+    I2 = shifted(frame1, (-12, 0))
+    flow, st, _, _ = oracle.rlof_track(frame1, I2, np.array([[3.0, 40.0]]),
+                                       oracle.RlofParams(levels=3, radius=4, model=2))
+    assert st[0] == oracle.OOB and np.all(flow[0] == 0)
+    # a point that starts outside the frame
+    _, st, _, _ = oracle.rlof_track(frame1, frame1, np.array([[-5.0, 40.0]]), prm)
+    assert st[0] == oracle.OOB
+    # one iteration is not enough to converge: tracked, but flagged
+    flow, st, it, _ = oracle.rlof_track(frame1, shifted(frame1, (2, 1)), np.array([[80.0, 48.0]]),
+                                        oracle.RlofParams(levels=1, radius=4, model=2, max_iter=1))
+    assert st[0] == oracle.MAXITER and it[0] == 1 and np.all(flow[0] != 0)
+
+
+def test_identical_frames_give_zero_flow(frame1):
+    pts = interior_points()
+    flow, st, it, illum = oracle.rlof_track(frame1, frame1, pts, oracle.RlofParams(levels=3, radius=5))
+    assert np.all(st == oracle.TRACKED) and np.abs(flow).max() < 1e-12 and np.abs(illum).max() < 1e-12
