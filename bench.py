@@ -1,0 +1,307 @@
+"""Benchmark: DeGraF detection + RLOF tracking on a 1242x375 driving-scene-shaped pair.
+
+One step = one pass of the whole hot path over one frame pair: DeGraF detection
+on frame 1 (window 7, step 3: 50,676 points), the 5-level pyramids of both frames,
+and RLOF tracking of every point (11x11 support, max 30 iterations, gain/offset
+model, FP32). Frames are seeded synthetic uint8 pairs (radial expansion up to
+150 px plus three moving rectangles) standing in for KITTI.
+
+Prints one JSON line. `value` is tracked points per second over the whole job
+(device-resident inputs, CUDA events, L2 flushed between steps); `e2e` is the
+same metric through the public host-buffer API with the copies in the timed
+region. `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "tracked points/s and frame pairs/s at 1242x375; % HBM roofline; EPE vs FP64 oracle"
+WORKLOAD = dict(workload="driving-scene pair 1242x375: DeGraF w=7 step=3 (50676 pts) + RLOF "
+                "5 levels 11x11 max 30 iters gain/offset model, FP32",
+                W=1242, H=375, win=7, step=3, levels=5, radius=5, max_iter=30, model=4)
+# FP32 lanes x 2 flop x SMs at the maximum SM clock (GB300: 152 SMs, 128 FP32 lanes each)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def flops_model(radius: int, model: int):
+    """Algorithmic FLOPs per Gauss-Newton iteration and per level set-up of one point.
+
+    Per support sample and iteration: bilinear sample 9, residual 3 (model 4) or 1,
+    Hampel weight 2, weighted regressors 3 or 2, normal-equation sums 16 + 8 (model 4)
+    or 6 + 4; per iteration a 4x4 (55) or 2x2 (10) Cholesky solve. Per level set-up
+    and sample: three bilinear samples 27 + gradient-matrix sums 6; plus 10.
+    """
+    n = (2 * radius + 1) ** 2
+    per_sample = 9 + 3 + 2 + 3 + 16 + 8 if model == 4 else 9 + 1 + 2 + 2 + 6 + 4
+    per_iter = per_sample * n + (55 if model == 4 else 10)
+    per_setup = 33 * n + 10
+    return per_iter, per_setup
+
+
+def algorithmic_flops(iters: np.ndarray, status: np.ndarray, levels: int, radius: int, model: int) -> float:
+    per_iter, per_setup = flops_model(radius, model)
+    tracked = (status == 0) | (status == 4)
+    setups = np.where(tracked, levels, 1).sum()  # lost points: only one set-up counted (lower bound)
+    return float(iters.astype(np.int64).sum() * per_iter + setups * per_setup)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+            self.t.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def kernel_traffic():
+    """DRAM bytes per rlof launch from the committed ncu summary, or None when the
+    kernel source changed after the capture."""
+    path = os.path.join(ROOT, "profiles", "rlof_track_traffic.json")
+    src = os.path.join(ROOT, "paper_1901_09971_gb300", "csrc", "rlof.cu")
+    try:
+        rec = json.load(open(path))
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        return rec["dram_bytes_per_launch"] if rec.get("rlof_cu_sha256") == digest else None
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def cpu_baseline(pair, reps: int = 2):
+    """The FP64 oracle as it stands, on this host's cores, over the full pair."""
+    import oracle
+    prm = oracle.RlofParams(levels=WORKLOAD["levels"], radius=WORKLOAD["radius"],
+                            max_iter=WORKLOAD["max_iter"], model=WORKLOAD["model"])
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(reps):
+        pts, _, _ = oracle.degraf_detect(pair.I1, WORKLOAD["win"], WORKLOAD["win"], WORKLOAD["step"])
+        oracle.rlof_track(pair.I1, pair.I2, pts, prm)
+        n += pts.shape[0]
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "points/s", "cores": threads, "kind": "oracle",
+            "sample": f"full 1242x375 pair ({n // reps} points, detection + pyramids + tracking) x {reps}, "
+                      f"{dt:.1f} s wall"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    pair = synth.make_pair(2)
+    import oracle
+    prm = oracle.RlofParams(levels=WORKLOAD["levels"], radius=WORKLOAD["radius"],
+                            max_iter=WORKLOAD["max_iter"], model=WORKLOAD["model"])
+
+    def step():
+        pts, _, _ = oracle.degraf_detect(pair.I1, WORKLOAD["win"], WORKLOAD["win"], WORKLOAD["step"])
+        oracle.rlof_track(pair.I1, pair.I2, pts, prm)
+        return pts.shape[0]
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    n = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    value = n / dt
+    cores = oracle.max_threads()
+    line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": {k: v for k, v in WORKLOAD.items()},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                             "sample": "full 1242x375 pair per step (detection + pyramids + tracking)"},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def run_cuda(args, rank: int, world: int, local_rank: int):
+    import torch
+    import paper_1901_09971_gb300 as dgf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pair = synth.make_pair(2, index=rank)
+    W, H = pair.W, pair.H
+    prm = dgf.RlofParams(levels=WORKLOAD["levels"], radius=WORKLOAD["radius"], max_iter=WORKLOAD["max_iter"],
+                         model=WORKLOAD["model"])
+    tr = dgf.PairTracker(W, H, WORKLOAD["win"], WORKLOAD["step"], prm, dev)
+    f1 = torch.from_numpy(pair.I1).to(dev)
+    f2 = torch.from_numpy(pair.I2).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def one_step(ev):
+        ev[0].record(stream)
+        dgf.detect(f1, tr.win, tr.step, out=tr.pts)
+        dgf.build_pyramid(f1, prm.levels, prm.storage, True, out=tr.pyr1)
+        dgf.build_pyramid(f2, prm.levels, prm.storage, False, out=tr.pyr2)
+        ev[1].record(stream)
+        dgf.track(tr.pyr1, tr.pyr2, W, H, tr.pts, prm, out=(tr.flow, tr.status, tr.iters, None))
+        ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        one_step([torch.cuda.Event(enable_timing=True) for _ in range(3)])
+    torch.cuda.synchronize(dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clocks:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)  # evict L2 between steps (outside the timed events)
+            one_step(evs[k])
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+    step_ms = np.array([e[0].elapsed_time(e[2]) for e in evs])
+    rlof_ms = np.array([e[1].elapsed_time(e[2]) for e in evs])
+    total_s = step_ms.sum() / 1e3
+    if dist:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    n_pts = tr.n
+    value = world * n_pts * args.steps / total_s
+
+    # dominant kernel: RLOF tracking, algorithmic FLOPs of the last step's trajectories
+    iters = tr.iters.cpu().numpy()
+    status = tr.status.cpu().numpy()
+    flops = algorithmic_flops(iters, status, prm.levels, prm.radius, prm.model)
+    achieved = flops / (rlof_ms.mean() / 1e3) / 1e12
+
+    # end to end through the public API: pinned host frames in, host results out
+    h1 = torch.from_numpy(pair.I1).pin_memory()
+    h2 = torch.from_numpy(pair.I2).pin_memory()
+    o_pts = torch.empty((n_pts, 2), dtype=torch.float32).pin_memory()
+    o_flow = torch.empty((n_pts, 2), dtype=torch.float32).pin_memory()
+    o_status = torch.empty(n_pts, dtype=torch.uint8).pin_memory()
+    d1 = torch.empty_like(f1)
+    d2 = torch.empty_like(f2)
+
+    def e2e_step():
+        d1.copy_(h1, non_blocking=True)
+        d2.copy_(h2, non_blocking=True)
+        pts, flow, st, _ = tr.run(d1, d2)
+        o_pts.copy_(pts, non_blocking=True)
+        o_flow.copy_(flow, non_blocking=True)
+        o_status.copy_(st, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e_ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    e2e_s = sum(e_ms) / 1e3
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * n_pts * args.steps / e2e_s
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(WORKLOAD, points_per_pair=n_pts, l2="flushed between steps (256 MiB write)",
+                               parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+                "pairs_per_s": world * args.steps / total_s,
+                "rlof_ms": float(rlof_ms.mean()), "detect_pyramid_ms": float((step_ms - rlof_ms).mean()),
+                "tracked_fraction": float(np.mean((status == 0) | (status == 4))),
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": kernel_traffic(),
+                             "peak_basis": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max clock)",
+                             "kernel": "rlof_kernel", "flops_per_launch": flops},
+                "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": 2 * W * H,
+                        "d2h_bytes_per_step": n_pts * (8 + 8 + 1)},
+                "gpu_launches": 4 * args.steps,
+                "clocks": clocks.summary()}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(pair)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_cuda(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * degraf.h - C ABI of the GB300 (sm_103a) DeGraF detection + RLOF tracking library.
+ *
+ * Implements the sparse-matching stage of DeGraF-Flow (Stephenson, Breckon,
+ * Katramados, arXiv 1901.09971, Section 2): DeGraF key-points on an even grid of
+ * frame 1 (Eq. 1-2 and the selection rule after them), tracked into frame 2 by
+ * robust local optical flow (RLOF) over an image pyramid.
+ *
+ * Conventions for every entry point:
+ *   - Array pointers marked "device" are CUDA device pointers owned by the caller.
+ *     The library never allocates memory in these calls and keeps no pointer after
+ *     returning.
+ *   - Work is enqueued asynchronously on `stream` (0 = legacy default stream). The
+ *     return value reports argument checks and launch errors only; errors raised
+ *     while kernels run surface at the caller's next synchronisation.
+ *   - Return value: DGF_OK (0) or a negative DGF_ERR_* code; dgf_strerror() names it.
+ *   - Image coordinates: x = column, y = row, pixel centres at integers.
+ *   - Floating-point work follows IEEE round-to-nearest (no fast-math).
+ */
+#ifndef DEGRAF_H
+#define DEGRAF_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define DGF_OK 0
+#define DGF_ERR_ARG (-1)       /* null pointer, bad size, pitch, window, radius or level count */
+#define DGF_ERR_WORKSPACE (-2) /* a caller buffer is smaller than the size query asks for */
+#define DGF_ERR_LEVELS (-3)    /* the coarsest pyramid level is smaller than the support */
+#define DGF_ERR_CUDA (-4)      /* a CUDA launch or runtime call failed */
+#define DGF_ERR_TIMEOUT (-5)   /* a bounded wait expired */
+#define DGF_ERR_DEVICE (-6)    /* a kernel reported an error through its status word */
+
+/* per-point tracking status (rlof_track `status` output) */
+#define DGF_TRACKED 0   /* converged at level 0 */
+#define DGF_OOB 1       /* the point centre left the level image */
+#define DGF_SMALL_EIG 2 /* gradient matrix too weak: lambda_min / (2r+1)^2 < min_eig */
+#define DGF_SINGULAR 3  /* non-positive Cholesky pivot in the Gauss-Newton solve */
+#define DGF_MAXITER 4   /* tracked, but level 0 hit max_iter before converging */
+
+/* pyramid storage types */
+#define DGF_F32 0
+#define DGF_F16 1
+
+#define DGF_MAX_LEVELS 6
+#define DGF_MAX_RADIUS 7
+#define DGF_MAX_WINDOW 64
+#define DGF_RLOF_PARAMS_VERSION 1
+
+/* Human-readable name of a DGF_* status code (static string, never NULL). */
+const char* dgf_strerror(int code);
+
+/* Library ABI version (major * 100 + minor). */
+int dgf_version(void);
+
+/* ---- DeGraF detection (Section 2, Eq. 1-2) ------------------------------- */
+
+/*
+ * Number of DeGraF key-points on a W x H frame: one per window position of the
+ * sliding grid with step `step` (Section 2, "Point detection"), counting only
+ * windows that lie fully inside the frame:
+ *   N = (floor((W - win_w) / step) + 1) * (floor((H - win_h) / step) + 1),
+ * or 0 when the window does not fit. Returns -1 on invalid arguments.
+ */
+long long dgf_degraf_count(int W, int H, int win_w, int win_h, int step);
+
+/*
+ * DeGraF key-point detection (Section 2, Eq. 1 and Eq. 2, selection rule after
+ * Eq. 2). For window (u, v) with top-left pixel (u*step, v*step), i = row and
+ * j = column inside the window:
+ *   S_pos = sum I, C_pos = (sum j I, sum i I) / S_pos;  m = max I in the window;
+ *   S_neg = sum (1 + m - I), C_neg = (sum j (1+m-I), sum i (1+m-I)) / S_neg;
+ *   key-point = window origin + (S_neg > S_pos ? C_neg : C_pos).
+ *   img      device, uint8 frame, row r at img + r * pitch (bytes), pitch >= W.
+ *   win_w, win_h in [1, DGF_MAX_WINDOW]; step >= 1.
+ *   pts      device, float [N][2] (x, y), N = dgf_degraf_count(); row-major over
+ *            window positions (v outer, u inner).
+ *   sums     device, nullable, int32 [N][4]: S_pos, sum j I, sum i I, m (exact).
+ * N = 0 is not an error (nothing is launched).
+ */
+int degraf_detect(const uint8_t* img, int W, int H, int pitch, int win_w, int win_h, int step,
+                  float* pts, int32_t* sums, cudaStream_t stream);
+
+/* ---- image pyramid -------------------------------------------------------- */
+
+/*
+ * Layout of a pyramid buffer. RLOF tracks through an image pyramid (Section 2,
+ * "Sparse point tracking"); the paper does not define it, and this library uses:
+ * level 0 = the frame; level l+1 is floor(W_l / 2) x floor(H_l / 2) with each pixel
+ * the mean of its 2x2 block of level l; gradients Ix, Iy are the Sobel kernels / 8
+ * with the border clamped. All values are exact dyadic rationals, so FP32 storage
+ * is exact; FP16 storage rounds each exact value once (round to nearest even).
+ * Planes are stored I_0 .. I_{L-1}, then (with_grad) Ix_0 .. Ix_{L-1},
+ * Iy_0 .. Iy_{L-1}; every plane starts on a 256-byte boundary and its rows are
+ * `pitch` elements apart (a multiple of 128 bytes). The intensity planes sit at the
+ * same offsets with or without gradients.
+ */
+typedef struct {
+    int levels, storage, with_grad;
+    int W[DGF_MAX_LEVELS], H[DGF_MAX_LEVELS], pitch[DGF_MAX_LEVELS]; /* pitch in elements */
+    size_t off_I[DGF_MAX_LEVELS], off_Ix[DGF_MAX_LEVELS], off_Iy[DGF_MAX_LEVELS]; /* bytes */
+    size_t bytes;
+} dgf_pyramid_layout;
+
+/* Fills *out for a W x H frame; off_Ix/off_Iy are 0 when with_grad = 0. Returns
+ * DGF_ERR_ARG for levels outside [1, DGF_MAX_LEVELS] or an empty coarsest level. */
+int dgf_pyramid_layout_get(int W, int H, int levels, int storage, int with_grad,
+                           dgf_pyramid_layout* out);
+
+/* Bytes a pyramid buffer needs (0 on invalid arguments). */
+size_t dgf_pyramid_bytes(int W, int H, int levels, int storage, int with_grad);
+
+/*
+ * Builds the pyramid of one uint8 frame into `pyr` (device, pyr_bytes >=
+ * dgf_pyramid_bytes(), 256-byte aligned). img/pitch as in degraf_detect.
+ * storage: DGF_F32 or DGF_F16. with_grad: 1 to also write Ix and Iy (frame 1 of a
+ * pair needs them, frame 2 does not).
+ */
+int pyramid_build(const uint8_t* img, int W, int H, int pitch, int levels, int storage,
+                  int with_grad, void* pyr, size_t pyr_bytes, cudaStream_t stream);
+
+/* ---- RLOF tracking (Section 2 "Sparse point tracking"; Section 3 "Parameters") */
+
+/*
+ * Tracking parameters. The paper names RLOF with its illumination model but gives
+ * no formulas; the reading implemented (identical in the FP64 test oracle):
+ *   for each level l = levels-1 .. 0 (coarse to fine):
+ *     p_l = (p + 1/2) / 2^l - 1/2; template T, Tx, Ty = bilinear samples of frame 1's
+ *     level at p_l + k, k in [-radius, radius]^2 (border taps clamped);
+ *     SMALL_EIG if lambda_min(sum [Tx Ty]^T [Tx Ty]) / (2 radius + 1)^2 < min_eig;
+ *     d = 0; up to max_iter Gauss-Newton steps: q = p_l + g + d (OOB if q leaves
+ *     [0, W_l-1] x [0, H_l-1]); J = bilinear frame-2 samples at q + k;
+ *       model 4: r = J - (1+m) T - c, a = (Tx, Ty, -T, -1)
+ *       model 2: r = J - T,           a = (Tx, Ty)
+ *     Hampel IRLS weights w = psi(r)/r with knots (hampel_a, hampel_b, hampel_c):
+ *       psi = r (|r|<=a), a sgn r (a<|r|<=b), a sgn r (c-|r|)/(c-b) (b<|r|<=c), 0 beyond;
+ *     solve (sum w a a^T) delta = -(sum w a r) by Cholesky (SINGULAR on a
+ *     non-positive pivot); d += delta[0:2], (m, c) += delta[2:4]; stop when
+ *     |delta[0:2]| < eps. Then g = 2 (g + d) for the next finer level.
+ *   flow = g + d at level 0.
+ */
+typedef struct {
+    int version;  /* DGF_RLOF_PARAMS_VERSION */
+    int levels;   /* pyramid levels, 1..DGF_MAX_LEVELS, as both pyramids were built */
+    int radius;   /* support radius r, 1..DGF_MAX_RADIUS; (2r+1)^2 samples */
+    int max_iter; /* Gauss-Newton iterations per level, 1..255 */
+    int model;    /* 2 = translation, 4 = translation + gain/offset illumination */
+    int storage;  /* DGF_F32 or DGF_F16, as both pyramids were built */
+    float eps;    /* convergence threshold on |delta d| in pixels */
+    float hampel_a, hampel_b, hampel_c; /* 0 < a <= b < c */
+    float min_eig;
+} dgf_rlof_params;
+
+/* Fills *p with the defaults: levels 3, radius 4, max_iter 30, model 4, F32,
+ * eps 1e-3, Hampel (8, 16, 32), min_eig 1e-3. */
+void dgf_rlof_params_default(dgf_rlof_params* p);
+
+/* Tuning hook: lanes per tracked point, 8, 16 or 32 (0 = automatic choice, the
+ * default). Applies to later rlof_track calls from any thread. Returns the previous
+ * setting, or DGF_ERR_ARG for another value. Radii above 5 always use 32 lanes. */
+int dgf_rlof_set_lanes(int lanes);
+
+/*
+ * Tracks n points from frame 1 into frame 2.
+ *   pyr1   device, pyramid of frame 1 built with with_grad = 1.
+ *   pyr2   device, pyramid of frame 2 (gradients optional).
+ *   W, H   level-0 size of both frames.
+ *   pts    device, float [n][2] start points in frame 1 (e.g. degraf_detect output).
+ *   flow   device, float [n][2] output: displacement into frame 2; 0 for lost points.
+ *   status device, uint8 [n] output: DGF_TRACKED .. DGF_MAXITER.
+ *   iters  device, nullable, uint8 [n]: Gauss-Newton updates over all levels
+ *          (saturates at 255).
+ *   illum  device, nullable, float [n][2]: gain m and offset c (model 4; else 0).
+ * Returns DGF_ERR_LEVELS when the coarsest level is narrower or lower than
+ * 2 radius + 2 pixels. n = 0 is not an error.
+ */
+int rlof_track(const void* pyr1, const void* pyr2, int W, int H, const float* pts, int n,
+               const dgf_rlof_params* p, float* flow, uint8_t* status, uint8_t* iters,
+               float* illum, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEGRAF_H */

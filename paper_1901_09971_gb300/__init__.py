@@ -1,0 +1,12 @@
+"""DeGraF detection + RLOF tracking (arXiv 1901.09971) as GB300 CUDA kernels.
+
+The compute lives in libdegraf.so (C ABI, include/degraf.h); this package is the
+thin torch binding. Nothing here computes on the CPU.
+"""
+from ._abi import (  # noqa: F401
+    DegrafError, F16, F32, MAXITER, OOB, SINGULAR, SMALL_EIG, TRACKED, load,
+)
+from .api import (  # noqa: F401
+    PairTracker, RlofParams, build_pyramid, degraf_count, detect, pyramid_bytes, pyramid_layout,
+    pyramid_planes, set_lanes, track, track_pair, version,
+)

@@ -1,0 +1,90 @@
+"""ctypes declarations of libdegraf.so (the C ABI in include/degraf.h).
+
+Loading never falls back to anything: a missing or unloadable library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+DGF_OK = 0
+DGF_ERR_ARG = -1
+DGF_ERR_WORKSPACE = -2
+DGF_ERR_LEVELS = -3
+DGF_ERR_CUDA = -4
+DGF_ERR_TIMEOUT = -5
+DGF_ERR_DEVICE = -6
+
+TRACKED, OOB, SMALL_EIG, SINGULAR, MAXITER = 0, 1, 2, 3, 4
+F32, F16 = 0, 1
+MAX_LEVELS = 6
+MAX_RADIUS = 7
+RLOF_PARAMS_VERSION = 1
+
+# Every entry point that include/degraf.h declares.
+EXPORTS = (
+    "dgf_strerror", "dgf_version", "dgf_degraf_count", "degraf_detect", "dgf_pyramid_layout_get",
+    "dgf_pyramid_bytes", "pyramid_build", "dgf_rlof_params_default", "dgf_rlof_set_lanes", "rlof_track",
+)
+
+
+class PyramidLayout(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("storage", ctypes.c_int), ("with_grad", ctypes.c_int),
+                ("W", ctypes.c_int * MAX_LEVELS), ("H", ctypes.c_int * MAX_LEVELS),
+                ("pitch", ctypes.c_int * MAX_LEVELS),
+                ("off_I", ctypes.c_size_t * MAX_LEVELS), ("off_Ix", ctypes.c_size_t * MAX_LEVELS),
+                ("off_Iy", ctypes.c_size_t * MAX_LEVELS), ("bytes", ctypes.c_size_t)]
+
+
+class RlofParamsC(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_int), ("levels", ctypes.c_int), ("radius", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("model", ctypes.c_int), ("storage", ctypes.c_int),
+                ("eps", ctypes.c_float), ("hampel_a", ctypes.c_float), ("hampel_b", ctypes.c_float),
+                ("hampel_c", ctypes.c_float), ("min_eig", ctypes.c_float)]
+
+
+class DegrafError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn} failed: {msg} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libdegraf.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdegraf.so not found at {path}; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    P, I, Z, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_longlong
+    L.dgf_strerror.argtypes, L.dgf_strerror.restype = [I], ctypes.c_char_p
+    L.dgf_version.argtypes, L.dgf_version.restype = [], I
+    L.dgf_degraf_count.argtypes, L.dgf_degraf_count.restype = [I, I, I, I, I], LL
+    L.degraf_detect.argtypes, L.degraf_detect.restype = [P, I, I, I, I, I, I, P, P, P], I
+    L.dgf_pyramid_layout_get.argtypes = [I, I, I, I, I, ctypes.POINTER(PyramidLayout)]
+    L.dgf_pyramid_layout_get.restype = I
+    L.dgf_pyramid_bytes.argtypes, L.dgf_pyramid_bytes.restype = [I, I, I, I, I], Z
+    L.pyramid_build.argtypes, L.pyramid_build.restype = [P, I, I, I, I, I, I, P, Z, P], I
+    L.dgf_rlof_params_default.argtypes = [ctypes.POINTER(RlofParamsC)]
+    L.dgf_rlof_params_default.restype = None
+    L.dgf_rlof_set_lanes.argtypes, L.dgf_rlof_set_lanes.restype = [I], I
+    L.rlof_track.argtypes = [P, P, I, I, P, I, ctypes.POINTER(RlofParamsC), P, P, P, P, P]
+    L.rlof_track.restype = I
+    _lib = L
+    return L
+
+
+def check(fn: str, rc: int) -> None:
+    if rc != DGF_OK:
+        raise DegrafError(fn, rc, load().dgf_strerror(rc).decode())

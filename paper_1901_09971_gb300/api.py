@@ -1,0 +1,198 @@
+"""Torch-facing binding of libdegraf.so: argument marshalling only.
+
+Every step of detection, pyramid construction and tracking runs in the library's
+CUDA kernels; torch supplies device memory and the current stream. Functions
+raise DegrafError with the library's status text on any failure.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import torch
+
+from . import _abi
+from ._abi import F16, F32, check, load
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _frame(frame: torch.Tensor):
+    if frame.dtype != torch.uint8 or frame.dim() != 2 or not frame.is_cuda:
+        raise ValueError("frame must be a 2-D uint8 CUDA tensor")
+    if frame.stride(1) != 1:
+        raise ValueError("frame rows must be contiguous")
+    H, W = frame.shape
+    return W, H, frame.stride(0)
+
+
+@dataclasses.dataclass
+class RlofParams:
+    """Tracking parameters (mirror of dgf_rlof_params)."""
+
+    levels: int = 3
+    radius: int = 4
+    max_iter: int = 30
+    model: int = 4
+    storage: int = F32
+    eps: float = 1e-3
+    hampel_a: float = 8.0
+    hampel_b: float = 16.0
+    hampel_c: float = 32.0
+    min_eig: float = 1e-3
+
+    def c(self) -> _abi.RlofParamsC:
+        return _abi.RlofParamsC(_abi.RLOF_PARAMS_VERSION, self.levels, self.radius, self.max_iter,
+                                self.model, self.storage, self.eps, self.hampel_a, self.hampel_b,
+                                self.hampel_c, self.min_eig)
+
+
+def version() -> int:
+    return int(load().dgf_version())
+
+
+def degraf_count(W: int, H: int, win: int, step: int, win_h: int | None = None) -> int:
+    n = int(load().dgf_degraf_count(W, H, win, win if win_h is None else win_h, step))
+    if n < 0:
+        raise _abi.DegrafError("dgf_degraf_count", _abi.DGF_ERR_ARG, "invalid argument")
+    return n
+
+
+def detect(frame: torch.Tensor, win: int, step: int, win_h: int | None = None,
+           with_sums: bool = False, out: torch.Tensor | None = None):
+    """DeGraF key-points of a uint8 frame: float32 [N, 2] (and int32 [N, 4] sums)."""
+    W, H, pitch = _frame(frame)
+    wh = win if win_h is None else win_h
+    n = degraf_count(W, H, win, step, wh)
+    pts = out if out is not None else torch.empty((n, 2), dtype=torch.float32, device=frame.device)
+    sums = torch.empty((n, 4), dtype=torch.int32, device=frame.device) if with_sums else None
+    check("degraf_detect", load().degraf_detect(_ptr(frame), W, H, pitch, win, wh, step, _ptr(pts),
+                                                _ptr(sums), _stream()))
+    return (pts, sums) if with_sums else pts
+
+
+def pyramid_layout(W: int, H: int, levels: int, storage: int = F32, with_grad: bool = True) -> dict:
+    L = _abi.PyramidLayout()
+    check("dgf_pyramid_layout_get",
+          load().dgf_pyramid_layout_get(W, H, levels, storage, int(with_grad), ctypes.byref(L)))
+    n = L.levels
+    return dict(levels=n, storage=L.storage, with_grad=bool(L.with_grad), W=list(L.W[:n]),
+                H=list(L.H[:n]), pitch=list(L.pitch[:n]), off_I=list(L.off_I[:n]),
+                off_Ix=list(L.off_Ix[:n]), off_Iy=list(L.off_Iy[:n]), bytes=int(L.bytes))
+
+
+def pyramid_bytes(W: int, H: int, levels: int, storage: int = F32, with_grad: bool = True) -> int:
+    return int(load().dgf_pyramid_bytes(W, H, levels, storage, int(with_grad)))
+
+
+def build_pyramid(frame: torch.Tensor, levels: int, storage: int = F32, with_grad: bool = True,
+                  out: torch.Tensor | None = None) -> torch.Tensor:
+    """Pyramid buffer (uint8 tensor laid out as pyramid_layout describes)."""
+    W, H, pitch = _frame(frame)
+    nbytes = pyramid_bytes(W, H, levels, storage, with_grad)
+    buf = out if out is not None else torch.empty(nbytes, dtype=torch.uint8, device=frame.device)
+    check("pyramid_build", load().pyramid_build(_ptr(frame), W, H, pitch, levels, storage,
+                                                int(with_grad), _ptr(buf), buf.numel(), _stream()))
+    return buf
+
+
+def pyramid_planes(buf: torch.Tensor, layout: dict):
+    """[(I, Ix, Iy)] per level as float32/float16 views [H_l, W_l] into buf."""
+    dt = torch.float32 if layout["storage"] == F32 else torch.float16
+    es = 4 if dt == torch.float32 else 2
+    out = []
+    for l in range(layout["levels"]):
+        Wl, Hl, p = layout["W"][l], layout["H"][l], layout["pitch"][l]
+
+        def plane(off):
+            return buf[off: off + p * Hl * es].view(dt).view(Hl, p)[:, :Wl]
+
+        grads = (plane(layout["off_Ix"][l]), plane(layout["off_Iy"][l])) if layout["with_grad"] else (None, None)
+        out.append((plane(layout["off_I"][l]), *grads))
+    return out
+
+
+def set_lanes(lanes: int) -> int:
+    prev = int(load().dgf_rlof_set_lanes(lanes))
+    if prev < 0:
+        raise _abi.DegrafError("dgf_rlof_set_lanes", prev, "lanes must be 0, 8, 16 or 32")
+    return prev
+
+
+def track(pyr1: torch.Tensor, pyr2: torch.Tensor, W: int, H: int, pts: torch.Tensor, params: RlofParams,
+          with_iters: bool = False, with_illum: bool = False, out=None):
+    """RLOF tracking of pts [n, 2] (float32, CUDA): returns flow, status[, iters][, illum]."""
+    if pts.dtype != torch.float32 or not pts.is_contiguous():
+        raise ValueError("pts must be a contiguous float32 tensor [n, 2]")
+    n = pts.shape[0]
+    dev = pts.device
+    if out is None:
+        flow = torch.empty((n, 2), dtype=torch.float32, device=dev)
+        status = torch.empty(n, dtype=torch.uint8, device=dev)
+        iters = torch.empty(n, dtype=torch.uint8, device=dev) if with_iters else None
+        illum = torch.empty((n, 2), dtype=torch.float32, device=dev) if with_illum else None
+    else:
+        flow, status, iters, illum = out
+    prm = params.c()
+    check("rlof_track", load().rlof_track(_ptr(pyr1), _ptr(pyr2), W, H, _ptr(pts), n, ctypes.byref(prm),
+                                          _ptr(flow), _ptr(status), _ptr(iters), _ptr(illum), _stream()))
+    res = [flow, status]
+    if with_iters:
+        res.append(iters)
+    if with_illum:
+        res.append(illum)
+    return tuple(res)
+
+
+class PairTracker:
+    """Device-resident DeGraF + RLOF for frame pairs of one size and parameter set.
+
+    Buffers (pyramids, points, outputs) are allocated once; ``run`` enqueues
+    detection, both pyramid builds and tracking on the current stream.
+    """
+
+    def __init__(self, W: int, H: int, win: int, step: int, params: RlofParams,
+                 device: torch.device | str = "cuda"):
+        self.W, self.H, self.win, self.step, self.params = W, H, win, step, params
+        self.device = torch.device(device)
+        self.n = degraf_count(W, H, win, step)
+        st = params.storage
+        self.pyr1 = torch.empty(pyramid_bytes(W, H, params.levels, st, True), dtype=torch.uint8,
+                                device=self.device)
+        self.pyr2 = torch.empty(pyramid_bytes(W, H, params.levels, st, False), dtype=torch.uint8,
+                                device=self.device)
+        self.pts = torch.empty((self.n, 2), dtype=torch.float32, device=self.device)
+        self.flow = torch.empty((self.n, 2), dtype=torch.float32, device=self.device)
+        self.status = torch.empty(self.n, dtype=torch.uint8, device=self.device)
+        self.iters = torch.empty(self.n, dtype=torch.uint8, device=self.device)
+
+    def run(self, frame1: torch.Tensor, frame2: torch.Tensor):
+        p = self.params
+        detect(frame1, self.win, self.step, out=self.pts)
+        build_pyramid(frame1, p.levels, p.storage, True, out=self.pyr1)
+        build_pyramid(frame2, p.levels, p.storage, False, out=self.pyr2)
+        track(self.pyr1, self.pyr2, self.W, self.H, self.pts, p,
+              out=(self.flow, self.status, self.iters, None))
+        return self.pts, self.flow, self.status, self.iters
+
+
+def track_pair(frame1, frame2, win: int, step: int, params: RlofParams, device="cuda"):
+    """End-to-end call on host or device frames: returns host (pts, flow, status).
+
+    Host frames (numpy arrays or CPU tensors) are copied to the device, tracked,
+    and the results copied back.
+    """
+    f1 = torch.as_tensor(frame1)
+    f2 = torch.as_tensor(frame2)
+    H, W = f1.shape
+    tr = PairTracker(W, H, win, step, params, device)
+    d1 = f1.to(tr.device, non_blocking=True)
+    d2 = f2.to(tr.device, non_blocking=True)
+    pts, flow, status, _ = tr.run(d1, d2)
+    return pts.cpu(), flow.cpu(), status.cpu()

@@ -1,0 +1,110 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every entry point
+include/degraf.h declares; host-side size queries and argument checks behave as
+documented (these paths return before any CUDA call); the product package never
+touches the oracle."""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+import paper_1901_09971_gb300 as dgf
+from paper_1901_09971_gb300 import _abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "degraf.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_][a-z0-9_ ]*\**\s+\**([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declarations_are_exported():
+    lib = dgf.load()
+    names = declared_functions()
+    assert "rlof_track" in names and "degraf_detect" in names and "pyramid_build" in names
+    assert sorted(_abi.EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", _abi.lib_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (\w+)$", out, flags=re.M))
+    assert set(names) <= exported
+
+
+def test_count_matches_oracle():
+    for (W, H, w, h, s) in [(1242, 375, 7, 7, 3), (256, 128, 8, 8, 4), (1240, 376, 3, 3, 9), (5, 5, 7, 7, 1),
+                            (64, 64, 64, 64, 1), (100, 37, 9, 2, 5)]:
+        assert dgf.degraf_count(W, H, w, s, win_h=h) == oracle.degraf_count(W, H, w, h, s)
+    assert dgf.load().dgf_degraf_count(100, 100, 65, 8, 1) == -1
+    assert dgf.load().dgf_degraf_count(100, 100, 8, 8, 0) == -1
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_pyramid_layout(storage):
+    es = 4 if storage == 0 else 2
+    a = dgf.pyramid_layout(1242, 375, 5, storage, True)
+    b = dgf.pyramid_layout(1242, 375, 5, storage, False)
+    assert a["W"] == [1242, 621, 310, 155, 77] and a["H"] == [375, 187, 93, 46, 23]
+    assert a["off_I"] == b["off_I"]  # intensity planes independent of the gradient planes
+    for l in range(5):
+        assert a["pitch"][l] * es % 128 == 0 and a["pitch"][l] >= a["W"][l]
+        for off in (a["off_I"][l], a["off_Ix"][l], a["off_Iy"][l]):
+            assert off % 256 == 0
+    assert a["bytes"] > b["bytes"] and dgf.pyramid_bytes(1242, 375, 5, storage, True) == a["bytes"]
+    assert dgf.pyramid_bytes(1242, 375, 7, storage, True) == 0
+    assert dgf.pyramid_bytes(3, 3, 3, storage, True) == 0  # empty coarsest level
+
+
+def test_strerror_and_defaults():
+    lib = dgf.load()
+    for code in range(0, -7, -1):
+        assert lib.dgf_strerror(code)
+    assert lib.dgf_strerror(-99) == b"unknown status"
+    p = _abi.RlofParamsC()
+    lib.dgf_rlof_params_default(ctypes.byref(p))
+    assert (p.version, p.levels, p.radius, p.max_iter, p.model) == (1, 3, 4, 30, 4)
+    assert abs(p.eps - 1e-3) < 1e-9 and (p.hampel_a, p.hampel_b, p.hampel_c) == (8.0, 16.0, 32.0)
+
+
+def test_host_side_errors_return_before_launch():
+    lib = dgf.load()
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails its checks first
+    p = dgf.RlofParams(levels=5, radius=5).c()
+    bad = dgf.RlofParams(levels=5, radius=5).c()
+    bad.version = 7
+    assert lib.rlof_track(fake, fake, 1242, 375, fake, 10, ctypes.byref(bad), fake, fake, None, None, None) == -1
+    bad = dgf.RlofParams(levels=5, radius=9).c()
+    assert lib.rlof_track(fake, fake, 1242, 375, fake, 10, ctypes.byref(bad), fake, fake, None, None, None) == -1
+    bad = dgf.RlofParams(hampel_a=8, hampel_b=16, hampel_c=16).c()
+    assert lib.rlof_track(fake, fake, 1242, 375, fake, 10, ctypes.byref(bad), fake, fake, None, None, None) == -1
+    # coarsest level 38x11 is lower than 2r + 2 = 12
+    deep = dgf.RlofParams(levels=6, radius=5).c()
+    assert lib.rlof_track(fake, fake, 1242, 375, fake, 10, ctypes.byref(deep), fake, fake, None, None, None) == -3
+    # null outputs with points to track
+    assert lib.rlof_track(fake, fake, 1242, 375, fake, 10, ctypes.byref(p), None, fake, None, None, None) == -1
+    # nothing to track: success without a launch
+    assert lib.rlof_track(None, None, 1242, 375, None, 0, ctypes.byref(p), None, None, None, None, None) == 0
+    # pyramid buffer too small / misaligned
+    assert lib.pyramid_build(fake, 1242, 375, 1242, 5, 0, 1, fake, 1024, None) == -2
+    assert lib.pyramid_build(fake, 1242, 375, 1242, 5, 0, 1, ctypes.c_void_p((1 << 20) + 64), 1 << 30, None) == -1
+    assert lib.pyramid_build(fake, 1242, 375, 1000, 5, 0, 1, fake, 1 << 30, None) == -1
+    # detection: bad window, and an empty grid (no launch)
+    assert lib.degraf_detect(fake, 100, 100, 100, 0, 7, 3, fake, None, None) == -1
+    assert lib.degraf_detect(fake, 5, 5, 5, 7, 7, 3, None, None, None) == 0
+
+
+def test_product_package_never_loads_the_oracle():
+    code = ("import sys; sys.path.insert(0, %r); import paper_1901_09971_gb300 as d; d.load(); "
+            "import bench; assert 'oracle' not in sys.modules, 'oracle imported'" % ROOT)
+    subprocess.run([sys.executable, "-c", code], check=True, cwd=ROOT)
+    pkg = os.path.join(ROOT, "paper_1901_09971_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                assert "oracle" not in open(os.path.join(dirpath, f)).read().lower(), f
