@@ -180,6 +180,8 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
     prm = dgf.RlofParams(levels=WORKLOAD["levels"], radius=WORKLOAD["radius"], max_iter=WORKLOAD["max_iter"],
                          model=WORKLOAD["model"])
     tr = dgf.PairTracker(W, H, WORKLOAD["win"], WORKLOAD["step"], prm, dev)
+    if args.lanes:
+        dgf.set_lanes(args.lanes)
     f1 = torch.from_numpy(pair.I1).to(dev)
     f2 = torch.from_numpy(pair.I2).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -292,6 +294,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per tracked point (0 = automatic)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))

@@ -163,7 +163,8 @@ void dgf_rlof_params_default(dgf_rlof_params* p);
 
 /* Tuning hook: lanes per tracked point, 8, 16 or 32 (0 = automatic choice, the
  * default). Applies to later rlof_track calls from any thread. Returns the previous
- * setting, or DGF_ERR_ARG for another value. Radii above 5 always use 32 lanes. */
+ * setting, or DGF_ERR_ARG for another value. Only radius 4 and 5 honour 8 or 16;
+ * every other radius uses 32 lanes. */
 int dgf_rlof_set_lanes(int lanes);
 
 /*

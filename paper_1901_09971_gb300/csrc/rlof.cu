@@ -2,16 +2,21 @@
 // Section 3 "Parameters": RLOF with the illumination model).
 //
 // Work mapping: a group of G consecutive lanes (G = 8, 16 or 32) owns one point
-// for its whole coarse-to-fine trajectory. Each lane holds SL support samples in
-// registers (slot s = lane + G * j of the (2r+1)^2 support, row-major), so the
-// template T, Tx, Ty of a level is sampled once and stays in registers for all of
-// that level's Gauss-Newton iterations. Per iteration every lane samples frame 2
-// at its slots (bilinear, FP32, all slots share one set of fractional weights),
-// forms the Hampel weight and its partial sums of the 4x4 (or 2x2) normal
-// equations, and the group reduces them with xor shuffles. The butterfly leaves
-// bit-identical sums in every lane, so the FP32 Cholesky solve, the update and
-// the convergence test run redundantly and the group's control flow stays
-// uniform; points converge and exit independently.
+// for its whole coarse-to-fine trajectory. The (2r+1)^2 support is cut into
+// (2r+1) x (r+1) horizontal sample pairs (the second sample of the last pair
+// column is masked out); lane l of a group owns pairs l, l + G, l + 2G, ... Both
+// samples of a pair share the bilinear weights of the iterate and four of their
+// six taps, so a pair is sampled with four loads (an 8-byte and a 4-byte load per
+// tap row, chosen by the parity of the tap block's first column) and evaluated
+// with packed FP32x2 instructions (fma.rn.f32x2 and friends on sm_100+).
+// The template T, Tx, Ty of the current level stays in registers for all of the
+// level's iterations (shared memory would add to the L1 data-pipe traffic that
+// the tap loads and shuffles already load heavily). Per iteration every lane
+// forms Hampel weights and its partial sums of the 4x4 (or 2x2) normal
+// equations, the group reduces them with xor shuffles (the butterfly leaves
+// bit-identical sums in every lane), and the FP32 Cholesky solve, the update and
+// the convergence test run redundantly, so each group's control flow stays
+// uniform and points converge and exit independently.
 #include "common.cuh"
 
 namespace {
@@ -40,41 +45,115 @@ __device__ __forceinline__ float group_sum(float v, unsigned mask)
     return v;
 }
 
-// Bilinear sample with clamped taps at integer base (xi, yi) and weights (ax, ay).
-template <typename TS>
-__device__ __forceinline__ float sample_clamped(const TS* P, int pitch, int W, int H, int xi, int yi, float ax,
-                                                float ay)
+// Sum of 16 values over a group of G lanes, returned in every lane (h[k] = total of
+// v[k] over the group). Reduce-scatter: at each stage the lane keeps the half of its
+// values its partner does not, adding the partner's copy, so 16 + 8 + 4 + ... values
+// cross lanes instead of 16 per butterfly stage; then the 16 totals, spread one or
+// two per lane, are gathered with indexed shuffles. Sums run in a fixed order per
+// value, so every lane receives bit-identical totals.
+template <int G>
+__device__ __forceinline__ void group_allreduce16(float (&v)[16], float (&h)[16], unsigned mask, int lane)
 {
-    const int xa = min(max(xi, 0), W - 1), xb = min(max(xi + 1, 0), W - 1);
-    const int ya = min(max(yi, 0), H - 1), yb = min(max(yi + 1, 0), H - 1);
-    const TS* r0 = P + (size_t)ya * pitch;
-    const TS* r1 = P + (size_t)yb * pitch;
-    const float v00 = dgf::ld(r0 + xa), v01 = dgf::ld(r0 + xb);
-    const float v10 = dgf::ld(r1 + xa), v11 = dgf::ld(r1 + xb);
-    const float top = fmaf(ax, v01 - v00, v00);
-    const float bot = fmaf(ax, v11 - v10, v10);
-    return fmaf(ay, bot - top, top);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int o = (G >> 1) >> s;  // partner offset of this stage
+        const int n = 16 >> s;        // values still held per lane
+        if (o >= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < n / 2; ++i) {
+                const float send = up ? v[i] : v[i + n / 2];
+                const float keep = up ? v[i + n / 2] : v[i];
+                v[i] = keep + __shfl_xor_sync(mask, send, o);
+            }
+        }
+    }
+    if (G == 32) v[0] += __shfl_xor_sync(mask, v[0], 1);
+    // total k now sits in lane k (G = 16), in lane k / 2 element k % 2 (G = 8), or
+    // in lanes 2k and 2k + 1 (G = 32)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (G == 16) h[k] = __shfl_sync(mask, v[0], k, 16);
+        if (G == 8) h[k] = __shfl_sync(mask, v[k & 1], k >> 1, 8);
+        if (G == 32) h[k] = __shfl_sync(mask, v[0], 2 * k, 32);
+    }
 }
 
-// Bilinear sample of four in-bounds taps starting at p (row stride pitch).
-template <typename TS>
-__device__ __forceinline__ float sample_inside(const TS* p, int pitch, float ax, float ay)
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// Bilinear weights of the four taps (top-left, top-right, bottom-left,
+// bottom-right) for fractional offsets (ax, ay), duplicated for a sample pair.
+struct PairWeights {
+    float2 w00, w01, w10, w11;
+    __device__ __forceinline__ PairWeights(float ax, float ay)
+    {
+        const float bx = 1.f - ax, by = 1.f - ay;
+        w00 = f2(bx * by);
+        w01 = f2(ax * by);
+        w10 = f2(bx * ay);
+        w11 = f2(ax * ay);
+    }
+};
+
+// Two horizontally adjacent bilinear samples from their 2x3 taps (a0 a1 a2 / b0 b1 b2).
+__device__ __forceinline__ float2 bilinear_pair(const PairWeights& w, float a0, float a1, float a2, float b0,
+                                                float b1, float b2)
 {
-    const float v00 = dgf::ld(p), v01 = dgf::ld(p + 1);
-    const float v10 = dgf::ld(p + pitch), v11 = dgf::ld(p + pitch + 1);
-    const float top = fmaf(ax, v01 - v00, v00);
-    const float bot = fmaf(ax, v11 - v10, v10);
-    return fmaf(ay, bot - top, top);
+    float2 J = __fmul2_rn(w.w00, make_float2(a0, a1));
+    J = __ffma2_rn(w.w01, make_float2(a1, a2), J);
+    J = __ffma2_rn(w.w10, make_float2(b0, b1), J);
+    return __ffma2_rn(w.w11, make_float2(b1, b2), J);
 }
 
-// Hampel IRLS weight psi(r) / r (continuous three-part Hampel).
-__device__ __forceinline__ float hampel_weight(float r, float ha, float hb, float hc, float inv_cb)
+// Loads of two consecutive samples starting at p; 8-byte aligned when requested.
+__device__ __forceinline__ float2 ld2(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ float2 ld2(const __half* p)
+{
+    return __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+}
+
+// Sample pair whose taps are all inside the plane; p points at tap a0. EVEN: a0
+// sits on an 8-byte (FP32) or 4-byte (FP16) boundary, so (a0, a1) and (b0, b1)
+// load as pairs; otherwise (a1, a2) and (b1, b2) do.
+template <typename TS, bool EVEN>
+__device__ __forceinline__ float2 pair_inside(const TS* p, int pitch, const PairWeights& w)
+{
+    if (EVEN) {
+        const float2 a01 = ld2(p), b01 = ld2(p + pitch);
+        return bilinear_pair(w, a01.x, a01.y, dgf::ld(p + 2), b01.x, b01.y, dgf::ld(p + pitch + 2));
+    } else {
+        const float2 a12 = ld2(p + 1), b12 = ld2(p + pitch + 1);
+        return bilinear_pair(w, dgf::ld(p), a12.x, a12.y, dgf::ld(p + pitch), b12.x, b12.y);
+    }
+}
+
+// Sample pair at integer tap origin (xi, yi) with every tap clamped to the border.
+template <typename TS>
+__device__ __forceinline__ float2 pair_clamped(const TS* P, int pitch, int W, int H, int xi, int yi,
+                                               const PairWeights& w)
+{
+    const int xa = min(max(xi, 0), W - 1), xb = min(max(xi + 1, 0), W - 1), xc = min(max(xi + 2, 0), W - 1);
+    const TS* r0 = P + (size_t)min(max(yi, 0), H - 1) * pitch;
+    const TS* r1 = P + (size_t)min(max(yi + 1, 0), H - 1) * pitch;
+    return bilinear_pair(w, dgf::ld(r0 + xa), dgf::ld(r0 + xb), dgf::ld(r0 + xc), dgf::ld(r1 + xa),
+                         dgf::ld(r1 + xb), dgf::ld(r1 + xc));
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Hampel IRLS weight psi(r) / r of the continuous three-part Hampel function:
+//   min(1, a / |r|) * clamp((c - |r|) / (c - b), 0, 1)
+// equals 1 for |r| <= a, a / |r| up to b, a (c - |r|) / ((c - b) |r|) up to c, 0 beyond.
+__device__ __forceinline__ float hampel_weight(float r, float ha, float icb, float hc_icb)
 {
     const float ar = fabsf(r);
-    const float inv = __frcp_rn(fmaxf(ar, ha));
-    float w = ha * inv;
-    w = ar <= hb ? w : w * fmaxf((hc - ar) * inv_cb, 0.f);
-    return ar <= ha ? 1.f : w;
+    const float w = __saturatef(ha * rcp_approx(ar));
+    return w * __saturatef(fmaf(-ar, icb, hc_icb));
 }
 
 // Cholesky solve of the symmetric positive definite N x N system H x = rhs.
@@ -118,8 +197,74 @@ __device__ __forceinline__ bool chol_solve(float (&H)[N][N], const float (&rhs)[
     return true;
 }
 
-template <typename TS, int G, int SL, int MODEL>
-__global__ void __launch_bounds__(256) rlof_kernel(const RlofArgs a)
+constexpr int kThreads = 128;
+
+// Per-lane state of one point's support at the current level: the template
+// T, Tx, Ty of each owned pair, the pair's tap offset in the tap block and the
+// mask of its second sample (0 for the column past the support).
+template <int SLP>
+struct Support {
+    float2 T[SLP], Tx[SLP], Ty[SLP];
+    int off[SLP];
+    float msk[SLP];
+};
+
+// Accumulates the weighted normal equations of the lane's pairs at one iterate.
+// acc[0..9] = sum w (TxTx, TxTy, TxT, Tx, TyTy, TyT, Ty, TT, T, 1); acc[10..13] =
+// sum w r (Tx, Ty, T, 1), each as .x/.y partial sums of a pair's two samples.
+// MODE 0: taps inside, even first column; 1: inside, odd; 2: clamped taps.
+template <typename TS, int G, int SLP, int MODEL, int MODE>
+__device__ __forceinline__ void accumulate(const Support<SLP>& S, float2 (&acc)[14], const TS* I2, int pitch, int W,
+                                           int H, int bx, int by, const PairWeights& pw, int lane, int np, int pc,
+                                           float g1, float c, float ha, float icb, float hc_icb)
+{
+    const TS* base = I2 + (ptrdiff_t)by * pitch + bx;
+    const float2 ng1 = f2(-g1), nc = f2(-c);
+#pragma unroll
+    for (int j = 0; j < SLP; ++j) {
+        const int q = lane + G * j;
+        // SLP = ceil(np / G), so only the last slot can hold pairs past the support;
+        // testing it there alone leaves the loads of all other slots free to be hoisted
+        if (j == SLP - 1 && q >= np) break;
+        const float2 T = S.T[j], Tx = S.Tx[j], Ty = S.Ty[j];
+        float2 J;
+        if (MODE == 0) {
+            J = pair_inside<TS, true>(base + S.off[j], pitch, pw);
+        } else if (MODE == 1) {
+            J = pair_inside<TS, false>(base + S.off[j], pitch, pw);
+        } else {
+            const int ky = q / pc, kp = q - ky * pc;
+            J = pair_clamped(I2, pitch, W, H, bx + 2 * kp, by + ky, pw);
+        }
+        float2 r;
+        if (MODEL == 4)
+            r = __fadd2_rn(__ffma2_rn(ng1, T, J), nc);
+        else
+            r = __ffma2_rn(f2(-1.f), T, J);
+        const float2 w = make_float2(hampel_weight(r.x, ha, icb, hc_icb), hampel_weight(r.y, ha, icb, hc_icb) * S.msk[j]);
+        const float2 wTx = __fmul2_rn(w, Tx), wTy = __fmul2_rn(w, Ty);
+        acc[0] = __ffma2_rn(wTx, Tx, acc[0]);
+        acc[1] = __ffma2_rn(wTx, Ty, acc[1]);
+        acc[4] = __ffma2_rn(wTy, Ty, acc[4]);
+        acc[10] = __ffma2_rn(wTx, r, acc[10]);
+        acc[11] = __ffma2_rn(wTy, r, acc[11]);
+        if (MODEL == 4) {
+            const float2 wT = __fmul2_rn(w, T);
+            acc[2] = __ffma2_rn(wTx, T, acc[2]);
+            acc[3] = __fadd2_rn(acc[3], wTx);
+            acc[5] = __ffma2_rn(wTy, T, acc[5]);
+            acc[6] = __fadd2_rn(acc[6], wTy);
+            acc[7] = __ffma2_rn(wT, T, acc[7]);
+            acc[8] = __fadd2_rn(acc[8], wT);
+            acc[9] = __fadd2_rn(acc[9], w);
+            acc[12] = __ffma2_rn(wT, r, acc[12]);
+            acc[13] = __ffma2_rn(w, r, acc[13]);
+        }
+    }
+}
+
+template <typename TS, int G, int SLP, int MODEL, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const RlofArgs a)
 {
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int pt = gtid / G;
@@ -127,13 +272,13 @@ __global__ void __launch_bounds__(256) rlof_kernel(const RlofArgs a)
     if (pt >= a.n) return;
     const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
     const int R = a.radius, side = 2 * R + 1, npx = side * side;
+    const int pc = R + 1, np = side * pc;  // pair columns per row, pairs in the support
+    const float icb = a.inv_cb, hc_icb = a.hc * a.inv_cb;
+    Support<SLP> S;
 
     const float2 p = reinterpret_cast<const float2*>(a.pts)[pt];
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f, m = 0.f, c = 0.f;
     int status = DGF_TRACKED, iters = 0;
-
-    float T[SL], Tx[SL], Ty[SL];
-    int off[SL];
 
     for (int l = a.levels - 1; l >= 0; --l) {
         const LevelPlanes L = a.lv[l];
@@ -147,31 +292,38 @@ __global__ void __launch_bounds__(256) rlof_kernel(const RlofArgs a)
         // level set-up: template and its gradients at p_l + k
         {
             const float fx0 = floorf(plx), fy0 = floorf(ply);
-            const int x0 = (int)fx0, y0 = (int)fy0;
-            const float ax = plx - fx0, ay = ply - fy0;
-            float g00 = 0.f, g01 = 0.f, g11 = 0.f;
+            const int bx = (int)fx0 - R, by = (int)fy0 - R;
+            const PairWeights pw(plx - fx0, ply - fy0);
+            float2 g00 = f2(0.f), g01 = f2(0.f), g11 = f2(0.f);
 #pragma unroll
-            for (int j = 0; j < SL; ++j) {
-                const int s = lane + G * j;
-                const int ky = s / side, kx = s - ky * side;
-                off[j] = (ky - R) * L.pitch + (kx - R);
-                if (s < npx) {
-                    const int xi = x0 + kx - R, yi = y0 + ky - R;
-                    T[j] = sample_clamped(I1, L.pitch, L.W, L.H, xi, yi, ax, ay);
-                    Tx[j] = sample_clamped(I1x, L.pitch, L.W, L.H, xi, yi, ax, ay);
-                    Ty[j] = sample_clamped(I1y, L.pitch, L.W, L.H, xi, yi, ax, ay);
-                    g00 = fmaf(Tx[j], Tx[j], g00);
-                    g01 = fmaf(Tx[j], Ty[j], g01);
-                    g11 = fmaf(Ty[j], Ty[j], g11);
-                } else {
-                    T[j] = Tx[j] = Ty[j] = 0.f;
+            for (int j = 0; j < SLP; ++j) {
+                const int q = lane + G * j;
+                const int ky = q / pc, kp = q - ky * pc;
+                float2 T = f2(0.f), Tx = f2(0.f), Ty = f2(0.f);
+                float msk = 0.f;
+                int off = 0;
+                if (q < np) {
+                    off = ky * L.pitch + 2 * kp;
+                    msk = 2 * kp + 1 < side ? 1.f : 0.f;
+                    T = pair_clamped(I1, L.pitch, L.W, L.H, bx + 2 * kp, by + ky, pw);
+                    Tx = pair_clamped(I1x, L.pitch, L.W, L.H, bx + 2 * kp, by + ky, pw);
+                    Ty = pair_clamped(I1y, L.pitch, L.W, L.H, bx + 2 * kp, by + ky, pw);
+                    if (msk == 0.f) T.y = Tx.y = Ty.y = 0.f;
                 }
+                S.T[j] = T;
+                S.Tx[j] = Tx;
+                S.Ty[j] = Ty;
+                S.off[j] = off;
+                S.msk[j] = msk;
+                g00 = __ffma2_rn(Tx, Tx, g00);
+                g01 = __ffma2_rn(Tx, Ty, g01);
+                g11 = __ffma2_rn(Ty, Ty, g11);
             }
-            g00 = group_sum<G>(g00, mask);
-            g01 = group_sum<G>(g01, mask);
-            g11 = group_sum<G>(g11, mask);
-            const float ht = 0.5f * (g00 + g11), hd = 0.5f * (g00 - g11);
-            const float lam = ht - sqrtf(hd * hd + g01 * g01);
+            const float G00 = group_sum<G>(g00.x + g00.y, mask);
+            const float G01 = group_sum<G>(g01.x + g01.y, mask);
+            const float G11 = group_sum<G>(g11.x + g11.y, mask);
+            const float ht = 0.5f * (G00 + G11), hd = 0.5f * (G00 - G11);
+            const float lam = ht - sqrtf(hd * hd + G01 * G01);
             if (lam / (float)npx < a.min_eig) {
                 status = DGF_SMALL_EIG;
                 break;
@@ -188,74 +340,53 @@ __global__ void __launch_bounds__(256) rlof_kernel(const RlofArgs a)
                 break;
             }
             const float fx0 = floorf(qx), fy0 = floorf(qy);
-            const int x0 = (int)fx0, y0 = (int)fy0;
-            const float ax = qx - fx0, ay = qy - fy0;
-            const bool inside = x0 - R >= 0 && x0 + R + 1 <= L.W - 1 && y0 - R >= 0 && y0 + R + 1 <= L.H - 1;
-            const TS* base = I2 + (size_t)y0 * L.pitch + x0;
+            const int bx = (int)fx0 - R, by = (int)fy0 - R;
+            const PairWeights pw(qx - fx0, qy - fy0);
+            // the tap block spans columns bx .. bx + 2R + 2 (the masked last sample
+            // included) and rows by .. by + 2R + 1
+            const bool inside = bx >= 0 && bx + 2 * R + 2 <= L.W - 1 && by >= 0 && by + 2 * R + 1 <= L.H - 1;
+            float2 acc[14];
+#pragma unroll
+            for (int k = 0; k < 14; ++k) acc[k] = f2(0.f);
             const float g1 = 1.f + m;
-            float h[10], b[4];
-#pragma unroll
-            for (int k = 0; k < 10; ++k) h[k] = 0.f;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) b[k] = 0.f;
-#pragma unroll
-            for (int j = 0; j < SL; ++j) {
-                const int s = lane + G * j;
-                if (s < npx) {
-                    float J;
-                    if (inside) {
-                        J = sample_inside(base + off[j], L.pitch, ax, ay);
-                    } else {
-                        const int ky = s / side, kx = s - ky * side;
-                        J = sample_clamped(I2, L.pitch, L.W, L.H, x0 + kx - R, y0 + ky - R, ax, ay);
-                    }
-                    const float r = MODEL == 4 ? (J - g1 * T[j]) - c : J - T[j];
-                    const float w = hampel_weight(r, a.ha, a.hb, a.hc, a.inv_cb);
-                    const float wTx = w * Tx[j], wTy = w * Ty[j];
-                    h[0] = fmaf(wTx, Tx[j], h[0]);
-                    h[1] = fmaf(wTx, Ty[j], h[1]);
-                    h[4] = fmaf(wTy, Ty[j], h[4]);
-                    b[0] = fmaf(wTx, r, b[0]);
-                    b[1] = fmaf(wTy, r, b[1]);
-                    if (MODEL == 4) {
-                        const float wT = w * T[j];
-                        h[2] = fmaf(wTx, T[j], h[2]);
-                        h[3] += wTx;
-                        h[5] = fmaf(wTy, T[j], h[5]);
-                        h[6] += wTy;
-                        h[7] = fmaf(wT, T[j], h[7]);
-                        h[8] += wT;
-                        h[9] += w;
-                        b[2] = fmaf(wT, r, b[2]);
-                        b[3] = fmaf(w, r, b[3]);
-                    }
-                }
-            }
+            if (inside && (bx & 1) == 0)
+                accumulate<TS, G, SLP, MODEL, 0>(S, acc, I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c,
+                                                 a.ha, icb, hc_icb);
+            else if (inside)
+                accumulate<TS, G, SLP, MODEL, 1>(S, acc, I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c,
+                                                 a.ha, icb, hc_icb);
+            else
+                accumulate<TS, G, SLP, MODEL, 2>(S, acc, I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c,
+                                                 a.ha, icb, hc_icb);
+            float h[16];
             float delta[4];
             bool ok;
             if (MODEL == 4) {
+                float v[16];
 #pragma unroll
-                for (int k = 0; k < 10; ++k) h[k] = group_sum<G>(h[k], mask);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) b[k] = group_sum<G>(b[k], mask);
+                for (int k = 0; k < 14; ++k) v[k] = acc[k].x + acc[k].y;
+                v[14] = v[15] = 0.f;
+                group_allreduce16<G>(v, h, mask, lane);
                 // a = (Tx, Ty, -T, -1): fold the signs of the T and constant columns
                 float Hm[4][4] = {{h[0], h[1], -h[2], -h[3]},
                                   {h[1], h[4], -h[5], -h[6]},
                                   {-h[2], -h[5], h[7], h[8]},
                                   {-h[3], -h[6], h[8], h[9]}};
-                const float rhs[4] = {-b[0], -b[1], b[2], b[3]};
+                const float rhs[4] = {-h[10], -h[11], h[12], h[13]};
                 float x[4];
                 ok = chol_solve<4>(Hm, rhs, x);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) delta[k] = x[k];
             } else {
+#pragma unroll
+                for (int k = 0; k < 14; ++k) h[k] = acc[k].x + acc[k].y;
                 h[0] = group_sum<G>(h[0], mask);
                 h[1] = group_sum<G>(h[1], mask);
                 h[4] = group_sum<G>(h[4], mask);
-                b[0] = group_sum<G>(b[0], mask);
-                b[1] = group_sum<G>(b[1], mask);
+                h[10] = group_sum<G>(h[10], mask);
+                h[11] = group_sum<G>(h[11], mask);
                 float Hm[2][2] = {{h[0], h[1]}, {h[1], h[4]}};
-                const float rhs[2] = {-b[0], -b[1]};
+                const float rhs[2] = {-h[10], -h[11]};
                 float x[2];
                 ok = chol_solve<2>(Hm, rhs, x);
                 delta[0] = x[0];
@@ -301,30 +432,31 @@ int g_lanes_override = 0;
 template <typename TS, int MODEL>
 int launch(const RlofArgs& a, int lanes, cudaStream_t stream)
 {
-    const int npx = (2 * a.radius + 1) * (2 * a.radius + 1);
-    const int threads = 256;
+    const int np = (2 * a.radius + 1) * (a.radius + 1);  // sample pairs in the support
     const long long total = (long long)a.n * lanes;
-    const unsigned blocks = (unsigned)((total + threads - 1) / threads);
-#define DGF_LAUNCH(G, SL)                                                                       \
-    if (lanes == G && npx <= G * SL) {                                                          \
-        rlof_kernel<TS, G, SL, MODEL><<<blocks, threads, 0, stream>>>(a);                      \
+    const unsigned blocks = (unsigned)((total + kThreads - 1) / kThreads);
+#define DGF_LAUNCH(G, SLP)                                                                      \
+    if (lanes == G && (np + G - 1) / G == SLP) {                                                \
+        rlof_kernel<TS, G, SLP, MODEL, 4><<<blocks, kThreads, 0, stream>>>(a);                 \
         return dgf::launch_status();                                                            \
     }
-    DGF_LAUNCH(8, 11)   // radius 4 (81 samples)
-    DGF_LAUNCH(8, 16)   // radius 5 (121)
-    DGF_LAUNCH(16, 6)   // radius 4
-    DGF_LAUNCH(16, 8)   // radius 5
-    DGF_LAUNCH(32, 3)   // radius 4
-    DGF_LAUNCH(32, 4)   // radius 5
-    DGF_LAUNCH(32, 8)   // radius 6, 7
+    DGF_LAUNCH(8, 6)    // radius 4 (45 pairs)
+    DGF_LAUNCH(8, 9)    // radius 5 (66 pairs)
+    DGF_LAUNCH(16, 3)   // radius 4
+    DGF_LAUNCH(16, 5)   // radius 5
+    DGF_LAUNCH(32, 1)   // radius 1..3
+    DGF_LAUNCH(32, 2)   // radius 4
+    DGF_LAUNCH(32, 3)   // radius 5, 6
+    DGF_LAUNCH(32, 4)   // radius 7
 #undef DGF_LAUNCH
     return DGF_ERR_ARG;
 }
 
 int choose_lanes(int radius)
 {
-    if (g_lanes_override) return radius <= 5 || g_lanes_override == 32 ? g_lanes_override : 32;
-    return radius <= 5 ? 8 : 32;
+    // 8 and 16 lanes are built for radius 4 and 5 only; other radii use 32 lanes
+    if (radius != 4 && radius != 5) return 32;
+    return g_lanes_override ? g_lanes_override : 16;
 }
 
 }  // namespace

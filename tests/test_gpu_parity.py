@@ -161,18 +161,20 @@ def test_track_parity_workloads(dgf, config, model, lanes):
         assert np.abs(lg[ok, 1] - lo[ok, 1]).max() < 0.5
 
 
-@pytest.mark.parametrize("radius,levels,n", [(1, 1, 1), (2, 2, 33), (3, 3, 257), (6, 4, 100),
-                                             (7, 2, 65), (4, 6, 500), (5, 5, 3)])
-def test_track_parity_shapes(dgf, radius, levels, n):
-    """Ragged point counts (group and block tails), every radius path, 1..6 levels."""
+@pytest.mark.parametrize("radius,levels,n,model", [(1, 1, 1, 2), (1, 2, 200, 2), (2, 2, 33, 4), (3, 3, 257, 4),
+                                                   (6, 4, 100, 4), (7, 2, 65, 4), (4, 6, 500, 4), (5, 5, 3, 4)])
+def test_track_parity_shapes(dgf, radius, levels, n, model):
+    """Ragged point counts (group and block tails), every radius path, 1..6 levels,
+    on a noise-free translation pair (supports this small make the 4-unknown
+    problem ill-posed under noise, where FP32 and FP64 trajectories part ways)."""
     W, H = 640, 480
-    p = synth.make_translation_pair(W, H, t=(2.5, -1.75), seed=radius * 10 + levels)
+    p = synth.make_translation_pair(W, H, t=(2.5, -1.75), seed=radius * 10 + levels, noise_sigma=0.0)
     rng = np.random.default_rng(n)
     pts = np.stack([rng.uniform(0, W - 1, n), rng.uniform(0, H - 1, n)], 1)
-    prm = oracle.RlofParams(levels=levels, radius=radius, model=4)
+    prm = oracle.RlofParams(levels=levels, radius=radius, model=model)
     (fg, sg, _, _), (fo, so, _, _) = run_both(dgf, p.I1, p.I2, pts, prm)
     agree, both, e = compare_tracks(fg, sg, fo, so)
-    assert np.sum(sg != so) <= max(1, 0.02 * n)
+    assert np.sum(sg != so) <= max(1, 0.01 * n)
     assert np.sum(e[both] > TOL_FLOW) <= max(1, 0.01 * both.sum())
 
 
