@@ -36,6 +36,7 @@ WORKLOAD = dict(workload="driving-scene pair 1242x375: DeGraF w=7 step=3 (50676 
 # FP32 lanes x 2 flop x SMs at the maximum SM clock (GB300: 152 SMs, 128 FP32 lanes each)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
+HBM_PEAK_GBS = 6786.9  # measured STREAM-style copy on the GB300s
 
 
 def flops_model(radius: int, model: int):
@@ -114,6 +115,53 @@ def kernel_traffic():
         return rec["dram_bytes_per_launch"] if rec.get("rlof_cu_sha256") == digest else None
     except (OSError, ValueError, KeyError):
         return None
+
+
+def run_batched(dgf, torch, dev, reps: int = 10):
+    """The mixed-size batch workload: 64 pairs (640x480 .. 1280x720, step 2..6,
+    window 8, 3 levels, 9x9 support) through one rlof_track_many call replayed from
+    a CUDA graph; detection + pyramids are also timed alone (stages 1|2) for their
+    HBM roofline."""
+    specs = [(W, H, 8, st) for (W, H, st) in synth.make_batch_specs(64, 3000)]
+    frames = [synth.make_translation_pair(W, H, seed=3000 + i) for i, (W, H, _, _) in enumerate(specs)]
+    d1 = [torch.from_numpy(p.I1).to(dev) for p in frames]
+    d2 = [torch.from_numpy(p.I2).to(dev) for p in frames]
+    prm = dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)
+    bt = dgf.BatchTracker(specs, prm, dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(stages):
+        for _ in range(3):
+            bt.run(d1, d2, use_graph=True, stages=stages)
+        torch.cuda.synchronize(dev)
+        ms = []
+        for k in range(reps):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bt.run(d1, d2, use_graph=True, stages=stages)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.median(ms))
+
+    t_all = timed(7)
+    t_dp = timed(1 | 2)
+    npts = sum(bt.n)
+    # algorithmic bytes of detection + both pyramids: frame 1 read twice, frame 2
+    # once, key-points written, 3 FP32 planes of frame 1 and 1 of frame 2 per level
+    nbytes = 0
+    for (W, H, win, step), n in zip(specs, bt.n):
+        px = sum((W >> l) * (H >> l) for l in range(prm.levels))
+        nbytes += 3 * W * H + 8 * n + 4 * 4 * px
+    gbs = nbytes / (t_dp / 1e3) / 1e9
+    return {"workload": "64 mixed pairs 640x480..1280x720, step 2..6, window 8, 3 levels, 9x9, model 4, FP32, "
+                        "one rlof_track_many call replayed from a CUDA graph",
+            "pairs": 64, "points": npts, "ms_per_batch": t_all, "points_per_s": npts / (t_all / 1e3),
+            "pairs_per_s": 64 / (t_all / 1e3),
+            "detect_pyramid": {"ms": t_dp, "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
+                               "frac_of_measured_hbm": gbs / HBM_PEAK_GBS}}
 
 
 def cpu_baseline(pair, reps: int = 2):
@@ -280,6 +328,8 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
                         "d2h_bytes_per_step": n_pts * (8 + 8 + 1)},
                 "gpu_launches": 4 * args.steps,
                 "clocks": clocks.summary()}
+        if not args.no_batched:
+            line["batched"] = run_batched(dgf, torch, dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pair)
         print(json.dumps(line), flush=True)
@@ -294,6 +344,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-pair batch section")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per tracked point (0 = automatic)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

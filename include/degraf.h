@@ -185,6 +185,55 @@ int rlof_track(const void* pyr1, const void* pyr2, int W, int H, const float* pt
                const dgf_rlof_params* p, float* flow, uint8_t* status, uint8_t* iters,
                float* illum, cudaStream_t stream);
 
+/* ---- batched pipeline (Section 2 over many frame pairs) ------------------- */
+
+/*
+ * One frame pair of a batch: both frames, the DeGraF grid and the caller's output
+ * buffers (device). N = dgf_degraf_count(W, H, win, win, step) key-points.
+ */
+typedef struct {
+    const uint8_t* frame1; /* device, uint8 W x H, rows `pitch` bytes apart */
+    const uint8_t* frame2; /* device, same size and pitch */
+    int W, H, pitch;
+    int win, step;         /* square DeGraF window and grid step */
+    float* pts;            /* device out, float [N][2] key-points of frame 1 */
+    float* flow;           /* device out, float [N][2] */
+    uint8_t* status;       /* device out, uint8 [N] */
+    uint8_t* iters;        /* device out, nullable, uint8 [N] */
+} dgf_pair;
+
+/*
+ * Workspace bytes rlof_track_many needs for this batch (both pyramids of every
+ * pair), or 0 when an argument is invalid.
+ */
+size_t dgf_track_many_workspace(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p);
+
+/* stages of rlof_track_many */
+#define DGF_STAGE_DETECT 1
+#define DGF_STAGE_PYRAMID 2
+#define DGF_STAGE_TRACK 4
+#define DGF_STAGE_ALL 7
+
+/*
+ * DeGraF detection, both pyramids and RLOF tracking of every pair (the same
+ * definitions as degraf_detect, pyramid_build and rlof_track, one parameter set
+ * for all pairs). Per chunk of 64 pairs: one detection launch per distinct window
+ * size, one pyramid launch for all frames and one tracking launch over every
+ * point of the chunk. pairs: host array of n_pairs descriptors (read during the
+ * call only). stages: DGF_STAGE_ALL, or a subset (tracking reads the points and
+ * pyramids an earlier call left in the same outputs and workspace).
+ * workspace: device, 256-byte aligned, ws_bytes >= dgf_track_many_workspace();
+ * owned by the caller and in use until the work completes on `stream`.
+ * use_graph = 1: the launch sequence is captured into a CUDA graph on first use
+ * of a given argument set (descriptors, parameters, workspace, device, lanes
+ * setting, stages) and the instantiated graph is replayed on later calls with the same
+ * set; while `stream` is already being captured by the caller, plain launches are
+ * enqueued instead. Returns DGF_ERR_WORKSPACE for a short workspace and the
+ * rlof_track codes otherwise.
+ */
+int rlof_track_many(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p, void* workspace,
+                    size_t ws_bytes, int stages, int use_graph, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

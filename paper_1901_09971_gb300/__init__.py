@@ -7,6 +7,6 @@ from ._abi import (  # noqa: F401
     DegrafError, F16, F32, MAXITER, OOB, SINGULAR, SMALL_EIG, TRACKED, load,
 )
 from .api import (  # noqa: F401
-    PairTracker, RlofParams, build_pyramid, degraf_count, detect, pyramid_bytes, pyramid_layout,
+    BatchTracker, PairTracker, RlofParams, build_pyramid, degraf_count, detect, pyramid_bytes, pyramid_layout,
     pyramid_planes, set_lanes, track, track_pair, version,
 )

@@ -19,6 +19,7 @@ DGF_ERR_DEVICE = -6
 
 TRACKED, OOB, SMALL_EIG, SINGULAR, MAXITER = 0, 1, 2, 3, 4
 F32, F16 = 0, 1
+STAGE_DETECT, STAGE_PYRAMID, STAGE_TRACK, STAGE_ALL = 1, 2, 4, 7
 MAX_LEVELS = 6
 MAX_RADIUS = 7
 RLOF_PARAMS_VERSION = 1
@@ -27,6 +28,7 @@ RLOF_PARAMS_VERSION = 1
 EXPORTS = (
     "dgf_strerror", "dgf_version", "dgf_degraf_count", "degraf_detect", "dgf_pyramid_layout_get",
     "dgf_pyramid_bytes", "pyramid_build", "dgf_rlof_params_default", "dgf_rlof_set_lanes", "rlof_track",
+    "dgf_track_many_workspace", "rlof_track_many",
 )
 
 
@@ -43,6 +45,13 @@ class RlofParamsC(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("model", ctypes.c_int), ("storage", ctypes.c_int),
                 ("eps", ctypes.c_float), ("hampel_a", ctypes.c_float), ("hampel_b", ctypes.c_float),
                 ("hampel_c", ctypes.c_float), ("min_eig", ctypes.c_float)]
+
+
+class PairC(ctypes.Structure):
+    _fields_ = [("frame1", ctypes.c_void_p), ("frame2", ctypes.c_void_p), ("W", ctypes.c_int),
+                ("H", ctypes.c_int), ("pitch", ctypes.c_int), ("win", ctypes.c_int), ("step", ctypes.c_int),
+                ("pts", ctypes.c_void_p), ("flow", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("iters", ctypes.c_void_p)]
 
 
 class DegrafError(RuntimeError):
@@ -81,6 +90,10 @@ def load(build_if_missing: bool = True):
     L.dgf_rlof_set_lanes.argtypes, L.dgf_rlof_set_lanes.restype = [I], I
     L.rlof_track.argtypes = [P, P, I, I, P, I, ctypes.POINTER(RlofParamsC), P, P, P, P, P]
     L.rlof_track.restype = I
+    L.dgf_track_many_workspace.argtypes = [ctypes.POINTER(PairC), I, ctypes.POINTER(RlofParamsC)]
+    L.dgf_track_many_workspace.restype = Z
+    L.rlof_track_many.argtypes = [ctypes.POINTER(PairC), I, ctypes.POINTER(RlofParamsC), P, Z, I, I, P]
+    L.rlof_track_many.restype = I
     _lib = L
     return L
 

@@ -182,6 +182,57 @@ class PairTracker:
         return self.pts, self.flow, self.status, self.iters
 
 
+class BatchTracker:
+    """Batched DeGraF + pyramids + RLOF over frame pairs of mixed sizes and steps.
+
+    ``specs`` is a list of (W, H, win, step). Outputs (points, flow, status,
+    iterations) and the workspace are allocated once; ``run`` takes lists of
+    uint8 frames (device tensors of the spec sizes) and enqueues one
+    rlof_track_many call (optionally replayed from a captured CUDA graph).
+    """
+
+    def __init__(self, specs, params: RlofParams, device: torch.device | str = "cuda"):
+        self.specs = [tuple(int(v) for v in sp) for sp in specs]
+        self.params = params
+        self.device = torch.device(device)
+        self.n = [degraf_count(W, H, win, step) for (W, H, win, step) in self.specs]
+        dev = self.device
+        self.pts = [torch.empty((n, 2), dtype=torch.float32, device=dev) for n in self.n]
+        self.flow = [torch.empty((n, 2), dtype=torch.float32, device=dev) for n in self.n]
+        self.status = [torch.empty(n, dtype=torch.uint8, device=dev) for n in self.n]
+        self.iters = [torch.empty(n, dtype=torch.uint8, device=dev) for n in self.n]
+        self._prm = params.c()
+        probe = self._descriptors([None] * len(self.specs), [None] * len(self.specs), probe=True)
+        nbytes = int(load().dgf_track_many_workspace(probe, len(self.specs), ctypes.byref(self._prm)))
+        if nbytes == 0:
+            raise _abi.DegrafError("dgf_track_many_workspace", _abi.DGF_ERR_ARG, "invalid batch")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+
+    def _descriptors(self, frames1, frames2, probe=False):
+        arr = (_abi.PairC * len(self.specs))()
+        for i, (W, H, win, step) in enumerate(self.specs):
+            f1, f2 = frames1[i], frames2[i]
+            if probe:
+                p1 = p2 = 1 << 20  # placeholders: the size query dereferences nothing
+                pitch = W
+            else:
+                if f1.shape != (H, W) or f2.shape != (H, W) or f1.stride(0) != f2.stride(0):
+                    raise ValueError(f"pair {i}: frames must be {H}x{W} with equal pitch")
+                _frame(f1)
+                _frame(f2)
+                p1, p2, pitch = f1.data_ptr(), f2.data_ptr(), f1.stride(0)
+            arr[i] = _abi.PairC(p1, p2, W, H, pitch, win, step, self.pts[i].data_ptr(), self.flow[i].data_ptr(),
+                                self.status[i].data_ptr(), self.iters[i].data_ptr())
+        return arr
+
+    def run(self, frames1, frames2, use_graph: bool = True, stages: int = _abi.STAGE_ALL):
+        arr = self._descriptors(frames1, frames2)
+        check("rlof_track_many", load().rlof_track_many(arr, len(self.specs), ctypes.byref(self._prm),
+                                                        _ptr(self.workspace), self.workspace.numel(), int(stages),
+                                                        int(use_graph), _stream()))
+        return self.pts, self.flow, self.status, self.iters
+
+
 def track_pair(frame1, frame2, win: int, step: int, params: RlofParams, device="cuda"):
     """End-to-end call on host or device frames: returns host (pts, flow, status).
 

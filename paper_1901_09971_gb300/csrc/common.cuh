@@ -1,8 +1,10 @@
-// Shared helpers of the CUDA library: the public ABI, storage-type loads and
-// stores, and launch-error mapping.
+// Shared helpers of the CUDA library: the public ABI, the pyramid geometry used by
+// host and device code alike, storage-type loads and stores, and launch-error
+// mapping.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "degraf.h"
@@ -14,6 +16,45 @@ __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
 __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+
+__host__ __device__ __forceinline__ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Geometry of one pyramid level inside a pyramid buffer (see dgf_pyramid_layout):
+// planes I_0..I_{L-1}, then Ix_0..Ix_{L-1}, Iy_0..Iy_{L-1}; each plane starts on a
+// 256-byte boundary, rows are padded to 128 bytes.
+struct LevelGeom {
+    int W, H, pitch;            // size and row pitch (elements)
+    size_t off_I, off_Ix, off_Iy;  // byte offsets (gradient offsets valid when built with them)
+    size_t bytes_all, bytes_intensity;  // buffer size with / without gradient planes
+};
+
+// Level l of a W x H frame with `levels` levels of element size es (4 or 2).
+// Returns false when a level up to `levels - 1` is empty.
+__host__ __device__ inline bool level_geom(int W, int H, int levels, int es, int l, LevelGeom* g)
+{
+    size_t pre = 0, tot = 0;
+    int w = W, h = H;
+    for (int k = 0; k < levels; ++k) {
+        if (w < 1 || h < 1) return false;
+        const int pitch = (int)round_up((size_t)w, (size_t)(128 / es));
+        const size_t plane = round_up((size_t)pitch * h * es, 256);
+        if (k == l) {
+            g->W = w;
+            g->H = h;
+            g->pitch = pitch;
+            pre = tot;
+        }
+        tot += plane;
+        w /= 2;
+        h /= 2;
+    }
+    g->off_I = pre;
+    g->off_Ix = tot + pre;
+    g->off_Iy = 2 * tot + pre;
+    g->bytes_all = 3 * tot;
+    g->bytes_intensity = tot;
+    return true;
+}
 
 inline int launch_status() {
     cudaError_t e = cudaGetLastError();

@@ -1,71 +1,86 @@
 // DeGraF key-point detection (arXiv 1901.09971, Section 2, Eq. 1-2).
 //
-// One thread per window. A CTA covers 32 x BY windows; when they overlap
-// (step < window) the union of their pixels is staged once in shared memory,
-// otherwise each thread reads its window straight from global memory. The window
+// One thread per window. A CTA covers 32 x BY windows of one frame (a launch may
+// cover the frames of a whole batch); when they overlap (step < window) the union
+// of their pixels is staged once in shared memory, otherwise each thread reads its
+// window straight from global memory. The window
 // sums S = sum I, X = sum j I, Y = sum i I and the maximum m are exact int32; the
 // negative-centroid sums follow from them in closed form,
 //   S_neg = n (1+m) - S,  X_neg = (1+m) h w (w-1)/2 - X,  Y_neg = (1+m) w h (h-1)/2 - Y,
 // and the selected centroid is formed in FP64 and rounded once to FP32, so every
 // coordinate is the exactly rounded value of Eq. 1 or Eq. 2 plus the window origin.
 #include "common.cuh"
+#include "batch.cuh"
 
 namespace {
 
-constexpr int kBX = 32;
+constexpr int kBX = 32;       // windows per CTA along x
+constexpr int kSmemMax = 48 * 1024;
 
-struct DetectArgs {
-    const uint8_t* img;
-    int W, H, pitch, ww, wh, step, nu, nv;
-    float* pts;
-    int32_t* sums;
-};
+long long grid_count(int n, int win, int step) { return n < win ? 0 : (long long)((n - win) / step) + 1; }
 
-__device__ __forceinline__ void emit(const DetectArgs& a, int u, int v, int S, int X, int Y, int m)
+}  // namespace
+
+namespace dgf {
+
+__device__ __forceinline__ void emit(const DetectJob& J, int ww, int wh, int u, int v, int S, int X, int Y, int m)
 {
-    const int n = a.ww * a.wh;
+    const int n = ww * wh;
     const int m1 = m + 1;
     const int Sn = n * m1 - S;
     double cx, cy;
     if (Sn > S) {  // Eq. 2 centroid: the larger weight sum wins, ties keep C_pos
-        const int Xn = m1 * (a.wh * (a.ww * (a.ww - 1) / 2)) - X;
-        const int Yn = m1 * (a.ww * (a.wh * (a.wh - 1) / 2)) - Y;
+        const int Xn = m1 * (wh * (ww * (ww - 1) / 2)) - X;
+        const int Yn = m1 * (ww * (wh * (wh - 1) / 2)) - Y;
         cx = (double)Xn / (double)Sn;
         cy = (double)Yn / (double)Sn;
     } else {  // Eq. 1 centroid
         cx = (double)X / (double)S;
         cy = (double)Y / (double)S;
     }
-    const long long k = (long long)v * a.nu + u;
-    const float2 p = make_float2((float)((double)(u * a.step) + cx), (float)((double)(v * a.step) + cy));
-    reinterpret_cast<float2*>(a.pts)[k] = p;
-    if (a.sums) reinterpret_cast<int4*>(a.sums)[k] = make_int4(S, X, Y, m);
+    const long long k = (long long)v * J.nu + u;
+    reinterpret_cast<float2*>(J.pts)[k] =
+        make_float2((float)((double)(u * J.step) + cx), (float)((double)(v * J.step) + cy));
+    if (J.sums) reinterpret_cast<int4*>(J.sums)[k] = make_int4(S, X, Y, m);
 }
 
-template <bool kStaged>
-__global__ void __launch_bounds__(256) degraf_detect_kernel(DetectArgs a, int tile_w, int tile_h)
+// One thread per window; CTAs of all frames of the batch in one grid.
+__global__ void __launch_bounds__(256) degraf_detect_kernel(const __grid_constant__ DetectBatch a)
 {
     extern __shared__ uint8_t tile[];
-    const int u0 = blockIdx.x * kBX, v0 = blockIdx.y * blockDim.y;
-    const int x0 = u0 * a.step, y0 = v0 * a.step;
-    if (kStaged) {
-        const int tw = min(tile_w, a.W - x0), th = min(tile_h, a.H - y0);
+    int f = 0;
+    for (int lo = 0, hi = a.n_jobs - 1; lo <= hi;) {
+        const int mid = (lo + hi) >> 1;
+        if (a.jobs[mid].cta_begin <= (int)blockIdx.x) {
+            f = mid;
+            lo = mid + 1;
+        } else {
+            hi = mid - 1;
+        }
+    }
+    const DetectJob& J = a.jobs[f];
+    const int t = blockIdx.x - J.cta_begin;
+    const int u0 = (t % J.tiles_x) * kBX, v0 = (t / J.tiles_x) * blockDim.y;
+    const int x0 = u0 * J.step, y0 = v0 * J.step;
+    const int tile_w = (kBX - 1) * J.step + a.ww, tile_h = ((int)blockDim.y - 1) * J.step + a.wh;
+    if (a.staged) {
+        const int tw = min(tile_w, J.W - x0), th = min(tile_h, J.H - y0);
         for (int r = threadIdx.y; r < th; r += blockDim.y) {
-            const uint8_t* src = a.img + (size_t)(y0 + r) * a.pitch + x0;
+            const uint8_t* src = J.img + (size_t)(y0 + r) * J.pitch + x0;
             for (int c = threadIdx.x; c < tw; c += blockDim.x) tile[r * tile_w + c] = src[c];
         }
         __syncthreads();
     }
     const int u = u0 + threadIdx.x, v = v0 + threadIdx.y;
-    if (u >= a.nu || v >= a.nv) return;
+    if (u >= J.nu || v >= J.nv) return;
     const uint8_t* w0;
     int rstride;
-    if (kStaged) {
-        w0 = tile + threadIdx.y * a.step * tile_w + threadIdx.x * a.step;
+    if (a.staged) {
+        w0 = tile + threadIdx.y * J.step * tile_w + threadIdx.x * J.step;
         rstride = tile_w;
     } else {
-        w0 = a.img + (size_t)(v * a.step) * a.pitch + u * a.step;
-        rstride = a.pitch;
+        w0 = J.img + (size_t)(v * J.step) * J.pitch + u * J.step;
+        rstride = J.pitch;
     }
     int S = 0, X = 0, Y = 0, m = 0;
     for (int i = 0; i < a.wh; ++i) {
@@ -81,12 +96,45 @@ __global__ void __launch_bounds__(256) degraf_detect_kernel(DetectArgs a, int ti
         X += rx;
         Y += i * rs;
     }
-    emit(a, u, v, S, X, Y, m);
+    emit(J, a.ww, a.wh, u, v, S, X, Y, m);
 }
 
-long long grid_count(int n, int win, int step) { return n < win ? 0 : (long long)((n - win) / step) + 1; }
+// Chooses the CTA shape (32 x by windows, staged through shared memory when the
+// windows overlap and every frame's tile fits), fills the CTA prefix counts and
+// launches detection for every frame of the batch.
+int launch_detect(DetectBatch& a, cudaStream_t stream)
+{
+    int max_step = 1;
+    bool overlap = true;
+    for (int f = 0; f < a.n_jobs; ++f) {
+        max_step = a.jobs[f].step > max_step ? a.jobs[f].step : max_step;
+        overlap = overlap && (a.jobs[f].step < a.ww || a.jobs[f].step < a.wh);
+    }
+    int by = 8;
+    const int tile_w = (kBX - 1) * max_step + a.ww;
+    int tile_h = (by - 1) * max_step + a.wh;
+    while (by > 1 && tile_w * tile_h > kSmemMax) {
+        by /= 2;
+        tile_h = (by - 1) * max_step + a.wh;
+    }
+    a.by = by;
+    a.staged = overlap && tile_w * tile_h <= kSmemMax;
+    a.tile_w = tile_w;
+    a.tile_h = tile_h;
+    long long ctas = 0;
+    for (int f = 0; f < a.n_jobs; ++f) {
+        DetectJob& J = a.jobs[f];
+        J.tiles_x = (J.nu + kBX - 1) / kBX;
+        J.cta_begin = (int)ctas;
+        ctas += (long long)J.tiles_x * ((J.nv + by - 1) / by);
+    }
+    if (ctas == 0) return DGF_OK;
+    if (ctas > 0x7fffffffLL) return DGF_ERR_ARG;
+    degraf_detect_kernel<<<(unsigned)ctas, dim3(kBX, by), a.staged ? (size_t)tile_w * tile_h : 0, stream>>>(a);
+    return launch_status();
+}
 
-}  // namespace
+}  // namespace dgf
 
 extern "C" long long dgf_degraf_count(int W, int H, int win_w, int win_h, int step)
 {
@@ -102,25 +150,20 @@ extern "C" int degraf_detect(const uint8_t* img, int W, int H, int pitch, int wi
     const long long n = dgf_degraf_count(W, H, win_w, win_h, step);
     if (n < 0 || !img || pitch < W) return DGF_ERR_ARG;
     if (n == 0) return DGF_OK;
-    if (!pts || !dgf::aligned(pts, 8) || (sums && !dgf::aligned(sums, 16))) return DGF_ERR_ARG;
-    DetectArgs a{img, W, H, pitch, win_w, win_h, step, (int)grid_count(W, win_w, step),
-                 (int)grid_count(H, win_h, step), pts, sums};
-    const bool overlap = step < win_w || step < win_h;
-    int by = 8;
-    int tile_w = (kBX - 1) * step + win_w;
-    int tile_h = (by - 1) * step + win_h;
-    const int kSmemMax = 48 * 1024;
-    while (by > 1 && tile_w * tile_h > kSmemMax) {
-        by /= 2;
-        tile_h = (by - 1) * step + win_h;
-    }
-    const bool staged = overlap && tile_w * tile_h <= kSmemMax;
-    dim3 block(kBX, by);
-    dim3 grid((a.nu + kBX - 1) / kBX, (a.nv + by - 1) / by);
-    if (grid.y > 65535) return DGF_ERR_ARG;
-    if (staged)
-        degraf_detect_kernel<true><<<grid, block, (size_t)tile_w * tile_h, stream>>>(a, tile_w, tile_h);
-    else
-        degraf_detect_kernel<false><<<grid, block, 0, stream>>>(a, 0, 0);
-    return dgf::launch_status();
+    if (!pts || !dgf::aligned(pts, 8) || (sums && !dgf::aligned(sums, 16)) || n > 0x7fffffffLL) return DGF_ERR_ARG;
+    dgf::DetectBatch a = {};
+    a.ww = win_w;
+    a.wh = win_h;
+    a.n_jobs = 1;
+    dgf::DetectJob& J = a.jobs[0];
+    J.img = img;
+    J.W = W;
+    J.H = H;
+    J.pitch = pitch;
+    J.step = step;
+    J.nu = (int)grid_count(W, win_w, step);
+    J.nv = (int)grid_count(H, win_h, step);
+    J.pts = pts;
+    J.sums = sums;
+    return dgf::launch_detect(a, stream);
 }

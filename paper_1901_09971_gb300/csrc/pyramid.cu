@@ -13,45 +13,65 @@
 // and writes I (and Ix, Iy) with coalesced rows. FP16 storage rounds each exact
 // value once.
 #include "common.cuh"
+#include "batch.cuh"
 
 namespace {
-
-struct LevelDesc {
-    int W, H, pitch;  // level size and row pitch (elements)
-    int tw, th;       // tile size (level pixels)
-    int tiles_x;      // tiles per row
-    int cta_begin;    // first CTA of this level in the flattened grid
-    size_t off_I, off_Ix, off_Iy;
-};
-
-struct PyrArgs {
-    const uint8_t* img;
-    int W, H, pitch, levels, with_grad;
-    char* base;
-    LevelDesc lv[DGF_MAX_LEVELS];
-    int cta_end;
-};
 
 constexpr int kThreads = 256;
 constexpr int kSmemBytes = 40 * 1024;
 
-int tile_w(int l) { return 64 >> (l < 4 ? l : 4); }
-int tile_h(int l) { return l == 0 ? 16 : (l == 1 ? 8 : 4); }
+__host__ __device__ inline int tile_w(int l) { return 64 >> (l < 4 ? l : 4); }
+__host__ __device__ inline int tile_h(int l) { return l == 0 ? 16 : (l == 1 ? 8 : 4); }
 
+// CTAs of one frame's pyramid: coarsest level first (those CTAs do the most work).
+__host__ __device__ inline int level_ctas(int W, int H, int l)
+{
+    const int w = W >> l, h = H >> l;
+    return ((w + tile_w(l) - 1) / tile_w(l)) * ((h + tile_h(l) - 1) / tile_h(l));
+}
+
+__host__ __device__ inline int frame_ctas(int W, int H, int levels)
+{
+    int n = 0;
+    for (int l = 0; l < levels; ++l) n += level_ctas(W, H, l);
+    return n;
+}
+
+}  // namespace
+
+namespace dgf {
+
+// One launch builds every level of up to kMaxFrames pyramids; CTAs are assigned
+// frame by frame (cta_begin is the prefix count).
 template <typename TS>
-__global__ void __launch_bounds__(kThreads) pyramid_kernel(PyrArgs a)
+__global__ void __launch_bounds__(kThreads) pyramid_kernel(const __grid_constant__ PyrBatch a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    // CTAs are ordered coarsest level first (they do the most work per CTA)
-    int l = a.levels - 1;
-    for (int k = 0; k < a.levels; ++k)
-        if ((int)blockIdx.x >= a.lv[k].cta_begin) { l = k; break; }
-    const LevelDesc& d = a.lv[l];
-    const int t = blockIdx.x - d.cta_begin;
-    const int tx0 = (t % d.tiles_x) * d.tw, ty0 = (t / d.tiles_x) * d.th;
+    int f = 0;  // frame of this CTA (binary search over the prefix counts)
+    for (int lo = 0, hi = a.n_frames - 1; lo <= hi;) {
+        const int mid = (lo + hi) >> 1;
+        if (a.frames[mid].cta_begin <= (int)blockIdx.x) {
+            f = mid;
+            lo = mid + 1;
+        } else {
+            hi = mid - 1;
+        }
+    }
+    const PyrFrame& F = a.frames[f];
+    int t = blockIdx.x - F.cta_begin, l = a.levels - 1;
+    for (; l > 0; --l) {
+        const int n = level_ctas(F.W, F.H, l);
+        if (t < n) break;
+        t -= n;
+    }
+    LevelGeom d;
+    level_geom(F.W, F.H, a.levels, (int)sizeof(TS), l, &d);
+    const int tw = tile_w(l), th = tile_h(l);
+    const int tiles_x = (d.W + tw - 1) / tw;
+    const int tx0 = (t % tiles_x) * tw, ty0 = (t / tiles_x) * th;
     const int s = 1 << l;
-    const int vw = d.tw + 2, vh = d.th + 2;  // level values incl. the halo
-    const int rw = vw * s, rh = vh * s;      // level-0 bytes under them
+    const int vw = tw + 2, vh = th + 2;  // level values incl. the halo
+    const int rw = vw * s, rh = vh * s;  // level-0 bytes under them
     float* val = reinterpret_cast<float*>(smem);
     unsigned char* raw = smem + ((vw * vh * 4 + 15) & ~15);
     const int gx0 = (tx0 - 1) * s, gy0 = (ty0 - 1) * s;
@@ -60,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) pyramid_kernel(PyrArgs a)
     for (int i = threadIdx.x; i < rw * rh; i += blockDim.x) {
         const int ry = i / rw, rx = i - ry * rw;
         const int gx = gx0 + rx, gy = gy0 + ry;
-        raw[i] = (gx >= 0 && gx < a.W && gy >= 0 && gy < a.H) ? a.img[(size_t)gy * a.pitch + gx] : 0;
+        raw[i] = (gx >= 0 && gx < F.W && gy >= 0 && gy < F.H) ? F.img[(size_t)gy * F.pitch + gx] : 0;
     }
     __syncthreads();
     // 2. exact level-l values on the tile and its halo (inside the level only)
@@ -80,16 +100,16 @@ __global__ void __launch_bounds__(kThreads) pyramid_kernel(PyrArgs a)
     }
     __syncthreads();
     // 3. write the tile: I, and Sobel / 8 with clamped neighbours
-    TS* I = reinterpret_cast<TS*>(a.base + d.off_I);
-    TS* Ix = reinterpret_cast<TS*>(a.base + d.off_Ix);
-    TS* Iy = reinterpret_cast<TS*>(a.base + d.off_Iy);
-    for (int i = threadIdx.x; i < d.tw * d.th; i += blockDim.x) {
-        const int ty = i / d.tw, tx = i - ty * d.tw;
+    TS* I = reinterpret_cast<TS*>(F.base + d.off_I);
+    TS* Ix = reinterpret_cast<TS*>(F.base + d.off_Ix);
+    TS* Iy = reinterpret_cast<TS*>(F.base + d.off_Iy);
+    for (int i = threadIdx.x; i < tw * th; i += blockDim.x) {
+        const int ty = i / tw, tx = i - ty * tw;
         const int x = tx0 + tx, y = ty0 + ty;
         if (x >= d.W || y >= d.H) continue;
         const size_t o = (size_t)y * d.pitch + x;
-        dgf::st(I + o, val[(ty + 1) * vw + tx + 1]);
-        if (a.with_grad) {
+        st(I + o, val[(ty + 1) * vw + tx + 1]);
+        if (F.with_grad) {
             // region index of a clamped level coordinate
             const int xm = max(x - 1, 0) - (tx0 - 1), xp = min(x + 1, d.W - 1) - (tx0 - 1);
             const int ym = max(y - 1, 0) - (ty0 - 1), yp = min(y + 1, d.H - 1) - (ty0 - 1);
@@ -98,15 +118,43 @@ __global__ void __launch_bounds__(kThreads) pyramid_kernel(PyrArgs a)
                              (val[yp * vw + xp] - val[yp * vw + xm]);
             const float gy = (val[yp * vw + xm] - val[ym * vw + xm]) + 2.f * (val[yp * vw + xc] - val[ym * vw + xc]) +
                              (val[yp * vw + xp] - val[ym * vw + xp]);
-            dgf::st(Ix + o, gx * 0.125f);
-            dgf::st(Iy + o, gy * 0.125f);
+            st(Ix + o, gx * 0.125f);
+            st(Iy + o, gy * 0.125f);
         }
     }
 }
 
-size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+// Shared memory of the most demanding level (the coarsest).
+size_t pyramid_smem(int levels)
+{
+    size_t smem = 0;
+    for (int l = 0; l < levels; ++l) {
+        const size_t vw = tile_w(l) + 2, vh = tile_h(l) + 2, s = (size_t)1 << l;
+        const size_t need = round_up(vw * vh * 4, 16) + vw * vh * s * s;
+        smem = smem > need ? smem : need;
+    }
+    return smem;
+}
 
-}  // namespace
+// Fills the CTA prefix counts and launches one pyramid build for every frame.
+int launch_pyramids(PyrBatch& a, int storage, cudaStream_t stream)
+{
+    int ctas = 0;
+    for (int f = 0; f < a.n_frames; ++f) {
+        a.frames[f].cta_begin = ctas;
+        ctas += frame_ctas(a.frames[f].W, a.frames[f].H, a.levels);
+    }
+    const size_t smem = pyramid_smem(a.levels);
+    if (smem > (size_t)kSmemBytes) return DGF_ERR_ARG;
+    if (ctas == 0) return DGF_OK;
+    if (storage == DGF_F32)
+        pyramid_kernel<float><<<ctas, kThreads, smem, stream>>>(a);
+    else
+        pyramid_kernel<__half><<<ctas, kThreads, smem, stream>>>(a);
+    return launch_status();
+}
+
+}  // namespace dgf
 
 extern "C" int dgf_pyramid_layout_get(int W, int H, int levels, int storage, int with_grad,
                                       dgf_pyramid_layout* out)
@@ -118,25 +166,18 @@ extern "C" int dgf_pyramid_layout_get(int W, int H, int levels, int storage, int
     L.levels = levels;
     L.storage = storage;
     L.with_grad = with_grad ? 1 : 0;
-    const size_t es = storage == DGF_F32 ? 4 : 2;
-    size_t plane[DGF_MAX_LEVELS];
-    int w = W, h = H;
+    const int es = storage == DGF_F32 ? 4 : 2;
     for (int l = 0; l < levels; ++l) {
-        if (w < 1 || h < 1) return DGF_ERR_ARG;
-        L.W[l] = w;
-        L.H[l] = h;
-        L.pitch[l] = (int)round_up((size_t)w, 128 / es);
-        plane[l] = round_up((size_t)L.pitch[l] * h * es, 256);
-        w /= 2;
-        h /= 2;
+        dgf::LevelGeom g;
+        if (!dgf::level_geom(W, H, levels, es, l, &g)) return DGF_ERR_ARG;
+        L.W[l] = g.W;
+        L.H[l] = g.H;
+        L.pitch[l] = g.pitch;
+        L.off_I[l] = g.off_I;
+        L.off_Ix[l] = L.with_grad ? g.off_Ix : 0;
+        L.off_Iy[l] = L.with_grad ? g.off_Iy : 0;
+        L.bytes = L.with_grad ? g.bytes_all : g.bytes_intensity;
     }
-    size_t off = 0;
-    for (int l = 0; l < levels; ++l) { L.off_I[l] = off; off += plane[l]; }
-    if (L.with_grad) {
-        for (int l = 0; l < levels; ++l) { L.off_Ix[l] = off; off += plane[l]; }
-        for (int l = 0; l < levels; ++l) { L.off_Iy[l] = off; off += plane[l]; }
-    }
-    L.bytes = off;
     *out = L;
     return DGF_OK;
 }
@@ -156,40 +197,9 @@ extern "C" int pyramid_build(const uint8_t* img, int W, int H, int pitch, int le
     if (rc != DGF_OK) return rc;
     if (!dgf::aligned(pyr, 256)) return DGF_ERR_ARG;
     if (pyr_bytes < L.bytes) return DGF_ERR_WORKSPACE;
-    PyrArgs a = {};
-    a.img = img;
-    a.W = W;
-    a.H = H;
-    a.pitch = pitch;
+    dgf::PyrBatch a = {};
     a.levels = levels;
-    a.with_grad = L.with_grad;
-    a.base = static_cast<char*>(pyr);
-    int ctas = 0;
-    for (int l = levels - 1; l >= 0; --l) {
-        LevelDesc& d = a.lv[l];
-        d.W = L.W[l];
-        d.H = L.H[l];
-        d.pitch = L.pitch[l];
-        d.tw = tile_w(l);
-        d.th = tile_h(l);
-        d.tiles_x = (d.W + d.tw - 1) / d.tw;
-        d.cta_begin = ctas;
-        d.off_I = L.off_I[l];
-        d.off_Ix = L.off_Ix[l];
-        d.off_Iy = L.off_Iy[l];
-        ctas += d.tiles_x * ((d.H + d.th - 1) / d.th);
-    }
-    a.cta_end = ctas;
-    // shared memory of the most demanding level (the coarsest)
-    size_t smem = 0;
-    for (int l = 0; l < levels; ++l) {
-        const size_t vw = tile_w(l) + 2, vh = tile_h(l) + 2, s = (size_t)1 << l;
-        smem = smem > round_up(vw * vh * 4, 16) + vw * vh * s * s ? smem : round_up(vw * vh * 4, 16) + vw * vh * s * s;
-    }
-    if (smem > (size_t)kSmemBytes) return DGF_ERR_ARG;
-    if (storage == DGF_F32)
-        pyramid_kernel<float><<<ctas, kThreads, smem, stream>>>(a);
-    else
-        pyramid_kernel<__half><<<ctas, kThreads, smem, stream>>>(a);
-    return dgf::launch_status();
+    a.n_frames = 1;
+    a.frames[0] = dgf::PyrFrame{img, W, H, pitch, L.with_grad, static_cast<char*>(pyr), 0};
+    return dgf::launch_pyramids(a, storage, stream);
 }

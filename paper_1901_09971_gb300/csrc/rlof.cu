@@ -18,24 +18,11 @@
 // the convergence test run redundantly, so each group's control flow stays
 // uniform and points converge and exit independently.
 #include "common.cuh"
+#include "batch.cuh"
 
-namespace {
+namespace rlof_detail {
 
-struct LevelPlanes {
-    const void *I1, *I1x, *I1y, *I2;
-    int W, H, pitch;
-};
-
-struct RlofArgs {
-    LevelPlanes lv[DGF_MAX_LEVELS];
-    int levels, radius, max_iter, n;
-    float eps2, ha, hb, hc, inv_cb, min_eig;
-    const float* pts;
-    float* flow;
-    uint8_t* status;
-    uint8_t* iters;
-    float* illum;
-};
+using dgf::TrackBatch;
 
 template <int G>
 __device__ __forceinline__ float group_sum(float v, unsigned mask)
@@ -263,73 +250,182 @@ __device__ __forceinline__ void accumulate(const Support<SLP>& S, float2 (&acc)[
     }
 }
 
-template <typename TS, int G, int SLP, int MODEL, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const RlofArgs a)
+// Writes one point's results (lane 0 of its group).
+__device__ __forceinline__ void write_point(const dgf::TrackJob& J, int pt, int status, float fx, float fy,
+                                            int iters, float m, float c, bool model4)
 {
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int pt = gtid / G;
+    const bool ok = status == DGF_TRACKED || status == DGF_MAXITER;
+    reinterpret_cast<float2*>(J.flow)[pt] = ok ? make_float2(fx, fy) : make_float2(0.f, 0.f);
+    J.status[pt] = (uint8_t)status;
+    if (J.iters) J.iters[pt] = (uint8_t)min(iters, 255);
+    if (J.illum) reinterpret_cast<float2*>(J.illum)[pt] = ok && model4 ? make_float2(m, c) : make_float2(0.f, 0.f);
+}
+
+// Job holding global point index gp (binary search over the prefix counts).
+__device__ __forceinline__ int find_job(const TrackBatch& a, int gp)
+{
+    int job = 0;
+    for (int lo = 0, hi = a.n_jobs - 1; lo <= hi;) {
+        const int mid = (lo + hi) >> 1;
+        if (a.jobs[mid].pt_begin <= gp) {
+            job = mid;
+            lo = mid + 1;
+        } else {
+            hi = mid - 1;
+        }
+    }
+    return job;
+}
+
+// Planes and size of level l of a job's pyramids.
+template <typename TS>
+struct LevelView {
+    const TS *I1, *I1x, *I1y, *I2;
+    int W, H, pitch;
+    __device__ __forceinline__ LevelView(const dgf::TrackJob& J, int levels, int l)
+    {
+        dgf::LevelGeom g;
+        dgf::level_geom(J.W, J.H, levels, (int)sizeof(TS), l, &g);
+        I1 = reinterpret_cast<const TS*>(J.pyr1 + g.off_I);
+        I1x = reinterpret_cast<const TS*>(J.pyr1 + g.off_Ix);
+        I1y = reinterpret_cast<const TS*>(J.pyr1 + g.off_Iy);
+        I2 = reinterpret_cast<const TS*>(J.pyr2 + g.off_I);
+        W = g.W;
+        H = g.H;
+        pitch = g.pitch;
+    }
+};
+
+// Level set-up: samples the template T, Tx, Ty at p_l + k into the lane's pairs
+// and applies the minimum-eigenvalue test. Returns false for SMALL_EIG.
+template <typename TS, int G, int SLP>
+__device__ __forceinline__ bool setup_level(Support<SLP>& S, const LevelView<TS>& L, float plx, float ply, int lane,
+                                            unsigned mask, int R, float min_eig)
+{
+    const int side = 2 * R + 1, pc = R + 1, np = side * pc;
+    const float fx0 = floorf(plx), fy0 = floorf(ply);
+    const int bx = (int)fx0 - R, by = (int)fy0 - R;
+    const PairWeights pw(plx - fx0, ply - fy0);
+    float2 g00 = f2(0.f), g01 = f2(0.f), g11 = f2(0.f);
+#pragma unroll
+    for (int j = 0; j < SLP; ++j) {
+        const int q = lane + G * j;
+        const int ky = q / pc, kp = q - ky * pc;
+        float2 T = f2(0.f), Tx = f2(0.f), Ty = f2(0.f);
+        float msk = 0.f;
+        int off = 0;
+        if (q < np) {
+            off = ky * L.pitch + 2 * kp;
+            msk = 2 * kp + 1 < side ? 1.f : 0.f;
+            T = pair_clamped(L.I1, L.pitch, L.W, L.H, bx + 2 * kp, by + ky, pw);
+            Tx = pair_clamped(L.I1x, L.pitch, L.W, L.H, bx + 2 * kp, by + ky, pw);
+            Ty = pair_clamped(L.I1y, L.pitch, L.W, L.H, bx + 2 * kp, by + ky, pw);
+            if (msk == 0.f) T.y = Tx.y = Ty.y = 0.f;
+        }
+        S.T[j] = T;
+        S.Tx[j] = Tx;
+        S.Ty[j] = Ty;
+        S.off[j] = off;
+        S.msk[j] = msk;
+        g00 = __ffma2_rn(Tx, Tx, g00);
+        g01 = __ffma2_rn(Tx, Ty, g01);
+        g11 = __ffma2_rn(Ty, Ty, g11);
+    }
+    const float G00 = group_sum<G>(g00.x + g00.y, mask);
+    const float G01 = group_sum<G>(g01.x + g01.y, mask);
+    const float G11 = group_sum<G>(g11.x + g11.y, mask);
+    const float ht = 0.5f * (G00 + G11), hd = 0.5f * (G00 - G11);
+    const float lam = ht - sqrtf(hd * hd + G01 * G01);
+    return !(lam / (float)(side * side) < min_eig);
+}
+
+// One Gauss-Newton step at iterate q (inside the level): accumulates, reduces and
+// solves the weighted normal equations. Returns false on a non-positive pivot.
+template <typename TS, int G, int SLP, int MODEL>
+__device__ __forceinline__ bool gn_step(const Support<SLP>& S, const LevelView<TS>& L, float qx, float qy, float m,
+                                        float c, int lane, unsigned mask, int R, float ha, float icb, float hc_icb,
+                                        float (&delta)[4])
+{
+    const int side = 2 * R + 1, pc = R + 1, np = side * pc;
+    const float fx0 = floorf(qx), fy0 = floorf(qy);
+    const int bx = (int)fx0 - R, by = (int)fy0 - R;
+    const PairWeights pw(qx - fx0, qy - fy0);
+    // the tap block spans columns bx .. bx + 2R + 2 (the masked last sample
+    // included) and rows by .. by + 2R + 1
+    const bool inside = bx >= 0 && bx + 2 * R + 2 <= L.W - 1 && by >= 0 && by + 2 * R + 1 <= L.H - 1;
+    float2 acc[14];
+#pragma unroll
+    for (int k = 0; k < 14; ++k) acc[k] = f2(0.f);
+    const float g1 = 1.f + m;
+    if (inside && (bx & 1) == 0)
+        accumulate<TS, G, SLP, MODEL, 0>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
+                                         hc_icb);
+    else if (inside)
+        accumulate<TS, G, SLP, MODEL, 1>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
+                                         hc_icb);
+    else
+        accumulate<TS, G, SLP, MODEL, 2>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
+                                         hc_icb);
+    float h[16];
+    if (MODEL == 4) {
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 14; ++k) v[k] = acc[k].x + acc[k].y;
+        v[14] = v[15] = 0.f;
+        group_allreduce16<G>(v, h, mask, lane);
+        // a = (Tx, Ty, -T, -1): fold the signs of the T and constant columns
+        float Hm[4][4] = {{h[0], h[1], -h[2], -h[3]},
+                          {h[1], h[4], -h[5], -h[6]},
+                          {-h[2], -h[5], h[7], h[8]},
+                          {-h[3], -h[6], h[8], h[9]}};
+        const float rhs[4] = {-h[10], -h[11], h[12], h[13]};
+        return chol_solve<4>(Hm, rhs, delta);
+    }
+    const float h0 = group_sum<G>(acc[0].x + acc[0].y, mask);
+    const float h1 = group_sum<G>(acc[1].x + acc[1].y, mask);
+    const float h4 = group_sum<G>(acc[4].x + acc[4].y, mask);
+    const float b0 = group_sum<G>(acc[10].x + acc[10].y, mask);
+    const float b1 = group_sum<G>(acc[11].x + acc[11].y, mask);
+    float Hm[2][2] = {{h0, h1}, {h1, h4}};
+    const float rhs[2] = {-b0, -b1};
+    float x[2];
+    const bool ok = chol_solve<2>(Hm, rhs, x);
+    delta[0] = x[0];
+    delta[1] = x[1];
+    delta[2] = delta[3] = 0.f;
+    return ok;
+}
+
+// One point per group, coarse-to-fine loops kept tight. Blocks are short-lived
+// (eight points each at 16 lanes), so the block scheduler balances points of
+// uneven iteration counts and pairs of uneven size; a persistent variant that
+// pulled points from a work counter through a per-group state machine measured
+// slower on both the single-pair and the 64-pair workloads.
+template <typename TS, int G, int SLP, int MODEL, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const __grid_constant__ TrackBatch a)
+{
+    const int gp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    if (gp >= a.total) return;
     const int lane = threadIdx.x & (G - 1);
-    if (pt >= a.n) return;
     const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-    const int R = a.radius, side = 2 * R + 1, npx = side * side;
-    const int pc = R + 1, np = side * pc;  // pair columns per row, pairs in the support
+    const int R = a.radius;
     const float icb = a.inv_cb, hc_icb = a.hc * a.inv_cb;
+    const dgf::TrackJob& J = a.jobs[find_job(a, gp)];
+    const int pt = gp - J.pt_begin;
     Support<SLP> S;
 
-    const float2 p = reinterpret_cast<const float2*>(a.pts)[pt];
+    const float2 p = reinterpret_cast<const float2*>(J.pts)[pt];
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f, m = 0.f, c = 0.f;
     int status = DGF_TRACKED, iters = 0;
 
     for (int l = a.levels - 1; l >= 0; --l) {
-        const LevelPlanes L = a.lv[l];
-        const TS* I1 = static_cast<const TS*>(L.I1);
-        const TS* I1x = static_cast<const TS*>(L.I1x);
-        const TS* I1y = static_cast<const TS*>(L.I1y);
-        const TS* I2 = static_cast<const TS*>(L.I2);
+        const LevelView<TS> L(J, a.levels, l);
         const float scale = __int_as_float((127 - l) << 23);  // 2^-l
         const float plx = (p.x + 0.5f) * scale - 0.5f, ply = (p.y + 0.5f) * scale - 0.5f;
-
-        // level set-up: template and its gradients at p_l + k
-        {
-            const float fx0 = floorf(plx), fy0 = floorf(ply);
-            const int bx = (int)fx0 - R, by = (int)fy0 - R;
-            const PairWeights pw(plx - fx0, ply - fy0);
-            float2 g00 = f2(0.f), g01 = f2(0.f), g11 = f2(0.f);
-#pragma unroll
-            for (int j = 0; j < SLP; ++j) {
-                const int q = lane + G * j;
-                const int ky = q / pc, kp = q - ky * pc;
-                float2 T = f2(0.f), Tx = f2(0.f), Ty = f2(0.f);
-                float msk = 0.f;
-                int off = 0;
-                if (q < np) {
-                    off = ky * L.pitch + 2 * kp;
-                    msk = 2 * kp + 1 < side ? 1.f : 0.f;
-                    T = pair_clamped(I1, L.pitch, L.W, L.H, bx + 2 * kp, by + ky, pw);
-                    Tx = pair_clamped(I1x, L.pitch, L.W, L.H, bx + 2 * kp, by + ky, pw);
-                    Ty = pair_clamped(I1y, L.pitch, L.W, L.H, bx + 2 * kp, by + ky, pw);
-                    if (msk == 0.f) T.y = Tx.y = Ty.y = 0.f;
-                }
-                S.T[j] = T;
-                S.Tx[j] = Tx;
-                S.Ty[j] = Ty;
-                S.off[j] = off;
-                S.msk[j] = msk;
-                g00 = __ffma2_rn(Tx, Tx, g00);
-                g01 = __ffma2_rn(Tx, Ty, g01);
-                g11 = __ffma2_rn(Ty, Ty, g11);
-            }
-            const float G00 = group_sum<G>(g00.x + g00.y, mask);
-            const float G01 = group_sum<G>(g01.x + g01.y, mask);
-            const float G11 = group_sum<G>(g11.x + g11.y, mask);
-            const float ht = 0.5f * (G00 + G11), hd = 0.5f * (G00 - G11);
-            const float lam = ht - sqrtf(hd * hd + G01 * G01);
-            if (lam / (float)npx < a.min_eig) {
-                status = DGF_SMALL_EIG;
-                break;
-            }
+        if (!setup_level<TS, G, SLP>(S, L, plx, ply, lane, mask, R, a.min_eig)) {
+            status = DGF_SMALL_EIG;
+            break;
         }
-
         dx = 0.f;
         dy = 0.f;
         bool converged = false;
@@ -339,60 +435,8 @@ __global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const RlofArgs a)
                 status = DGF_OOB;
                 break;
             }
-            const float fx0 = floorf(qx), fy0 = floorf(qy);
-            const int bx = (int)fx0 - R, by = (int)fy0 - R;
-            const PairWeights pw(qx - fx0, qy - fy0);
-            // the tap block spans columns bx .. bx + 2R + 2 (the masked last sample
-            // included) and rows by .. by + 2R + 1
-            const bool inside = bx >= 0 && bx + 2 * R + 2 <= L.W - 1 && by >= 0 && by + 2 * R + 1 <= L.H - 1;
-            float2 acc[14];
-#pragma unroll
-            for (int k = 0; k < 14; ++k) acc[k] = f2(0.f);
-            const float g1 = 1.f + m;
-            if (inside && (bx & 1) == 0)
-                accumulate<TS, G, SLP, MODEL, 0>(S, acc, I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c,
-                                                 a.ha, icb, hc_icb);
-            else if (inside)
-                accumulate<TS, G, SLP, MODEL, 1>(S, acc, I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c,
-                                                 a.ha, icb, hc_icb);
-            else
-                accumulate<TS, G, SLP, MODEL, 2>(S, acc, I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c,
-                                                 a.ha, icb, hc_icb);
-            float h[16];
             float delta[4];
-            bool ok;
-            if (MODEL == 4) {
-                float v[16];
-#pragma unroll
-                for (int k = 0; k < 14; ++k) v[k] = acc[k].x + acc[k].y;
-                v[14] = v[15] = 0.f;
-                group_allreduce16<G>(v, h, mask, lane);
-                // a = (Tx, Ty, -T, -1): fold the signs of the T and constant columns
-                float Hm[4][4] = {{h[0], h[1], -h[2], -h[3]},
-                                  {h[1], h[4], -h[5], -h[6]},
-                                  {-h[2], -h[5], h[7], h[8]},
-                                  {-h[3], -h[6], h[8], h[9]}};
-                const float rhs[4] = {-h[10], -h[11], h[12], h[13]};
-                float x[4];
-                ok = chol_solve<4>(Hm, rhs, x);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) delta[k] = x[k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < 14; ++k) h[k] = acc[k].x + acc[k].y;
-                h[0] = group_sum<G>(h[0], mask);
-                h[1] = group_sum<G>(h[1], mask);
-                h[4] = group_sum<G>(h[4], mask);
-                h[10] = group_sum<G>(h[10], mask);
-                h[11] = group_sum<G>(h[11], mask);
-                float Hm[2][2] = {{h[0], h[1]}, {h[1], h[4]}};
-                const float rhs[2] = {-h[10], -h[11]};
-                float x[2];
-                ok = chol_solve<2>(Hm, rhs, x);
-                delta[0] = x[0];
-                delta[1] = x[1];
-            }
-            if (!ok) {
+            if (!gn_step<TS, G, SLP, MODEL>(S, L, qx, qy, m, c, lane, mask, R, a.ha, icb, hc_icb, delta)) {
                 status = DGF_SINGULAR;
                 break;
             }
@@ -416,30 +460,25 @@ __global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const RlofArgs a)
             status = DGF_MAXITER;
         }
     }
-
-    if (lane == 0) {
-        const bool ok = status == DGF_TRACKED || status == DGF_MAXITER;
-        reinterpret_cast<float2*>(a.flow)[pt] = ok ? make_float2(gx + dx, gy + dy) : make_float2(0.f, 0.f);
-        a.status[pt] = (uint8_t)status;
-        if (a.iters) a.iters[pt] = (uint8_t)min(iters, 255);
-        if (a.illum)
-            reinterpret_cast<float2*>(a.illum)[pt] = ok && MODEL == 4 ? make_float2(m, c) : make_float2(0.f, 0.f);
-    }
+    if (lane == 0) write_point(J, pt, status, gx + dx, gy + dy, iters, m, c, MODEL == 4);
 }
 
 int g_lanes_override = 0;
 
+template <typename TS, int MODEL, int G, int SLP>
+int launch_one(const TrackBatch& a, cudaStream_t stream)
+{
+    const long long total = (long long)a.total * G;
+    rlof_kernel<TS, G, SLP, MODEL, 4><<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, stream>>>(a);
+    return dgf::launch_status();
+}
+
 template <typename TS, int MODEL>
-int launch(const RlofArgs& a, int lanes, cudaStream_t stream)
+int launch(const TrackBatch& a, int lanes, cudaStream_t stream)
 {
     const int np = (2 * a.radius + 1) * (a.radius + 1);  // sample pairs in the support
-    const long long total = (long long)a.n * lanes;
-    const unsigned blocks = (unsigned)((total + kThreads - 1) / kThreads);
-#define DGF_LAUNCH(G, SLP)                                                                      \
-    if (lanes == G && (np + G - 1) / G == SLP) {                                                \
-        rlof_kernel<TS, G, SLP, MODEL, 4><<<blocks, kThreads, 0, stream>>>(a);                 \
-        return dgf::launch_status();                                                            \
-    }
+#define DGF_LAUNCH(G, SLP) \
+    if (lanes == G && (np + G - 1) / G == SLP) return launch_one<TS, MODEL, G, SLP>(a, stream);
     DGF_LAUNCH(8, 6)    // radius 4 (45 pairs)
     DGF_LAUNCH(8, 9)    // radius 5 (66 pairs)
     DGF_LAUNCH(16, 3)   // radius 4
@@ -459,7 +498,9 @@ int choose_lanes(int radius)
     return g_lanes_override ? g_lanes_override : 16;
 }
 
-}  // namespace
+}  // namespace rlof_detail
+
+using namespace rlof_detail;
 
 extern "C" void dgf_rlof_params_default(dgf_rlof_params* p)
 {
@@ -487,53 +528,66 @@ extern "C" int dgf_rlof_set_lanes(int lanes)
     return prev;
 }
 
-extern "C" int rlof_track(const void* pyr1, const void* pyr2, int W, int H, const float* pts, int n,
-                          const dgf_rlof_params* p, float* flow, uint8_t* status, uint8_t* iters, float* illum,
-                          cudaStream_t stream)
+namespace dgf {
+
+// Validates tracking parameters; fills the shared fields of a launch.
+int prepare_params(const dgf_rlof_params* p, TrackBatch& a)
 {
-    if (!p || p->version != DGF_RLOF_PARAMS_VERSION || n < 0) return DGF_ERR_ARG;
-    if (p->radius < 1 || p->radius > DGF_MAX_RADIUS || p->max_iter < 1 || p->max_iter > 255 ||
-        (p->model != 2 && p->model != 4) || !(p->eps >= 0.f) || !(p->hampel_a > 0.f) ||
+    if (!p || p->version != DGF_RLOF_PARAMS_VERSION) return DGF_ERR_ARG;
+    if (p->levels < 1 || p->levels > DGF_MAX_LEVELS || p->radius < 1 || p->radius > DGF_MAX_RADIUS ||
+        p->max_iter < 1 || p->max_iter > 255 || (p->model != 2 && p->model != 4) ||
+        (p->storage != DGF_F32 && p->storage != DGF_F16) || !(p->eps >= 0.f) || !(p->hampel_a > 0.f) ||
         !(p->hampel_b >= p->hampel_a) || !(p->hampel_c > p->hampel_b) || !(p->min_eig >= 0.f))
         return DGF_ERR_ARG;
-    dgf_pyramid_layout L1;
-    int rc = dgf_pyramid_layout_get(W, H, p->levels, p->storage, 1, &L1);
-    if (rc != DGF_OK) return rc;
-    const int need = 2 * p->radius + 2;
-    if (L1.W[p->levels - 1] < need || L1.H[p->levels - 1] < need) return DGF_ERR_LEVELS;
-    if (n == 0) return DGF_OK;
-    if (!pyr1 || !pyr2 || !pts || !flow || !status || !dgf::aligned(pyr1, 256) || !dgf::aligned(pyr2, 256) ||
-        !dgf::aligned(pts, 8) || !dgf::aligned(flow, 8) || (illum && !dgf::aligned(illum, 8)))
-        return DGF_ERR_ARG;
-    RlofArgs a = {};
-    for (int l = 0; l < p->levels; ++l) {
-        const char* b1 = static_cast<const char*>(pyr1);
-        const char* b2 = static_cast<const char*>(pyr2);
-        a.lv[l].I1 = b1 + L1.off_I[l];
-        a.lv[l].I1x = b1 + L1.off_Ix[l];
-        a.lv[l].I1y = b1 + L1.off_Iy[l];
-        a.lv[l].I2 = b2 + L1.off_I[l];  // intensity planes sit at the same offsets with or without gradients
-        a.lv[l].W = L1.W[l];
-        a.lv[l].H = L1.H[l];
-        a.lv[l].pitch = L1.pitch[l];
-    }
     a.levels = p->levels;
     a.radius = p->radius;
     a.max_iter = p->max_iter;
-    a.n = n;
+    a.es = p->storage == DGF_F32 ? 4 : 2;
     a.eps2 = p->eps * p->eps;
     a.ha = p->hampel_a;
-    a.hb = p->hampel_b;
     a.hc = p->hampel_c;
     a.inv_cb = 1.f / (p->hampel_c - p->hampel_b);
     a.min_eig = p->min_eig;
-    a.pts = pts;
-    a.flow = flow;
-    a.status = status;
-    a.iters = iters;
-    a.illum = illum;
+    return DGF_OK;
+}
+
+// Coarsest level large enough for the support (2 radius + 2 taps).
+int check_levels(int W, int H, const dgf_rlof_params* p)
+{
+    dgf::LevelGeom g;
+    if (!dgf::level_geom(W, H, p->levels, p->storage == DGF_F32 ? 4 : 2, p->levels - 1, &g)) return DGF_ERR_ARG;
+    const int need = 2 * p->radius + 2;
+    return g.W < need || g.H < need ? DGF_ERR_LEVELS : DGF_OK;
+}
+
+int lanes_setting() { return ::rlof_detail::g_lanes_override; }
+
+int launch_track(const TrackBatch& a, const dgf_rlof_params* p, cudaStream_t stream)
+{
+    using namespace ::rlof_detail;
     const int lanes = choose_lanes(p->radius);
     if (p->storage == DGF_F32)
         return p->model == 4 ? launch<float, 4>(a, lanes, stream) : launch<float, 2>(a, lanes, stream);
     return p->model == 4 ? launch<__half, 4>(a, lanes, stream) : launch<__half, 2>(a, lanes, stream);
+}
+
+}  // namespace
+
+extern "C" int rlof_track(const void* pyr1, const void* pyr2, int W, int H, const float* pts, int n,
+                          const dgf_rlof_params* p, float* flow, uint8_t* status, uint8_t* iters, float* illum,
+                          cudaStream_t stream)
+{
+    TrackBatch a = {};
+    int rc = dgf::prepare_params(p, a);
+    if (rc == DGF_OK) rc = n < 0 || W < 1 || H < 1 ? DGF_ERR_ARG : dgf::check_levels(W, H, p);
+    if (rc != DGF_OK) return rc;
+    if (n == 0) return DGF_OK;
+    if (!pyr1 || !pyr2 || !pts || !flow || !status || !dgf::aligned(pyr1, 256) || !dgf::aligned(pyr2, 256) ||
+        !dgf::aligned(pts, 8) || !dgf::aligned(flow, 8) || (illum && !dgf::aligned(illum, 8)))
+        return DGF_ERR_ARG;
+    a.n_jobs = 1;
+    a.total = n;
+    a.jobs[0] = dgf::TrackJob{static_cast<const char*>(pyr1), static_cast<const char*>(pyr2), W, H, pts, flow, status,
+                              iters, illum, 0};
+    return dgf::launch_track(a, p, stream);
 }

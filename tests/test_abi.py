@@ -99,6 +99,28 @@ def test_host_side_errors_return_before_launch():
     assert lib.degraf_detect(fake, 5, 5, 5, 7, 7, 3, None, None, None) == 0
 
 
+def test_batch_host_checks_return_before_launch():
+    lib = dgf.load()
+    prm = dgf.RlofParams(levels=3, radius=4).c()
+    pairs = (_abi.PairC * 2)()
+    fake = 1 << 20
+    for i, (W, H, step) in enumerate([(640, 480, 2), (1242, 375, 6)]):
+        pairs[i] = _abi.PairC(fake, fake, W, H, W, 8, step, fake, fake, fake, 0)
+    need = lib.dgf_track_many_workspace(pairs, 2, ctypes.byref(prm))
+    b = [dgf.pyramid_bytes(W, H, 3, 0, True) + dgf.pyramid_bytes(W, H, 3, 0, False)
+         for (W, H) in [(640, 480), (1242, 375)]]
+    assert need == sum(b)
+    # short workspace, misaligned workspace, bad pair, bad parameters: no launch
+    assert lib.rlof_track_many(pairs, 2, ctypes.byref(prm), ctypes.c_void_p(fake), need - 1, 7, 0, None) == -2
+    assert lib.rlof_track_many(pairs, 2, ctypes.byref(prm), ctypes.c_void_p(fake + 8), need, 7, 0, None) == -1
+    bad = (_abi.PairC * 1)(_abi.PairC(fake, 0, 640, 480, 640, 8, 2, fake, fake, fake, 0))
+    assert lib.dgf_track_many_workspace(bad, 1, ctypes.byref(prm)) == 0
+    deep = dgf.RlofParams(levels=6, radius=5).c()
+    assert lib.rlof_track_many(pairs, 2, ctypes.byref(deep), ctypes.c_void_p(fake), 1 << 40, 7, 0, None) == -3
+    assert lib.rlof_track_many(pairs, 0, ctypes.byref(prm), None, 0, 7, 0, None) == 0
+    assert lib.rlof_track_many(pairs, 2, ctypes.byref(prm), ctypes.c_void_p(fake), need, 8, 0, None) == -1
+
+
 def test_product_package_never_loads_the_oracle():
     code = ("import sys; sys.path.insert(0, %r); import paper_1901_09971_gb300 as d; d.load(); "
             "import bench; assert 'oracle' not in sys.modules, 'oracle imported'" % ROOT)

@@ -1,0 +1,134 @@
+"""GPU parity of the batched pipeline (rlof_track_many): every pair's key-points,
+flow, status and iteration counts equal those of the single-pair path bit for bit
+(same arithmetic, only the scheduling differs), and the single-pair path is held
+to the FP64 oracle by the same bars as tests/test_gpu_parity.py."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_FLOW = 1e-2
+
+
+@pytest.fixture(scope="module")
+def dgf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1901_09971_gb300 as m
+    m.load()
+    return m
+
+
+def frames_for(specs, seed0):
+    out = []
+    for i, (W, H, win, step) in enumerate(specs):
+        p = synth.make_translation_pair(W, H, seed=seed0 + i)
+        out.append((p.I1, p.I2))
+    return out
+
+
+def single_pair_path(dgf, I1, I2, win, step, prm):
+    f1 = torch.from_numpy(I1).cuda()
+    f2 = torch.from_numpy(I2).cuda()
+    H, W = I1.shape
+    tr = dgf.PairTracker(W, H, win, step, prm)
+    pts, flow, st, it = tr.run(f1, f2)
+    torch.cuda.synchronize()
+    return pts.cpu().numpy(), flow.cpu().numpy(), st.cpu().numpy(), it.cpu().numpy()
+
+
+def run_batch(dgf, specs, frames, prm, use_graph):
+    bt = dgf.BatchTracker(specs, prm)
+    d1 = [torch.from_numpy(a).cuda() for a, _ in frames]
+    d2 = [torch.from_numpy(b).cuda() for _, b in frames]
+    bt.run(d1, d2, use_graph=use_graph)
+    torch.cuda.synchronize()
+    return bt, d1, d2
+
+
+def assert_same_as_single(dgf, bt, frames, specs, prm):
+    for i, ((I1, I2), (W, H, win, step)) in enumerate(zip(frames, specs)):
+        pts, flow, st, it = single_pair_path(dgf, I1, I2, win, step, prm)
+        assert np.array_equal(bt.pts[i].cpu().numpy(), pts), f"pair {i} points"
+        assert np.array_equal(bt.flow[i].cpu().numpy(), flow), f"pair {i} flow"
+        assert np.array_equal(bt.status[i].cpu().numpy(), st), f"pair {i} status"
+        assert np.array_equal(bt.iters[i].cpu().numpy(), it), f"pair {i} iterations"
+
+
+SMALL_SPECS = [(320, 240, 8, 2), (256, 109, 8, 3), (310, 93, 7, 4), (320, 180, 8, 6), (97, 61, 7, 3),
+               (160, 120, 8, 4)]
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_equals_single_pair_path_and_oracle(dgf, use_graph):
+    prm = dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)
+    frames = frames_for(SMALL_SPECS, 3100)
+    bt, _, _ = run_batch(dgf, SMALL_SPECS, frames, prm, use_graph)
+    assert_same_as_single(dgf, bt, frames, SMALL_SPECS, prm)
+    oprm = oracle.RlofParams(levels=3, radius=4, max_iter=30, model=4)
+    for i, ((I1, I2), (W, H, win, step)) in enumerate(zip(frames, SMALL_SPECS)):
+        pts_o, _, _ = oracle.degraf_detect(I1, win, win, step)
+        pts = bt.pts[i].cpu().numpy()
+        assert pts.shape == pts_o.shape and np.abs(pts - pts_o).max() <= 1e-4
+        fo, so, _, _ = oracle.rlof_track(I1, I2, pts.astype(np.float64), oprm)
+        sg, fg = bt.status[i].cpu().numpy(), bt.flow[i].cpu().numpy()
+        both = (sg == 0) & (so == 0)
+        e = np.hypot(*(fg.astype(np.float64) - fo).T)
+        assert np.mean(sg == so) >= 0.99
+        assert np.mean(e[both] <= TOL_FLOW) >= 0.999
+
+
+def test_graph_replay_sees_new_frame_contents(dgf):
+    prm = dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)
+    specs = SMALL_SPECS[:3]
+    frames = frames_for(specs, 3200)
+    bt, d1, d2 = run_batch(dgf, specs, frames, prm, True)
+    first = [f.cpu().numpy().copy() for f in bt.flow]
+    frames2 = frames_for(specs, 3300)
+    for k, (a, b) in enumerate(frames2):  # same buffers, new contents: the cached graph replays
+        d1[k].copy_(torch.from_numpy(a))
+        d2[k].copy_(torch.from_numpy(b))
+    bt.run(d1, d2, use_graph=True)
+    torch.cuda.synchronize()
+    assert any(not np.array_equal(first[k], bt.flow[k].cpu().numpy()) for k in range(len(specs)))
+    assert_same_as_single(dgf, bt, frames2, specs, prm)
+
+
+def test_more_pairs_than_one_chunk(dgf):
+    """70 pairs: two chunks of the persistent launch, each with its own counter."""
+    prm = dgf.RlofParams(levels=2, radius=4, max_iter=20, model=2)
+    specs = [(64 + (i % 5) * 8, 48 + (i % 3) * 8, 8, 3 + (i % 2)) for i in range(70)]
+    frames = frames_for(specs, 3400)
+    bt, _, _ = run_batch(dgf, specs, frames, prm, False)
+    assert_same_as_single(dgf, bt, frames, specs, prm)
+
+
+def test_mixed_size_batch_of_64_pairs(dgf):
+    """The mixed-size batch workload: 64 pairs of 640x480 .. 1280x720, steps 2..6,
+    window 8, 3 levels, 9x9 support; every pair equals the single-pair path, and
+    sampled points of four pairs are checked against the oracle."""
+    specs = [(W, H, 8, step) for (W, H, step) in synth.make_batch_specs(64, 3000)]
+    frames = []
+    for i, (W, H, win, step) in enumerate(specs):
+        p = synth.make_translation_pair(W, H, seed=3000 + i)
+        frames.append((p.I1, p.I2))
+    prm = dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)
+    bt, _, _ = run_batch(dgf, specs, frames, prm, True)
+    assert sum(bt.n) > 1_000_000
+    assert_same_as_single(dgf, bt, frames, specs, prm)
+    oprm = oracle.RlofParams(levels=3, radius=4, max_iter=30, model=4)
+    rng = np.random.default_rng(0)
+    for i in (0, 17, 42, 63):
+        I1, I2 = frames[i]
+        idx = rng.choice(bt.n[i], size=min(400, bt.n[i]), replace=False)
+        pts = bt.pts[i].cpu().numpy()[idx]
+        fo, so, _, _ = oracle.rlof_track(I1, I2, pts.astype(np.float64), oprm)
+        sg, fg = bt.status[i].cpu().numpy()[idx], bt.flow[i].cpu().numpy()[idx]
+        both = (sg == 0) & (so == 0)
+        e = np.hypot(*(fg.astype(np.float64) - fo).T)
+        assert np.mean(sg == so) >= 0.98
+        assert np.mean(e[both] <= TOL_FLOW) >= 0.99
