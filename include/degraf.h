@@ -234,6 +234,33 @@ size_t dgf_track_many_workspace(const dgf_pair* pairs, int n_pairs, const dgf_rl
 int rlof_track_many(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p, void* workspace,
                     size_t ws_bytes, int stages, int use_graph, cudaStream_t stream);
 
+/* ---- one pair without allocation (no counterpart in the paper) ------------ */
+
+/* Size of the scratch array rlof_track_pair_noalloc uses (24 MiB). */
+#define DGF_NOALLOC_SCRATCH_BYTES (24u << 20)
+
+/*
+ * For callers that cannot allocate device memory while they track (a real-time
+ * loop that must not risk an allocation stall, a plug-in inside an application
+ * that owns the GPU's memory, code that forbids allocation after start-up): the
+ * same detection + pyramids + tracking as rlof_track_many for ONE pair, with the
+ * two pyramids placed in a fixed scratch array compiled into the library instead
+ * of a caller workspace. The caller still provides the frames and every output
+ * buffer of *pair. Nothing is allocated: no cudaMalloc, no cudaFree, no graph.
+ *   - The scratch array (DGF_NOALLOC_SCRATCH_BYTES) occupies device memory on
+ *     every GPU that loads the library until the process exits.
+ *   - A pair whose two pyramids need more (dgf_track_many_workspace(pair, 1, p) >
+ *     DGF_NOALLOC_SCRATCH_BYTES; e.g. beyond about 1280x720 at 5 FP32 levels) is
+ *     rejected with DGF_ERR_WORKSPACE before anything is enqueued.
+ *   - The first call on each device looks up the array's device address (the
+ *     device must be current); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's pyramids. Calls
+ *     whose work overlaps on the GPU (different streams without ordering between
+ *     them, or several host threads) race on it: order them on one stream.
+ * Returns the rlof_track_many codes.
+ */
+int rlof_track_pair_noalloc(const dgf_pair* pair, const dgf_rlof_params* p, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ RLOF_PARAMS_VERSION = 1
 EXPORTS = (
     "dgf_strerror", "dgf_version", "dgf_degraf_count", "degraf_detect", "dgf_pyramid_layout_get",
     "dgf_pyramid_bytes", "pyramid_build", "dgf_rlof_params_default", "dgf_rlof_set_lanes", "rlof_track",
-    "dgf_track_many_workspace", "rlof_track_many",
+    "dgf_track_many_workspace", "rlof_track_many", "rlof_track_pair_noalloc",
 )
 
 
@@ -94,6 +94,8 @@ def load(build_if_missing: bool = True):
     L.dgf_track_many_workspace.restype = Z
     L.rlof_track_many.argtypes = [ctypes.POINTER(PairC), I, ctypes.POINTER(RlofParamsC), P, Z, I, I, P]
     L.rlof_track_many.restype = I
+    L.rlof_track_pair_noalloc.argtypes = [ctypes.POINTER(PairC), ctypes.POINTER(RlofParamsC), P]
+    L.rlof_track_pair_noalloc.restype = I
     _lib = L
     return L
 

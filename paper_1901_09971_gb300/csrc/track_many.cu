@@ -217,3 +217,57 @@ extern "C" int rlof_track_many(const dgf_pair* pairs, int n_pairs, const dgf_rlo
     }
     return cudaGraphLaunch(it->second, stream) == cudaSuccess ? DGF_OK : DGF_ERR_CUDA;
 }
+
+// ---- single pair without any allocation ------------------------------------
+//
+// Some callers cannot allocate device memory when they want to track: code that
+// must not call cudaMalloc after start-up (real-time loops where an allocation
+// could stall or fail, plug-ins whose host application owns all device memory,
+// code whose rules forbid dynamic allocation once running). They still own their
+// frames and output buffers; what they cannot provide is the pyramid workspace.
+// This entry point uses a fixed scratch array compiled into the library instead.
+// Every GPU that loads the library holds the array until the process exits.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)24 << 20;  // DGF_NOALLOC_SCRATCH_BYTES
+static_assert(kNoAllocScratchBytes == (size_t)DGF_NOALLOC_SCRATCH_BYTES, "scratch size and header disagree");
+
+// The pyramids of the pair being tracked. Shared by every call: nothing in it
+// needs to start at zero (each call rewrites every byte it later reads).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+
+// Device address of the scratch array on the current device. The host-side name
+// of a __device__ array is only a stand-in, so the address is looked up once per
+// device (with that device current) and kept.
+void* scratch_address(int dev)
+{
+    static void* addr[kMaxDevices] = {};
+    static std::mutex mu;
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+        addr[dev] = p;
+    }
+    return addr[dev];
+}
+
+}  // namespace
+
+extern "C" int rlof_track_pair_noalloc(const dgf_pair* pair, const dgf_rlof_params* p, cudaStream_t stream)
+{
+    PairPlan plan1;
+    int rc;
+    const size_t need = plan(pair, 1, p, &plan1, &rc);
+    if (rc != DGF_OK) return rc;
+    if (need > kNoAllocScratchBytes) return DGF_ERR_WORKSPACE;  // frames too large for the fixed scratch
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DGF_ERR_CUDA;
+    char* ws = static_cast<char*>(scratch_address(dev));
+    if (!ws) return DGF_ERR_CUDA;
+    return enqueue(pair, 1, p, &plan1, ws, DGF_STAGE_ALL, stream);
+}
