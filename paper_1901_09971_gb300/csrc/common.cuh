@@ -17,7 +17,8 @@ __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg
 __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 
-__host__ __device__ __forceinline__ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+// Rounds v up to a multiple of a, a power of two.
+__host__ __device__ __forceinline__ size_t round_up(size_t v, size_t a) { return (v + a - 1) & ~(a - 1); }
 
 // Geometry of one pyramid level inside a pyramid buffer (see dgf_pyramid_layout):
 // planes I_0..I_{L-1}, then Ix_0..Ix_{L-1}, Iy_0..Iy_{L-1}; each plane starts on a

@@ -7,8 +7,8 @@
 // sums S = sum I, X = sum j I, Y = sum i I and the maximum m are exact int32; the
 // negative-centroid sums follow from them in closed form,
 //   S_neg = n (1+m) - S,  X_neg = (1+m) h w (w-1)/2 - X,  Y_neg = (1+m) w h (h-1)/2 - Y,
-// and the selected centroid is formed in FP64 and rounded once to FP32, so every
-// coordinate is the exactly rounded value of Eq. 1 or Eq. 2 plus the window origin.
+// and the selected centroid is an FP32 quotient of exact integers plus the window
+// origin (two correctly rounded steps, within one FP32 ulp of Eq. 1 or Eq. 2).
 #include "common.cuh"
 #include "batch.cuh"
 
@@ -28,26 +28,69 @@ __device__ __forceinline__ void emit(const DetectJob& J, int ww, int wh, int u, 
     const int n = ww * wh;
     const int m1 = m + 1;
     const int Sn = n * m1 - S;
-    double cx, cy;
+    int num_x, num_y, den;
     if (Sn > S) {  // Eq. 2 centroid: the larger weight sum wins, ties keep C_pos
-        const int Xn = m1 * (wh * (ww * (ww - 1) / 2)) - X;
-        const int Yn = m1 * (ww * (wh * (wh - 1) / 2)) - Y;
-        cx = (double)Xn / (double)Sn;
-        cy = (double)Yn / (double)Sn;
+        num_x = m1 * (wh * (ww * (ww - 1) / 2)) - X;
+        num_y = m1 * (ww * (wh * (wh - 1) / 2)) - Y;
+        den = Sn;
     } else {  // Eq. 1 centroid
-        cx = (double)X / (double)S;
-        cy = (double)Y / (double)S;
+        num_x = X;
+        num_y = Y;
+        den = S;
+    }
+    // correctly rounded quotients, then the window origin: one rounding each. FP32
+    // operands are exact below 2^24 (every window up to about 45 x 45); larger
+    // moments divide in FP64 (GB300's FP64 rate is low, so only where needed)
+    float cx, cy;
+    if (num_x < (1 << 24) && num_y < (1 << 24) && den < (1 << 24)) {
+        cx = __fdiv_rn((float)num_x, (float)den);
+        cy = __fdiv_rn((float)num_y, (float)den);
+    } else {
+        cx = (float)((double)num_x / (double)den);
+        cy = (float)((double)num_y / (double)den);
     }
     const long long k = (long long)v * J.nu + u;
-    reinterpret_cast<float2*>(J.pts)[k] =
-        make_float2((float)((double)(u * J.step) + cx), (float)((double)(v * J.step) + cy));
+    reinterpret_cast<float2*>(J.pts)[k] = make_float2(__fadd_rn((float)(u * J.step), cx), __fadd_rn((float)(v * J.step), cy));
     if (J.sums) reinterpret_cast<int4*>(J.sums)[k] = make_int4(S, X, Y, m);
+}
+
+// Window sums of a window of width <= 8 from a staged tile whose rows start on
+// 4-byte boundaries: per row, the window's bytes become two 32-bit words (funnel
+// shifts of three aligned loads), bytes past the window are masked off, and
+// dp4a forms the row sum and the column-weighted row sum while a bytewise max
+// tracks m.
+__device__ __forceinline__ void window_sums_packed(const uint8_t* tile, int stride, int c0, int r0, int ww, int wh,
+                                                   int& S, int& X, int& Y, int& m)
+{
+    const unsigned shift = (c0 & 3) * 8;
+    const unsigned mlo = ww >= 4 ? 0xffffffffu : (1u << (8 * ww)) - 1u;
+    const unsigned mhi = ww >= 8 ? 0xffffffffu : ww <= 4 ? 0u : (1u << (8 * (ww - 4))) - 1u;
+    const unsigned* row = reinterpret_cast<const unsigned*>(tile + r0 * stride) + (c0 >> 2);
+    unsigned mx = 0;
+    int s = 0, x = 0, y = 0;
+    for (int i = 0; i < wh; ++i) {
+        const unsigned w0 = row[0], w1 = row[1], w2 = row[2];
+        const unsigned lo = __funnelshift_r(w0, w1, shift) & mlo;
+        const unsigned hi = __funnelshift_r(w1, w2, shift) & mhi;
+        const int rs = (int)__dp4a(lo, 0x01010101u, __dp4a(hi, 0x01010101u, 0u));
+        x += (int)__dp4a(lo, 0x03020100u, __dp4a(hi, 0x07060504u, 0u));
+        s += rs;
+        y += i * rs;
+        mx = __vmaxu4(mx, __vmaxu4(lo, hi));
+        row += stride >> 2;
+    }
+    mx = __vmaxu4(mx, mx >> 16);
+    mx = __vmaxu4(mx, mx >> 8);
+    S = s;
+    X = x;
+    Y = y;
+    m = (int)(mx & 0xffu);
 }
 
 // One thread per window; CTAs of all frames of the batch in one grid.
 __global__ void __launch_bounds__(256) degraf_detect_kernel(const __grid_constant__ DetectBatch a)
 {
-    extern __shared__ uint8_t tile[];
+    extern __shared__ __align__(16) uint8_t tile[];
     int f = 0;
     for (int lo = 0, hi = a.n_jobs - 1; lo <= hi;) {
         const int mid = (lo + hi) >> 1;
@@ -63,38 +106,57 @@ __global__ void __launch_bounds__(256) degraf_detect_kernel(const __grid_constan
     const int u0 = (t % J.tiles_x) * kBX, v0 = (t / J.tiles_x) * blockDim.y;
     const int x0 = u0 * J.step, y0 = v0 * J.step;
     const int tile_w = (kBX - 1) * J.step + a.ww, tile_h = ((int)blockDim.y - 1) * J.step + a.wh;
+    const int stride = a.tile_w;  // row stride of the staged tile (multiple of 4)
     if (a.staged) {
+        // stage the pixels under the CTA's windows: a thread owns columns tx, tx+32, ..
+        // of rows ty, ty+BY, ..; per column it issues all its row loads before storing
         const int tw = min(tile_w, J.W - x0), th = min(tile_h, J.H - y0);
-        for (int r = threadIdx.y; r < th; r += blockDim.y) {
-            const uint8_t* src = J.img + (size_t)(y0 + r) * J.pitch + x0;
-            for (int c = threadIdx.x; c < tw; c += blockDim.x) tile[r * tile_w + c] = src[c];
+        for (int c = threadIdx.x; c < tw; c += blockDim.x) {
+            const uint8_t* src = J.img + (size_t)y0 * J.pitch + x0 + c;
+            uint8_t v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int r = threadIdx.y + k * blockDim.y;
+                v[k] = r < th ? __ldg(src + (size_t)r * J.pitch) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int r = threadIdx.y + k * blockDim.y;
+                if (r < th) tile[r * stride + c] = v[k];
+            }
+            for (int r = threadIdx.y + 8 * blockDim.y; r < th; r += blockDim.y)  // tall tiles (by < 8)
+                tile[r * stride + c] = __ldg(src + (size_t)r * J.pitch);
         }
         __syncthreads();
     }
     const int u = u0 + threadIdx.x, v = v0 + threadIdx.y;
     if (u >= J.nu || v >= J.nv) return;
-    const uint8_t* w0;
-    int rstride;
-    if (a.staged) {
-        w0 = tile + threadIdx.y * J.step * tile_w + threadIdx.x * J.step;
-        rstride = tile_w;
-    } else {
-        w0 = J.img + (size_t)(v * J.step) * J.pitch + u * J.step;
-        rstride = J.pitch;
-    }
     int S = 0, X = 0, Y = 0, m = 0;
-    for (int i = 0; i < a.wh; ++i) {
-        const uint8_t* row = w0 + (size_t)i * rstride;
-        int rs = 0, rx = 0;
-        for (int j = 0; j < a.ww; ++j) {
-            const int I = row[j];
-            rs += I;
-            rx += j * I;
-            m = max(m, I);
+    if (a.staged && a.ww <= 8) {
+        window_sums_packed(tile, stride, threadIdx.x * J.step, threadIdx.y * J.step, a.ww, a.wh, S, X, Y, m);
+    } else {
+        const uint8_t* w0;
+        int rstride;
+        if (a.staged) {
+            w0 = tile + threadIdx.y * J.step * stride + threadIdx.x * J.step;
+            rstride = stride;
+        } else {
+            w0 = J.img + (size_t)(v * J.step) * J.pitch + u * J.step;
+            rstride = J.pitch;
         }
-        S += rs;
-        X += rx;
-        Y += i * rs;
+        for (int i = 0; i < a.wh; ++i) {
+            const uint8_t* row = w0 + (size_t)i * rstride;
+            int rs = 0, rx = 0;
+            for (int j = 0; j < a.ww; ++j) {
+                const int I = row[j];
+                rs += I;
+                rx += j * I;
+                m = max(m, I);
+            }
+            S += rs;
+            X += rx;
+            Y += i * rs;
+        }
     }
     emit(J, a.ww, a.wh, u, v, S, X, Y, m);
 }
@@ -111,7 +173,9 @@ int launch_detect(DetectBatch& a, cudaStream_t stream)
         overlap = overlap && (a.jobs[f].step < a.ww || a.jobs[f].step < a.wh);
     }
     int by = 8;
-    const int tile_w = (kBX - 1) * max_step + a.ww;
+    // rows padded to 4 bytes plus two words, so the packed path's three aligned
+    // word loads past a window start stay inside the row
+    const int tile_w = ((kBX - 1) * max_step + a.ww + 3) / 4 * 4 + 8;
     int tile_h = (by - 1) * max_step + a.wh;
     while (by > 1 && tile_w * tile_h > kSmemMax) {
         by /= 2;
@@ -119,7 +183,7 @@ int launch_detect(DetectBatch& a, cudaStream_t stream)
     }
     a.by = by;
     a.staged = overlap && tile_w * tile_h <= kSmemMax;
-    a.tile_w = tile_w;
+    a.tile_w = tile_w;  // row stride of the staged tile
     a.tile_h = tile_h;
     long long ctas = 0;
     for (int f = 0; f < a.n_jobs; ++f) {

@@ -3,154 +3,284 @@
 // paper does not define).
 //
 // Definition used: level l+1 = 2x2 block means of level l (sizes floor(W_l/2) x
-// floor(H_l/2)); Ix, Iy = Sobel / 8 with clamped borders. Level-l pixel (x, y) is
-// therefore exactly (sum of the 2^l x 2^l block of level-0 bytes at (2^l x, 2^l y))
-// / 4^l: an integer times a power of two, exact in FP32 for every level this
-// library allows, and so are the Sobel sums. Hence every level can be computed
-// straight from the uint8 frame, independently of the others, in one launch:
-// each CTA owns one tile of one level, stages the level-0 bytes under the tile plus
-// a one-pixel level-l halo in shared memory, forms the exact level values there,
-// and writes I (and Ix, Iy) with coalesced rows. FP16 storage rounds each exact
-// value once.
+// floor(H_l/2)); Ix, Iy = Sobel / 8 with clamped borders. Every level value is an
+// integer byte sum times 4^-l and every Sobel sum a small multiple of it, so all of
+// them are exact in FP32 (FP16 storage rounds each exact value once).
+//
+// One CTA owns a 64 x 32 tile of level 0 and produces the matching tile of every
+// level: it stages the frame bytes under the tile plus a halo of 2^(L-1) pixels in
+// shared memory (enough for a one-pixel halo at the coarsest level), then walks
+// down the levels, forming each level's values on its halo'd region from the
+// previous one with 2x2 means and writing I, Ix, Iy of the tile with coalesced
+// rows (16-byte stores at level 0). The frame is read about once from DRAM and
+// every output byte is written once, which makes the kernel a streaming one.
 #include "common.cuh"
 #include "batch.cuh"
 
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSmemBytes = 40 * 1024;
+constexpr int kTX = 64, kTY = 32;  // level-0 tile
 
-__host__ __device__ inline int tile_w(int l) { return 64 >> (l < 4 ? l : 4); }
-__host__ __device__ inline int tile_h(int l) { return l == 0 ? 16 : (l == 1 ? 8 : 4); }
+__host__ __device__ inline int halo(int levels) { return levels >= 2 ? 1 << (levels - 1) : 1; }
 
-// CTAs of one frame's pyramid: coarsest level first (those CTAs do the most work).
-__host__ __device__ inline int level_ctas(int W, int H, int l)
+__host__ __device__ inline int frame_ctas(int W, int H) { return ((W + kTX - 1) / kTX) * ((H + kTY - 1) / kTY); }
+
+__host__ __device__ inline size_t round16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+// Shared memory of one CTA: the byte region, then the float regions of levels 1..L-1.
+inline size_t smem_bytes(int levels)
 {
-    const int w = W >> l, h = H >> l;
-    return ((w + tile_w(l) - 1) / tile_w(l)) * ((h + tile_h(l) - 1) / tile_h(l));
+    const int h = halo(levels);
+    const int RW = kTX + 2 * h, RH = kTY + 2 * h;
+    size_t off = round16((size_t)RW * RH);
+    for (int l = 1; l < levels; ++l) off += round16((size_t)(RW >> l) * (RH >> l) * 4);
+    return off;
 }
 
-__host__ __device__ inline int frame_ctas(int W, int H, int levels)
+template <typename TS>
+__device__ __forceinline__ void store4(TS* p, float a, float b, float c, float d);
+template <>
+__device__ __forceinline__ void store4<float>(float* p, float a, float b, float c, float d)
 {
-    int n = 0;
-    for (int l = 0; l < levels; ++l) n += level_ctas(W, H, l);
-    return n;
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+template <>
+__device__ __forceinline__ void store4<__half>(__half* p, float a, float b, float c, float d)
+{
+    __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+    uint2 v;
+    v.x = *reinterpret_cast<unsigned*>(&lo);
+    v.y = *reinterpret_cast<unsigned*>(&hi);
+    *reinterpret_cast<uint2*>(p) = v;
 }
 
 }  // namespace
 
 namespace dgf {
 
-// One launch builds every level of up to kMaxFrames pyramids; CTAs are assigned
-// frame by frame (cta_begin is the prefix count).
-template <typename TS>
-__global__ void __launch_bounds__(kThreads) pyramid_kernel(const __grid_constant__ PyrBatch a)
+// Level 0 of the tile: I and Sobel / 8 straight from the staged bytes, four
+// pixels per item. INTERIOR: the halo'd region lies inside the frame, so no
+// neighbour needs clamping.
+template <typename TS, bool INTERIOR>
+__device__ __forceinline__ void level0(const PyrFrame& F, const LevelGeom& g, const unsigned char* raw, int RW,
+                                       int X0, int Y0, int h)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    int f = 0;  // frame of this CTA (binary search over the prefix counts)
-    for (int lo = 0, hi = a.n_frames - 1; lo <= hi;) {
-        const int mid = (lo + hi) >> 1;
-        if (a.frames[mid].cta_begin <= (int)blockIdx.x) {
-            f = mid;
-            lo = mid + 1;
+    TS* I = reinterpret_cast<TS*>(F.base + g.off_I);
+    TS* Ix = reinterpret_cast<TS*>(F.base + g.off_Ix);
+    TS* Iy = reinterpret_cast<TS*>(F.base + g.off_Iy);
+    const int gx0 = X0 - h, gy0 = Y0 - h;
+    for (int i = threadIdx.x; i < kTY * (kTX / 4); i += blockDim.x) {
+        const int ty = i >> 4, tx = (i & 15) << 2;  // kTX / 4 = 16 items per row
+        const int y = Y0 + ty;
+        if (!INTERIOR && (y >= F.H || X0 + tx >= F.W)) continue;
+        float vI[4], vx[4], vy[4];
+        if (INTERIOR) {
+            const unsigned char* rc = raw + (ty + h) * RW + tx + h - 1;  // columns x-1 .. x+4
+            const unsigned char* rm = rc - RW;
+            const unsigned char* rp = rc + RW;
+            int a[6], b[6], c[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                a[j] = rm[j];
+                b[j] = rc[j];
+                c[j] = rp[j];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int sx = (a[k + 2] - a[k]) + 2 * (b[k + 2] - b[k]) + (c[k + 2] - c[k]);
+                const int sy = (c[k] - a[k]) + 2 * (c[k + 1] - a[k + 1]) + (c[k + 2] - a[k + 2]);
+                vI[k] = (float)b[k + 1];
+                vx[k] = (float)sx * 0.125f;
+                vy[k] = (float)sy * 0.125f;
+            }
         } else {
-            hi = mid - 1;
+            const int ym = max(y - 1, 0) - gy0, yc = y - gy0, yp = min(y + 1, F.H - 1) - gy0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int x = min(X0 + tx + k, F.W - 1);  // past the edge: recomputed, not stored
+                const int xm = max(x - 1, 0) - gx0, xc = x - gx0, xp = min(x + 1, F.W - 1) - gx0;
+                const unsigned char* rm = raw + ym * RW;
+                const unsigned char* rc = raw + yc * RW;
+                const unsigned char* rp = raw + yp * RW;
+                const int sx = ((int)rm[xp] - rm[xm]) + 2 * ((int)rc[xp] - rc[xm]) + ((int)rp[xp] - rp[xm]);
+                const int sy = ((int)rp[xm] - rm[xm]) + 2 * ((int)rp[xc] - rm[xc]) + ((int)rp[xp] - rm[xp]);
+                vI[k] = (float)rc[xc];
+                vx[k] = (float)sx * 0.125f;
+                vy[k] = (float)sy * 0.125f;
+            }
         }
-    }
-    const PyrFrame& F = a.frames[f];
-    int t = blockIdx.x - F.cta_begin, l = a.levels - 1;
-    for (; l > 0; --l) {
-        const int n = level_ctas(F.W, F.H, l);
-        if (t < n) break;
-        t -= n;
-    }
-    LevelGeom d;
-    level_geom(F.W, F.H, a.levels, (int)sizeof(TS), l, &d);
-    const int tw = tile_w(l), th = tile_h(l);
-    const int tiles_x = (d.W + tw - 1) / tw;
-    const int tx0 = (t % tiles_x) * tw, ty0 = (t / tiles_x) * th;
-    const int s = 1 << l;
-    const int vw = tw + 2, vh = th + 2;  // level values incl. the halo
-    const int rw = vw * s, rh = vh * s;  // level-0 bytes under them
-    float* val = reinterpret_cast<float*>(smem);
-    unsigned char* raw = smem + ((vw * vh * 4 + 15) & ~15);
-    const int gx0 = (tx0 - 1) * s, gy0 = (ty0 - 1) * s;
-
-    // 1. stage the level-0 bytes (only those inside the frame are ever used)
-    for (int i = threadIdx.x; i < rw * rh; i += blockDim.x) {
-        const int ry = i / rw, rx = i - ry * rw;
-        const int gx = gx0 + rx, gy = gy0 + ry;
-        raw[i] = (gx >= 0 && gx < F.W && gy >= 0 && gy < F.H) ? F.img[(size_t)gy * F.pitch + gx] : 0;
-    }
-    __syncthreads();
-    // 2. exact level-l values on the tile and its halo (inside the level only)
-    const float scale = 1.0f / (float)(s * s);  // 4^-l, exact
-    for (int i = threadIdx.x; i < vw * vh; i += blockDim.x) {
-        const int vy = i / vw, vx = i - vy * vw;
-        const int x = tx0 - 1 + vx, y = ty0 - 1 + vy;
-        float v = 0.f;
-        if (x >= 0 && x < d.W && y >= 0 && y < d.H) {
-            int sum = 0;
-            const unsigned char* b = raw + (vy * s) * rw + vx * s;
-            for (int yy = 0; yy < s; ++yy)
-                for (int xx = 0; xx < s; ++xx) sum += b[yy * rw + xx];
-            v = (float)sum * scale;
-        }
-        val[i] = v;
-    }
-    __syncthreads();
-    // 3. write the tile: I, and Sobel / 8 with clamped neighbours
-    TS* I = reinterpret_cast<TS*>(F.base + d.off_I);
-    TS* Ix = reinterpret_cast<TS*>(F.base + d.off_Ix);
-    TS* Iy = reinterpret_cast<TS*>(F.base + d.off_Iy);
-    for (int i = threadIdx.x; i < tw * th; i += blockDim.x) {
-        const int ty = i / tw, tx = i - ty * tw;
-        const int x = tx0 + tx, y = ty0 + ty;
-        if (x >= d.W || y >= d.H) continue;
-        const size_t o = (size_t)y * d.pitch + x;
-        st(I + o, val[(ty + 1) * vw + tx + 1]);
-        if (F.with_grad) {
-            // region index of a clamped level coordinate
-            const int xm = max(x - 1, 0) - (tx0 - 1), xp = min(x + 1, d.W - 1) - (tx0 - 1);
-            const int ym = max(y - 1, 0) - (ty0 - 1), yp = min(y + 1, d.H - 1) - (ty0 - 1);
-            const int xc = tx + 1, yc = ty + 1;
-            const float gx = (val[ym * vw + xp] - val[ym * vw + xm]) + 2.f * (val[yc * vw + xp] - val[yc * vw + xm]) +
-                             (val[yp * vw + xp] - val[yp * vw + xm]);
-            const float gy = (val[yp * vw + xm] - val[ym * vw + xm]) + 2.f * (val[yp * vw + xc] - val[ym * vw + xc]) +
-                             (val[yp * vw + xp] - val[ym * vw + xp]);
-            st(Ix + o, gx * 0.125f);
-            st(Iy + o, gy * 0.125f);
+        const size_t o = (size_t)y * g.pitch + X0 + tx;
+        if (INTERIOR || X0 + tx + 3 < F.W) {
+            store4<TS>(I + o, vI[0], vI[1], vI[2], vI[3]);
+            if (F.with_grad) {
+                store4<TS>(Ix + o, vx[0], vx[1], vx[2], vx[3]);
+                store4<TS>(Iy + o, vy[0], vy[1], vy[2], vy[3]);
+            }
+        } else {
+            for (int k = 0; k < 4 && X0 + tx + k < F.W; ++k) {
+                st(I + o + k, vI[k]);
+                if (F.with_grad) {
+                    st(Ix + o + k, vx[k]);
+                    st(Iy + o + k, vy[k]);
+                }
+            }
         }
     }
 }
 
-// Shared memory of the most demanding level (the coarsest).
-size_t pyramid_smem(int levels)
+// Levels 1 .. L-1 of the tile: each level's halo'd region as 2x2 means of the
+// previous one, then the tile's I, Ix, Iy from it.
+template <typename TS, bool INTERIOR>
+__device__ __forceinline__ void coarse_levels(const PyrFrame& F, int L, const LevelGeom* geo, unsigned char* smem,
+                                              int RW, int RH, int X0, int Y0, int h)
 {
-    size_t smem = 0;
-    for (int l = 0; l < levels; ++l) {
-        const size_t vw = tile_w(l) + 2, vh = tile_h(l) + 2, s = (size_t)1 << l;
-        const size_t need = round_up(vw * vh * 4, 16) + vw * vh * s * s;
-        smem = smem > need ? smem : need;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const unsigned char* raw = smem;
+    size_t prev_off = 0, cur_off = round16((size_t)RW * RH);
+    for (int l = 1; l < L; ++l) {
+        if (l > 1) {
+            prev_off = cur_off;
+            cur_off += round16((size_t)(RW >> (l - 1)) * (RH >> (l - 1)) * 4);
+        }
+        const LevelGeom& g = geo[l];
+        const int rw = RW >> l, rh = RH >> l, pw = RW >> (l - 1);
+        const int ox = (X0 >> l) - (h >> l), oy = (Y0 >> l) - (h >> l);  // region origin at level l
+        float* cur = reinterpret_cast<float*>(smem + cur_off);
+        const float* prev = reinterpret_cast<const float*>(smem + prev_off);
+        for (int ry = warp; ry < rh; ry += nwarps) {
+            for (int rx = lane; rx < rw; rx += 32) {
+                float v = 0.f;
+                if (INTERIOR || (ox + rx >= 0 && ox + rx < g.W && oy + ry >= 0 && oy + ry < g.H)) {
+                    if (l == 1) {
+                        const unsigned char* b = raw + (2 * ry) * RW + 2 * rx;
+                        v = (float)(((int)b[0] + b[1]) + ((int)b[RW] + b[RW + 1])) * 0.25f;
+                    } else {
+                        const float* b = prev + (2 * ry) * pw + 2 * rx;
+                        v = ((b[0] + b[1]) + (b[pw] + b[pw + 1])) * 0.25f;
+                    }
+                }
+                cur[ry * rw + rx] = v;
+            }
+        }
+        __syncthreads();
+        TS* I = reinterpret_cast<TS*>(F.base + g.off_I);
+        TS* Ix = reinterpret_cast<TS*>(F.base + g.off_Ix);
+        TS* Iy = reinterpret_cast<TS*>(F.base + g.off_Iy);
+        const int tws = 6 - l, tw = kTX >> l, th = kTY >> l, hl = h >> l;  // kTX = 2^6
+        for (int i = threadIdx.x; i < tw * th; i += blockDim.x) {
+            const int ty = i >> tws, tx = i & (tw - 1);
+            const int x = (X0 >> l) + tx, y = (Y0 >> l) + ty;
+            if (!INTERIOR && (x >= g.W || y >= g.H)) continue;
+            const int xc = tx + hl, yc = ty + hl;
+            const int xm = INTERIOR ? xc - 1 : max(x - 1, 0) - ox, xp = INTERIOR ? xc + 1 : min(x + 1, g.W - 1) - ox;
+            const int ym = INTERIOR ? yc - 1 : max(y - 1, 0) - oy, yp = INTERIOR ? yc + 1 : min(y + 1, g.H - 1) - oy;
+            const size_t o = (size_t)y * g.pitch + x;
+            st(I + o, cur[yc * rw + xc]);
+            if (F.with_grad) {
+                const float gx = (cur[ym * rw + xp] - cur[ym * rw + xm]) + 2.f * (cur[yc * rw + xp] - cur[yc * rw + xm]) +
+                                 (cur[yp * rw + xp] - cur[yp * rw + xm]);
+                const float gy = (cur[yp * rw + xm] - cur[ym * rw + xm]) + 2.f * (cur[yp * rw + xc] - cur[ym * rw + xc]) +
+                                 (cur[yp * rw + xp] - cur[ym * rw + xp]);
+                st(Ix + o, gx * 0.125f);
+                st(Iy + o, gy * 0.125f);
+            }
+        }
     }
-    return smem;
+}
+
+template <typename TS, int L>
+__global__ void __launch_bounds__(kThreads) pyramid_kernel(const __grid_constant__ PyrBatch a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ LevelGeom geo[DGF_MAX_LEVELS];
+    __shared__ int frame;
+    if (threadIdx.x < L) {  // one thread per level: find the frame, then its level geometry
+        int f = 0;
+        for (int lo = 0, hi = a.n_frames - 1; lo <= hi;) {
+            const int mid = (lo + hi) >> 1;
+            if (a.frames[mid].cta_begin <= (int)blockIdx.x) {
+                f = mid;
+                lo = mid + 1;
+            } else {
+                hi = mid - 1;
+            }
+        }
+        level_geom(a.frames[f].W, a.frames[f].H, L, (int)sizeof(TS), threadIdx.x, &geo[threadIdx.x]);
+        if (threadIdx.x == 0) frame = f;
+    }
+    __syncthreads();
+    const PyrFrame& F = a.frames[frame];
+    const int t = blockIdx.x - F.cta_begin;
+    const int tiles_x = (F.W + kTX - 1) / kTX;
+    const int X0 = (t % tiles_x) * kTX, Y0 = (t / tiles_x) * kTY;
+    constexpr int h = L >= 2 ? 1 << (L - 1) : 1;
+    constexpr int RW = kTX + 2 * h, RH = kTY + 2 * h;
+    constexpr int NB = (RW * RH + kThreads - 1) / kThreads;  // staged bytes per thread
+    const int gx0 = X0 - h, gy0 = Y0 - h;
+    // the halo'd region inside the frame: no clamping at any level
+    const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + RW <= F.W && gy0 + RH <= F.H;
+
+    // 1. frame bytes under the tile and its halo (outside the frame: 0, never used);
+    // every thread issues all of its loads before its first shared-memory store,
+    // so the CTA waits for one round trip rather than one per byte
+    for (int k0 = 0; k0 < NB; k0 += 16) {  // up to 16 loads in flight per thread
+        unsigned char v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int i = threadIdx.x + (k0 + k) * kThreads;
+            const int ry = i / RW, rx = i - ry * RW;
+            const int gx = gx0 + rx, gy = gy0 + ry;
+            const bool in = k0 + k < NB && i < RW * RH && (interior || (gx >= 0 && gx < F.W && gy >= 0 && gy < F.H));
+            v[k] = in ? __ldg(F.img + (size_t)gy * F.pitch + gx) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int i = threadIdx.x + (k0 + k) * kThreads;
+            if (k0 + k < NB && i < RW * RH) smem[i] = v[k];
+        }
+    }
+    __syncthreads();
+
+    if (interior) {
+        level0<TS, true>(F, geo[0], smem, RW, X0, Y0, h);
+        coarse_levels<TS, true>(F, L, geo, smem, RW, RH, X0, Y0, h);
+    } else {
+        level0<TS, false>(F, geo[0], smem, RW, X0, Y0, h);
+        coarse_levels<TS, false>(F, L, geo, smem, RW, RH, X0, Y0, h);
+    }
 }
 
 // Fills the CTA prefix counts and launches one pyramid build for every frame.
 int launch_pyramids(PyrBatch& a, int storage, cudaStream_t stream)
 {
-    int ctas = 0;
+    long long ctas = 0;
     for (int f = 0; f < a.n_frames; ++f) {
-        a.frames[f].cta_begin = ctas;
-        ctas += frame_ctas(a.frames[f].W, a.frames[f].H, a.levels);
+        a.frames[f].cta_begin = (int)ctas;
+        ctas += frame_ctas(a.frames[f].W, a.frames[f].H);
     }
-    const size_t smem = pyramid_smem(a.levels);
-    if (smem > (size_t)kSmemBytes) return DGF_ERR_ARG;
     if (ctas == 0) return DGF_OK;
-    if (storage == DGF_F32)
-        pyramid_kernel<float><<<ctas, kThreads, smem, stream>>>(a);
-    else
-        pyramid_kernel<__half><<<ctas, kThreads, smem, stream>>>(a);
+    if (ctas > 0x7fffffffLL) return DGF_ERR_ARG;
+    const size_t smem = smem_bytes(a.levels);
+    const unsigned grid = (unsigned)ctas;
+#define DGF_PYR(L)                                                                           \
+    case L:                                                                                  \
+        if (storage == DGF_F32)                                                              \
+            pyramid_kernel<float, L><<<grid, kThreads, smem, stream>>>(a);                  \
+        else                                                                                 \
+            pyramid_kernel<__half, L><<<grid, kThreads, smem, stream>>>(a);                 \
+        break;
+    switch (a.levels) {
+        DGF_PYR(1)
+        DGF_PYR(2)
+        DGF_PYR(3)
+        DGF_PYR(4)
+        DGF_PYR(5)
+        DGF_PYR(6)
+        default:
+            return DGF_ERR_ARG;
+    }
+#undef DGF_PYR
     return launch_status();
 }
 

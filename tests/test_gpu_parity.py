@@ -62,9 +62,9 @@ def test_detect_parity(dgf, size, ww, wh, step):
     assert np.array_equal(sums_g.cpu().numpy().astype(np.int64), sums_o[:, :4])
     err = np.abs(pts_g.cpu().numpy().astype(np.float64) - pts_o).max()
     assert err <= TOL_PTS
-    # exactly rounded: within half an FP32 ulp of the FP64 value
-    half_ulp = np.spacing(np.abs(pts_o).astype(np.float32)).astype(np.float64) / 2
-    assert np.all(np.abs(pts_g.cpu().numpy().astype(np.float64) - pts_o) <= half_ulp + 1e-12)
+    # two correctly rounded FP32 steps (quotient, then origin): within one FP32 ulp
+    ulp = np.spacing(np.abs(pts_o).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(pts_g.cpu().numpy().astype(np.float64) - pts_o) <= ulp)
 
 
 def test_detect_pitched_frame(dgf):
