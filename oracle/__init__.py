@@ -78,6 +78,12 @@ def lib():
         _lib.oracle_rlof_track.argtypes = [P, P, I, I, P, I, ctypes.POINTER(_RlofParams), P, P, P,
                                            P, I]
         _lib.oracle_rlof_track.restype = I
+        _lib.oracle_degraf_detect_f64.argtypes = [P, I, I, I, I, I, P]
+        _lib.oracle_degraf_detect_f64.restype = I
+        _lib.oracle_degraf_vjp.argtypes = [P, I, I, I, I, I, P, P]
+        _lib.oracle_degraf_vjp.restype = I
+        _lib.oracle_rlof_vjp.argtypes = [P, P, I, I, P, I, ctypes.POINTER(_RlofParams), P, P, P, P, P, P, P]
+        _lib.oracle_rlof_vjp.restype = I
         _lib.oracle_max_threads.argtypes = []
         _lib.oracle_max_threads.restype = I
     return _lib
@@ -155,6 +161,51 @@ def rlof_track(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofPara
     if rc:
         raise ValueError("oracle_rlof_track: bad arguments")
     return flow, status, iters, illum
+
+
+def degraf_detect_f64(img: np.ndarray, win_w: int, win_h: int | None = None, step: int = 1):
+    """Key-points of a real-valued image (same definition; for finite differences)."""
+    win_h = win_w if win_h is None else win_h
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    H, W = img.shape
+    pts = np.zeros((degraf_count(W, H, win_w, win_h, step), 2), np.float64)
+    if lib().oracle_degraf_detect_f64(_ptr(img), W, H, win_w, win_h, step, _ptr(pts)):
+        raise ValueError("oracle_degraf_detect_f64: bad arguments")
+    return pts
+
+
+def degraf_vjp(img: np.ndarray, win_w: int, win_h: int | None, step: int, grad_pts: np.ndarray) -> np.ndarray:
+    """sum_k grad_pts[k] . d(point_k)/d(img) as an image (float64 [H, W])."""
+    win_h = win_w if win_h is None else win_h
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    H, W = img.shape
+    g = np.ascontiguousarray(grad_pts, dtype=np.float64).reshape(-1, 2)
+    out = np.zeros((H, W), np.float64)
+    if lib().oracle_degraf_vjp(_ptr(img), W, H, win_w, win_h, step, _ptr(g), _ptr(out)):
+        raise ValueError("oracle_degraf_vjp: bad arguments")
+    return out
+
+
+def rlof_vjp(I1, I2, pts, params: RlofParams, flow, illum, status, grad_flow, grad_illum=None):
+    """Implicit-function VJP of tracking: (grad_I1, grad_I2) float64 [H, W]."""
+    I1 = np.ascontiguousarray(I1, dtype=np.float64)
+    I2 = np.ascontiguousarray(I2, dtype=np.float64)
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+    flow = np.ascontiguousarray(flow, dtype=np.float64).reshape(-1, 2)
+    illum = np.ascontiguousarray(illum, dtype=np.float64).reshape(-1, 2)
+    status = np.ascontiguousarray(status, dtype=np.uint8)
+    gf = np.ascontiguousarray(grad_flow, dtype=np.float64).reshape(-1, 2)
+    gi = None if grad_illum is None else np.ascontiguousarray(grad_illum, dtype=np.float64).reshape(-1, 2)
+    H, W = I1.shape
+    g1 = np.zeros((H, W), np.float64)
+    g2 = np.zeros((H, W), np.float64)
+    prm = params._c()
+    rc = lib().oracle_rlof_vjp(_ptr(I1), _ptr(I2), W, H, _ptr(pts), pts.shape[0], ctypes.byref(prm), _ptr(flow),
+                               _ptr(illum), _ptr(status), _ptr(gf), None if gi is None else _ptr(gi), _ptr(g1),
+                               _ptr(g2))
+    if rc:
+        raise ValueError("oracle_rlof_vjp: bad arguments")
+    return g1, g2
 
 
 def max_threads() -> int:

@@ -435,3 +435,242 @@ int oracle_max_threads(void)
     return 1;
 #endif
 }
+
+/* ---------------------------------------------------------- DeGraF adjoint */
+
+/*
+ * DeGraF on a real-valued image (same definition as oracle_degraf_detect, FP64
+ * sums). Used to take finite differences of the key-points; argmax ties resolve to
+ * the first pixel in row-major order.
+ */
+int oracle_degraf_detect_f64(const double* img, int W, int H, int win_w, int win_h, int step, double* pts)
+{
+    if (!img || W < 1 || H < 1 || win_w < 1 || win_h < 1 || step < 1) return -1;
+    long nu = grid_count(W, win_w, step), nv = grid_count(H, win_h, step);
+    for (long v = 0; v < nv; ++v)
+        for (long u = 0; u < nu; ++u) {
+            long k = v * nu + u, ox = u * step, oy = v * step;
+            double S = 0, X = 0, Y = 0, m = -1e300;
+            for (int i = 0; i < win_h; ++i)
+                for (int j = 0; j < win_w; ++j) {
+                    double I = img[(oy + i) * (long)W + ox + j];
+                    S += I; X += j * I; Y += i * I;
+                    if (I > m) m = I;
+                }
+            double Sn = 0, Xn = 0, Yn = 0;
+            for (int i = 0; i < win_h; ++i)
+                for (int j = 0; j < win_w; ++j) {
+                    double inv = 1 + m - img[(oy + i) * (long)W + ox + j];
+                    Sn += inv; Xn += j * inv; Yn += i * inv;
+                }
+            int use_neg = Sn > S;
+            pts[2 * k] = ox + (use_neg ? Xn / Sn : X / S);
+            pts[2 * k + 1] = oy + (use_neg ? Yn / Sn : Y / S);
+        }
+    return 0;
+}
+
+/*
+ * Vector-Jacobian product of DeGraF: grad_img += sum over key-points k of
+ * grad_pts[k] . d(point_k)/d(img), valid wherever the selection and the window
+ * maximum are locally constant. From Eq. 1: d(x_pos)/dI_ij = (j - x_pos) / S_pos
+ * (likewise y with i). From Eq. 2 with weights 1 + m - I: d(x_neg)/dI_ij =
+ * -(j - x_neg) / S_neg, plus, on the window's first maximum pixel (where m moves
+ * with I), sum_ij (j - x_neg) / S_neg. The window origin is a constant.
+ */
+int oracle_degraf_vjp(const double* img, int W, int H, int win_w, int win_h, int step, const double* grad_pts,
+                      double* grad_img)
+{
+    if (!img || !grad_pts || !grad_img || W < 1 || H < 1 || win_w < 1 || win_h < 1 || step < 1) return -1;
+    long nu = grid_count(W, win_w, step), nv = grid_count(H, win_h, step);
+    for (long v = 0; v < nv; ++v)
+        for (long u = 0; u < nu; ++u) {
+            long k = v * nu + u, ox = u * step, oy = v * step;
+            double S = 0, X = 0, Y = 0, m = -1e300;
+            int ai = 0, aj = 0;
+            for (int i = 0; i < win_h; ++i)
+                for (int j = 0; j < win_w; ++j) {
+                    double I = img[(oy + i) * (long)W + ox + j];
+                    S += I; X += j * I; Y += i * I;
+                    if (I > m) { m = I; ai = i; aj = j; }
+                }
+            double Sn = 0, Xn = 0, Yn = 0;
+            for (int i = 0; i < win_h; ++i)
+                for (int j = 0; j < win_w; ++j) {
+                    double inv = 1 + m - img[(oy + i) * (long)W + ox + j];
+                    Sn += inv; Xn += j * inv; Yn += i * inv;
+                }
+            int use_neg = Sn > S;
+            double gx = grad_pts[2 * k], gy = grad_pts[2 * k + 1];
+            if (!use_neg) {
+                double cx = X / S, cy = Y / S;
+                for (int i = 0; i < win_h; ++i)
+                    for (int j = 0; j < win_w; ++j)
+                        grad_img[(oy + i) * (long)W + ox + j] += (gx * (j - cx) + gy * (i - cy)) / S;
+            } else {
+                double cx = Xn / Sn, cy = Yn / Sn, tot = 0;
+                for (int i = 0; i < win_h; ++i)
+                    for (int j = 0; j < win_w; ++j) {
+                        double d = (gx * (j - cx) + gy * (i - cy)) / Sn;
+                        grad_img[(oy + i) * (long)W + ox + j] -= d;
+                        tot += d;
+                    }
+                grad_img[(oy + ai) * (long)W + ox + aj] += tot;
+            }
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------ RLOF adjoint */
+
+/* Derivative of the Hampel influence function (almost everywhere). */
+static double hampel_dpsi(double r, double a, double b, double c)
+{
+    double ar = fabs(r);
+    if (ar <= a) return 1.0;
+    if (ar <= b) return 0.0;
+    if (ar <= c) return -a / (c - b);
+    return 0.0;
+}
+
+/* Solves the n x n system A x = rhs by Gaussian elimination with partial pivoting.
+ * Returns 0 when A is singular. */
+static int lu_solve(int n, double A[4][4], double rhs[4], double x[4])
+{
+    int perm[4] = {0, 1, 2, 3};
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (A[piv][col] == 0.0) return 0;
+        if (piv != col) {
+            for (int j = 0; j < n; ++j) { double t = A[col][j]; A[col][j] = A[piv][j]; A[piv][j] = t; }
+            double t = rhs[col]; rhs[col] = rhs[piv]; rhs[piv] = t;
+            int tp = perm[col]; perm[col] = perm[piv]; perm[piv] = tp;
+        }
+        for (int r = col + 1; r < n; ++r) {
+            double f = A[r][col] / A[col][col];
+            for (int j = col; j < n; ++j) A[r][j] -= f * A[col][j];
+            rhs[r] -= f * rhs[col];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = rhs[i];
+        for (int j = i + 1; j < n; ++j) s -= A[i][j] * x[j];
+        x[i] = s / A[i][i];
+    }
+    return 1;
+}
+
+/* Adds w * value at the four (clamped) bilinear taps of (x, y) in a W x H plane. */
+static void scatter_bilinear(double* G, int W, int H, double x, double y, double value)
+{
+    double fx0 = floor(x), fy0 = floor(y);
+    int x0 = (int)fx0, y0 = (int)fy0;
+    double ax = x - fx0, ay = y - fy0;
+    int xa = clampi(x0, 0, W - 1), xb = clampi(x0 + 1, 0, W - 1);
+    int ya = clampi(y0, 0, H - 1), yb = clampi(y0 + 1, 0, H - 1);
+    G[(long)ya * W + xa] += (1 - ax) * (1 - ay) * value;
+    G[(long)ya * W + xb] += ax * (1 - ay) * value;
+    G[(long)yb * W + xa] += (1 - ax) * ay * value;
+    G[(long)yb * W + xb] += ax * ay * value;
+}
+
+/*
+ * Vector-Jacobian product of RLOF tracking by implicit differentiation at the
+ * converged level-0 state theta = (d, m, c) (the tracker's reading as in
+ * oracle_rlof_track). The fixed point satisfies F(theta; I1, I2) = sum_k psi(r_k)
+ * a_k = 0, so d(theta)/dI = -A^-1 dF/dI with A = dF/dtheta = sum_k psi'(r_k) a_k
+ * s_k^T, s_k = dr_k/dtheta = (dJ_k/dx, dJ_k/dy, -T_k, -1) (exact derivatives of the
+ * bilinear interpolant of I2). With A^T lambda = (grad_flow, grad_illum):
+ *   grad_I2 += -sum_k psi'(r_k) (lambda . a_k) dJ_k/dI2
+ *   grad_I1 += -sum_k [ mu_T dT_k/dI1 + psi(r_k) (lambda_0 dTx_k/dI1 + lambda_1 dTy_k/dI1) ]
+ *     with mu_T = -(1+m) psi'(r_k) (lambda . a_k) - psi(r_k) lambda_2,
+ * where T, Tx, Ty are bilinear samples of level-0 I1 and its Sobel/8 gradients (the
+ * gradients' adjoint is the transposed Sobel stencil with the clamped border).
+ * Model 2 drops m, c and the T, constant components. Coarse levels only choose
+ * the basin, so they carry no gradient; points not TRACKED get none.
+ * flow, illum, status are the forward outputs; grad_illum may be NULL.
+ */
+int oracle_rlof_vjp(const double* I1, const double* I2, int W, int H, const double* pts, int n,
+                    const oracle_rlof_params* prm, const double* flow, const double* illum, const uint8_t* status,
+                    const double* grad_flow, const double* grad_illum, double* grad_I1, double* grad_I2)
+{
+    if (!I1 || !I2 || W < 1 || H < 1 || n < 0 || !rlof_params_ok(prm) || !grad_I1 || !grad_I2) return -1;
+    const int r = prm->radius, nm = prm->model == 4 ? 4 : 2;
+    double* gT = calloc((size_t)W * H, sizeof(double));   /* adjoint of the template plane */
+    double* gTx = calloc((size_t)W * H, sizeof(double));  /* adjoint of the Sobel-x plane */
+    double* gTy = calloc((size_t)W * H, sizeof(double));
+    double* Ix = malloc(sizeof(double) * (size_t)W * H);
+    double* Iy = malloc(sizeof(double) * (size_t)W * H);
+    double* lev0 = malloc(sizeof(double) * 3 * (size_t)W * H);
+    if (!gT || !gTx || !gTy || !Ix || !Iy || !lev0 || oracle_pyramid(I1, W, H, 1, lev0)) {
+        free(gT); free(gTx); free(gTy); free(Ix); free(Iy); free(lev0);
+        return -1;
+    }
+    memcpy(Ix, lev0 + (long)W * H, sizeof(double) * (size_t)W * H);
+    memcpy(Iy, lev0 + 2L * W * H, sizeof(double) * (size_t)W * H);
+    for (int k = 0; k < n; ++k) {
+        if (status[k] != OR_TRACKED) continue;
+        double px = pts[2 * k], py = pts[2 * k + 1];
+        double qx = px + flow[2 * k], qy = py + flow[2 * k + 1];
+        double m = nm == 4 ? illum[2 * k] : 0, c = nm == 4 ? illum[2 * k + 1] : 0;
+        double A[4][4] = {{0}};
+        for (int ky = -r; ky <= r; ++ky)
+            for (int kx = -r; kx <= r; ++kx) {
+                double T = bilinear(I1, W, H, px + kx, py + ky);
+                double Tx = bilinear(Ix, W, H, px + kx, py + ky), Ty = bilinear(Iy, W, H, px + kx, py + ky);
+                double x = qx + kx, y = qy + ky;
+                double J = bilinear(I2, W, H, x, y);
+                double fx0 = floor(x), fy0 = floor(y), ax = x - fx0, ay = y - fy0;
+                int x0 = (int)fx0, y0 = (int)fy0;
+                double v00 = I2[(long)clampi(y0, 0, H - 1) * W + clampi(x0, 0, W - 1)];
+                double v01 = I2[(long)clampi(y0, 0, H - 1) * W + clampi(x0 + 1, 0, W - 1)];
+                double v10 = I2[(long)clampi(y0 + 1, 0, H - 1) * W + clampi(x0, 0, W - 1)];
+                double v11 = I2[(long)clampi(y0 + 1, 0, H - 1) * W + clampi(x0 + 1, 0, W - 1)];
+                double Jx = (1 - ay) * (v01 - v00) + ay * (v11 - v10);
+                double Jy = (1 - ax) * (v10 - v00) + ax * (v11 - v01);
+                double res = nm == 4 ? J - (1 + m) * T - c : J - T;
+                double dpsi = hampel_dpsi(res, prm->hampel_a, prm->hampel_b, prm->hampel_c);
+                double a[4] = {Tx, Ty, -T, -1}, s[4] = {Jx, Jy, -T, -1};
+                for (int i = 0; i < nm; ++i)
+                    for (int j = 0; j < nm; ++j) A[i][j] += dpsi * a[i] * s[j];
+            }
+        double At[4][4], u[4] = {grad_flow[2 * k], grad_flow[2 * k + 1], 0, 0}, lam[4];
+        if (nm == 4 && grad_illum) { u[2] = grad_illum[2 * k]; u[3] = grad_illum[2 * k + 1]; }
+        for (int i = 0; i < nm; ++i)
+            for (int j = 0; j < nm; ++j) At[i][j] = A[j][i];
+        if (!lu_solve(nm, At, u, lam)) continue;
+        for (int ky = -r; ky <= r; ++ky)
+            for (int kx = -r; kx <= r; ++kx) {
+                double T = bilinear(I1, W, H, px + kx, py + ky);
+                double Tx = bilinear(Ix, W, H, px + kx, py + ky), Ty = bilinear(Iy, W, H, px + kx, py + ky);
+                double x = qx + kx, y = qy + ky;
+                double J = bilinear(I2, W, H, x, y);
+                double res = nm == 4 ? J - (1 + m) * T - c : J - T;
+                double psi = oracle_hampel_psi(res, prm->hampel_a, prm->hampel_b, prm->hampel_c);
+                double dpsi = hampel_dpsi(res, prm->hampel_a, prm->hampel_b, prm->hampel_c);
+                double la = lam[0] * Tx + lam[1] * Ty + (nm == 4 ? -lam[2] * T - lam[3] : 0.0);
+                scatter_bilinear(grad_I2, W, H, x, y, -dpsi * la);
+                double muT = nm == 4 ? -(1 + m) * dpsi * la - psi * lam[2] : -dpsi * la;
+                scatter_bilinear(gT, W, H, px + kx, py + ky, -muT);
+                scatter_bilinear(gTx, W, H, px + kx, py + ky, -psi * lam[0]);
+                scatter_bilinear(gTy, W, H, px + kx, py + ky, -psi * lam[1]);
+            }
+    }
+    /* I1 adjoint: the template plane directly, the gradient planes through the
+     * transposed Sobel / 8 stencil (each output pixel's taps are clamped). */
+    static const int sobel_x[3][3] = {{-1, 0, 1}, {-2, 0, 2}, {-1, 0, 1}};
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            long o = (long)y * W + x;
+            grad_I1[o] += gT[o];
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    long t = (long)clampi(y + dy, 0, H - 1) * W + clampi(x + dx, 0, W - 1);
+                    grad_I1[t] += (sobel_x[dy + 1][dx + 1] * gTx[o] + sobel_x[dx + 1][dy + 1] * gTy[o]) / 8.0;
+                }
+        }
+    free(gT); free(gTx); free(gTy); free(Ix); free(Iy); free(lev0);
+    return 0;
+}
