@@ -185,6 +185,54 @@ int rlof_track(const void* pyr1, const void* pyr2, int W, int H, const float* pt
                const dgf_rlof_params* p, float* flow, uint8_t* status, uint8_t* iters,
                float* illum, cudaStream_t stream);
 
+/* ---- adjoints (gradients with respect to the frames; the paper has none) ---- */
+
+/* Workspace bytes of degraf_detect_backward (one record per key-point). */
+size_t dgf_degraf_backward_workspace(int W, int H, int win_w, int win_h, int step);
+
+/*
+ * Vector-Jacobian product of degraf_detect (Eq. 1-2 differentiated):
+ * grad_img += sum_k grad_pts[k] . d(point_k)/d(img), treating the frame as real
+ * valued. For C_pos: d(x)/dI_ij = (j - x_local) / S_pos (y likewise with i). For
+ * C_neg: -(j - x_local) / S_neg, plus sum_ij (j - x_local) / S_neg on the window's
+ * first maximum pixel in row-major order (m moves with it). Valid wherever the
+ * selection and the maximum do not change.
+ *   img, W, H, pitch, win_w, win_h, step: as given to degraf_detect.
+ *   grad_pts   device, float [N][2].
+ *   workspace  device, 256-byte aligned, ws_bytes >= dgf_degraf_backward_workspace().
+ *   grad_img   device, float, row y at grad_img + y * grad_pitch (elements,
+ *              >= W); accumulated into. Deterministic (gathered, no atomics).
+ */
+int degraf_detect_backward(const uint8_t* img, int W, int H, int pitch, int win_w, int win_h, int step,
+                           const float* grad_pts, void* workspace, size_t ws_bytes, float* grad_img,
+                           int grad_pitch, cudaStream_t stream);
+
+/* Workspace bytes of rlof_track_backward (three W x H float planes). */
+size_t dgf_rlof_backward_workspace(int W, int H);
+
+/*
+ * Vector-Jacobian product of rlof_track by implicit differentiation at the
+ * converged level-0 state theta = (d, m, c): there F = sum_k psi(r_k) a_k = 0, so
+ * d(theta)/dI = -A^-1 dF/dI with A = sum_k psi'(r_k) a_k s_k^T, s_k = dr_k/dtheta
+ * (exact derivatives of the bilinear interpolant of frame 2). With A^T lambda =
+ * (grad_flow, grad_illum): grad_I2 += -sum_k psi'(r_k) (lambda . a_k) dJ_k/dI2, and
+ * grad_I1 collects the template terms through the bilinear weights and the
+ * transposed Sobel / 8 stencil. Coarser levels only select the basin and carry no
+ * gradient; points whose status is not DGF_TRACKED contribute nothing. The key-
+ * points are constants.
+ *   pyr1, pyr2, W, H, pts, n, p: as given to rlof_track; flow, illum, status: its
+ *   outputs (illum required for model 4).
+ *   grad_flow   device, float [n][2]; grad_illum: nullable float [n][2] (model 4).
+ *   workspace   device, 256-byte aligned, >= dgf_rlof_backward_workspace(W, H).
+ *   grad_I1, grad_I2  device, float, row pitch grad_pitch elements; accumulated
+ *               into with atomics (the summation order, and so the last bits, may
+ *               vary between runs).
+ */
+int rlof_track_backward(const void* pyr1, const void* pyr2, int W, int H, const float* pts, int n,
+                        const dgf_rlof_params* p, const float* flow, const float* illum, const uint8_t* status,
+                        const float* grad_flow, const float* grad_illum, void* workspace, size_t ws_bytes,
+                        float* grad_I1, float* grad_I2, int grad_pitch, cudaStream_t stream);
+
 /* ---- batched pipeline (Section 2 over many frame pairs) ------------------- */
 
 /*

@@ -29,6 +29,7 @@ EXPORTS = (
     "dgf_strerror", "dgf_version", "dgf_degraf_count", "degraf_detect", "dgf_pyramid_layout_get",
     "dgf_pyramid_bytes", "pyramid_build", "dgf_rlof_params_default", "dgf_rlof_set_lanes", "rlof_track",
     "dgf_track_many_workspace", "rlof_track_many", "rlof_track_pair_noalloc",
+    "dgf_degraf_backward_workspace", "degraf_detect_backward", "dgf_rlof_backward_workspace", "rlof_track_backward",
 )
 
 
@@ -94,6 +95,14 @@ def load(build_if_missing: bool = True):
     L.dgf_track_many_workspace.restype = Z
     L.rlof_track_many.argtypes = [ctypes.POINTER(PairC), I, ctypes.POINTER(RlofParamsC), P, Z, I, I, P]
     L.rlof_track_many.restype = I
+    L.dgf_degraf_backward_workspace.argtypes = [I, I, I, I, I]
+    L.dgf_degraf_backward_workspace.restype = Z
+    L.degraf_detect_backward.argtypes = [P, I, I, I, I, I, I, P, P, Z, P, I, P]
+    L.degraf_detect_backward.restype = I
+    L.dgf_rlof_backward_workspace.argtypes = [I, I]
+    L.dgf_rlof_backward_workspace.restype = Z
+    L.rlof_track_backward.argtypes = [P, P, I, I, P, I, ctypes.POINTER(RlofParamsC), P, P, P, P, P, P, Z, P, P, I, P]
+    L.rlof_track_backward.restype = I
     L.rlof_track_pair_noalloc.argtypes = [ctypes.POINTER(PairC), ctypes.POINTER(RlofParamsC), P]
     L.rlof_track_pair_noalloc.restype = I
     _lib = L

@@ -150,6 +150,87 @@ def track(pyr1: torch.Tensor, pyr2: torch.Tensor, W: int, H: int, pts: torch.Ten
     return tuple(res)
 
 
+def detect_backward(frame: torch.Tensor, win: int, step: int, grad_pts: torch.Tensor, win_h: int | None = None,
+                    grad_img: torch.Tensor | None = None) -> torch.Tensor:
+    """Adds sum_k grad_pts[k] . d(point_k)/d(frame) into grad_img (float32 [H, W])."""
+    W, H, pitch = _frame(frame)
+    wh = win if win_h is None else win_h
+    if grad_img is None:
+        grad_img = torch.zeros((H, W), dtype=torch.float32, device=frame.device)
+    grad_pts = grad_pts.contiguous().float()
+    ws = torch.empty(int(load().dgf_degraf_backward_workspace(W, H, win, wh, step)), dtype=torch.uint8,
+                     device=frame.device)
+    check("degraf_detect_backward", load().degraf_detect_backward(
+        _ptr(frame), W, H, pitch, win, wh, step, _ptr(grad_pts), _ptr(ws), ws.numel(), _ptr(grad_img),
+        grad_img.stride(0), _stream()))
+    return grad_img
+
+
+def track_backward(pyr1, pyr2, W: int, H: int, pts, params: RlofParams, flow, illum, status, grad_flow,
+                   grad_illum=None, grad_I1=None, grad_I2=None):
+    """Adds the implicit-function VJP of tracking into (grad_I1, grad_I2) float32 [H, W]."""
+    dev = pts.device
+    if grad_I1 is None:
+        grad_I1 = torch.zeros((H, W), dtype=torch.float32, device=dev)
+    if grad_I2 is None:
+        grad_I2 = torch.zeros((H, W), dtype=torch.float32, device=dev)
+    ws = torch.empty(int(load().dgf_rlof_backward_workspace(W, H)), dtype=torch.uint8, device=dev)
+    grad_flow = grad_flow.contiguous().float()
+    gi = grad_illum.contiguous().float() if grad_illum is not None else None
+    prm = params.c()
+    check("rlof_track_backward", load().rlof_track_backward(
+        _ptr(pyr1), _ptr(pyr2), W, H, _ptr(pts), pts.shape[0], ctypes.byref(prm), _ptr(flow), _ptr(illum),
+        _ptr(status), _ptr(grad_flow), _ptr(gi), _ptr(ws), ws.numel(), _ptr(grad_I1), _ptr(grad_I2),
+        grad_I1.stride(0), _stream()))
+    return grad_I1, grad_I2
+
+
+def _as_u8(frame: torch.Tensor) -> torch.Tensor:
+    return frame.detach().round().clamp(0, 255).to(torch.uint8).contiguous()
+
+
+class DeGraFDetect(torch.autograd.Function):
+    """Key-points of a frame given as float intensities (rounded to uint8 for the
+    forward); backward is degraf_detect_backward."""
+
+    @staticmethod
+    def forward(ctx, frame: torch.Tensor, win: int, step: int):
+        u8 = _as_u8(frame)
+        ctx.save_for_backward(u8)
+        ctx.win, ctx.step = win, step
+        return detect(u8, win, step)
+
+    @staticmethod
+    def backward(ctx, grad_pts):
+        (u8,) = ctx.saved_tensors
+        return detect_backward(u8, ctx.win, ctx.step, grad_pts), None, None
+
+
+class RLOFTrack(torch.autograd.Function):
+    """Flow of fixed key-points from frame 1 to frame 2 (float intensities, rounded
+    to uint8 for the forward); backward is rlof_track_backward (gradients for both
+    frames, none for the key-points or the parameters). Returns flow and status."""
+
+    @staticmethod
+    def forward(ctx, frame1: torch.Tensor, frame2: torch.Tensor, pts: torch.Tensor, params: RlofParams):
+        f1, f2 = _as_u8(frame1), _as_u8(frame2)
+        H, W = f1.shape
+        pyr1 = build_pyramid(f1, params.levels, params.storage, True)
+        pyr2 = build_pyramid(f2, params.levels, params.storage, False)
+        pts = pts.detach().contiguous().float()
+        flow, status, illum = track(pyr1, pyr2, W, H, pts, params, with_illum=True)
+        ctx.save_for_backward(pyr1, pyr2, pts, flow, illum, status)
+        ctx.params, ctx.W, ctx.H = params, W, H
+        ctx.mark_non_differentiable(status)
+        return flow, status
+
+    @staticmethod
+    def backward(ctx, grad_flow, grad_status):
+        pyr1, pyr2, pts, flow, illum, status = ctx.saved_tensors
+        g1, g2 = track_backward(pyr1, pyr2, ctx.W, ctx.H, pts, ctx.params, flow, illum, status, grad_flow)
+        return g1, g2, None, None
+
+
 class PairTracker:
     """Device-resident DeGraF + RLOF for frame pairs of one size and parameter set.
 
