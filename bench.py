@@ -164,6 +164,62 @@ def run_batched(dgf, torch, dev, reps: int = 10):
                                "frac_of_measured_hbm": gbs / HBM_PEAK_GBS}}
 
 
+def _timed(torch, dev, fn, reps, flush):
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize(dev)
+    ms = []
+    for k in range(reps):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return float(np.median(ms))
+
+
+def run_fp16(dgf, torch, dev, reps: int = 5):
+    """FP16 pyramid storage against FP32 storage: 32 pairs at 1242x375 (translation
+    flow, window 8, step 4, 3 levels, 9x9) through rlof_track_many."""
+    pairs = [synth.make_pair(4, index=i) for i in range(32)]
+    d1 = [torch.from_numpy(p.I1).to(dev) for p in pairs]
+    d2 = [torch.from_numpy(p.I2).to(dev) for p in pairs]
+    specs = [(pairs[0].W, pairs[0].H, 8, 4)] * 32
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {"workload": "32 pairs 1242x375, translation flow, window 8, step 4, 3 levels, 9x9, model 4"}
+    for name, storage in (("f32", dgf.F32), ("f16", dgf.F16)):
+        bt = dgf.BatchTracker(specs, dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4, storage=storage), dev)
+        t = _timed(torch, dev, lambda: bt.run(d1, d2, use_graph=True), reps, flush)
+        out[name] = {"ms_per_batch": t, "points_per_s": sum(bt.n) / (t / 1e3)}
+    out["f16_speedup"] = out["f32"]["ms_per_batch"] / out["f16"]["ms_per_batch"]
+    return out
+
+
+def run_adjoint(dgf, torch, dev, reps: int = 5):
+    """Forward + implicit adjoint of tracking for 8 pairs at 1242x375 (step 4, 3
+    levels, 9x9, model 4), loss = sum of w . flow with w ~ N(0, 1) per point."""
+    pairs = [synth.make_pair(5, index=i) for i in range(8)]
+    prm = dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)
+    frames = [(torch.from_numpy(p.I1).float().to(dev), torch.from_numpy(p.I2).float().to(dev)) for p in pairs]
+    pts = [dgf.detect(torch.from_numpy(p.I1).to(dev), 8, 4) for p in pairs]
+    ws = [torch.randn(pt.shape, device=dev) for pt in pts]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        for (f1, f2), pt, w in zip(frames, pts, ws):
+            a = f1.detach().requires_grad_(True)
+            b = f2.detach().requires_grad_(True)
+            flow, _ = dgf.RLOFTrack.apply(a, b, pt, prm)
+            (flow * w).sum().backward()
+
+    t = _timed(torch, dev, step, reps, flush)
+    return {"workload": "8 pairs 1242x375, step 4, 3 levels, 9x9, model 4: forward + implicit adjoint (torch autograd)",
+            "ms_per_8_pairs": t, "pairs_per_s": 8 / (t / 1e3)}
+
+
 def cpu_baseline(pair, reps: int = 2):
     """The FP64 oracle as it stands, on this host's cores, over the full pair."""
     import oracle
@@ -330,6 +386,8 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
                 "clocks": clocks.summary()}
         if not args.no_batched:
             line["batched"] = run_batched(dgf, torch, dev)
+            line["fp16_storage"] = run_fp16(dgf, torch, dev)
+            line["adjoint"] = run_adjoint(dgf, torch, dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pair)
         print(json.dumps(line), flush=True)
@@ -344,7 +402,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batched", action="store_true", help="skip the 64-pair batch section")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batch, FP16-storage and adjoint sections")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per tracked point (0 = automatic)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

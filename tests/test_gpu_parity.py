@@ -178,17 +178,26 @@ def test_track_parity_shapes(dgf, radius, levels, n, model):
     assert np.sum(e[both] > TOL_FLOW) <= max(1, 0.01 * both.sum())
 
 
-def test_track_fp16_storage_error(dgf):
-    """FP16 storage: endpoint error against the FP64 oracle is reported, not barred;
-    the converged points must stay close."""
-    p = synth.make_pair(1)
+@pytest.mark.parametrize("config", [1, 4])
+def test_track_fp16_storage_error(dgf, config):
+    """FP16 storage: endpoint error against the FP64 oracle is reported beside the
+    FP32-storage error on the same points (no fixed bar; the converged points must
+    stay close)."""
+    p = synth.make_pair(config)
     pts, _, _ = oracle.degraf_detect(p.I1, p.win, p.win, p.step)
+    if config == 4:
+        pts = pts[::7]  # a sample of the 1242x375 pair keeps the oracle fast
     prm = oracle.RlofParams(levels=p.levels, radius=p.radius, model=4)
-    (fg, sg, _, _), (fo, so, _, _) = run_both(dgf, p.I1, p.I2, pts, prm, storage=1)
-    agree, both, e = compare_tracks(fg, sg, fo, so)
-    print(f"fp16 storage: status agree {agree:.4f}, median epe {np.median(e[both]):.2e}, "
-          f"p99 {np.percentile(e[both], 99):.2e}")
-    assert agree >= 0.98 and np.median(e[both]) < 0.05
+    res = {}
+    for storage in (0, 1):
+        (fg, sg, _, _), (fo, so, _, _) = run_both(dgf, p.I1, p.I2, pts, prm, storage=storage)
+        agree, both, e = compare_tracks(fg, sg, fo, so)
+        res[storage] = (agree, both, e)
+        print(f"workload {config} storage {'f16' if storage else 'f32'}: status agree {agree:.4f}, "
+              f"EPE vs FP64 oracle on converged points: mean {e[both].mean():.2e} median {np.median(e[both]):.2e} "
+              f"p99 {np.percentile(e[both], 99):.2e} max {e[both].max():.2e}")
+    agree, both, e = res[1]
+    assert agree >= 0.97 and np.median(e[both]) < 0.05
 
 
 def test_track_exact_shift(dgf):
