@@ -108,25 +108,48 @@ __global__ void __launch_bounds__(256) degraf_detect_kernel(const __grid_constan
     const int tile_w = (kBX - 1) * J.step + a.ww, tile_h = ((int)blockDim.y - 1) * J.step + a.wh;
     const int stride = a.tile_w;  // row stride of the staged tile (multiple of 4)
     if (a.staged) {
-        // stage the pixels under the CTA's windows: a thread owns columns tx, tx+32, ..
-        // of rows ty, ty+BY, ..; per column it issues all its row loads before storing
+        // stage the pixels under the CTA's windows as aligned 32-bit words: per row
+        // the word under each 4-byte group and, for a misaligned row, the next word
+        // (only if it still holds a byte of the tile, so no load leaves the frame),
+        // funnel-shifted; 4 rows x 2 words per thread in flight at a time
         const int tw = min(tile_w, J.W - x0), th = min(tile_h, J.H - y0);
-        for (int c = threadIdx.x; c < tw; c += blockDim.x) {
-            const uint8_t* src = J.img + (size_t)y0 * J.pitch + x0 + c;
-            uint8_t v[8];
+        const int nw = (tw + 3) >> 2;
+        unsigned* tile32 = reinterpret_cast<unsigned*>(tile);
+        for (int r0 = threadIdx.y; r0 < th; r0 += 4 * blockDim.y) {
+            unsigned lo[4][2], hi[4][2], sh[4];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int r = threadIdx.y + k * blockDim.y;
-                v[k] = r < th ? __ldg(src + (size_t)r * J.pitch) : 0;
+            for (int i = 0; i < 4; ++i) {
+                const int r = r0 + i * blockDim.y;
+                const uintptr_t src = reinterpret_cast<uintptr_t>(J.img + (size_t)(y0 + min(r, th - 1)) * J.pitch + x0);
+                const unsigned a = (unsigned)(src & 3u);
+                const unsigned* w = reinterpret_cast<const unsigned*>(src & ~(uintptr_t)3);
+                sh[i] = a * 8u;
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int k = threadIdx.x + 32 * m;
+                    const bool ok = r < th && k < nw;
+                    lo[i][m] = ok ? __ldg(w + k) : 0u;
+                    hi[i][m] = ok && a && 4 * (k + 1) - (int)a < tw ? __ldg(w + k + 1) : 0u;
+                }
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int r = threadIdx.y + k * blockDim.y;
-                if (r < th) tile[r * stride + c] = v[k];
+            for (int i = 0; i < 4; ++i) {
+                const int r = r0 + i * blockDim.y;
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int k = threadIdx.x + 32 * m;
+                    if (r < th && k < nw) tile32[r * (stride >> 2) + k] = __funnelshift_r(lo[i][m], hi[i][m], sh[i]);
+                }
             }
-            for (int r = threadIdx.y + 8 * blockDim.y; r < th; r += blockDim.y)  // tall tiles (by < 8)
-                tile[r * stride + c] = __ldg(src + (size_t)r * J.pitch);
         }
+        for (int k = 64 + threadIdx.x; k < nw; k += 32)  // rows wider than 256 bytes (large steps)
+            for (int r = threadIdx.y; r < th; r += blockDim.y) {
+                const uintptr_t src = reinterpret_cast<uintptr_t>(J.img + (size_t)(y0 + r) * J.pitch + x0);
+                const unsigned a = (unsigned)(src & 3u);
+                const unsigned* w = reinterpret_cast<const unsigned*>(src & ~(uintptr_t)3);
+                const unsigned lo = __ldg(w + k), hi = a && 4 * (k + 1) - (int)a < tw ? __ldg(w + k + 1) : 0u;
+                tile32[r * (stride >> 2) + k] = __funnelshift_r(lo, hi, a * 8u);
+            }
         __syncthreads();
     }
     const int u = u0 + threadIdx.x, v = v0 + threadIdx.y;

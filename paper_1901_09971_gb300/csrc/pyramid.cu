@@ -130,14 +130,17 @@ __device__ __forceinline__ void level0(const PyrFrame& F, const LevelGeom& g, co
 }
 
 // Levels 1 .. L-1 of the tile: each level's halo'd region as 2x2 means of the
-// previous one, then the tile's I, Ix, Iy from it.
-template <typename TS, bool INTERIOR>
-__device__ __forceinline__ void coarse_levels(const PyrFrame& F, int L, const LevelGeom* geo, unsigned char* smem,
-                                              int RW, int RH, int X0, int Y0, int h)
+// previous one, then the tile's I, Ix, Iy from it. The level loop unrolls, so every
+// region size is a compile-time constant (flat loops, constant divisors).
+template <typename TS, bool INTERIOR, int L>
+__device__ __forceinline__ void coarse_levels(const PyrFrame& F, const LevelGeom* geo, unsigned char* smem, int X0,
+                                              int Y0)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    constexpr int h = L >= 2 ? 1 << (L - 1) : 1;
+    constexpr int RW = kTX + 2 * h, RH = kTY + 2 * h;
     const unsigned char* raw = smem;
     size_t prev_off = 0, cur_off = round16((size_t)RW * RH);
+#pragma unroll
     for (int l = 1; l < L; ++l) {
         if (l > 1) {
             prev_off = cur_off;
@@ -145,31 +148,31 @@ __device__ __forceinline__ void coarse_levels(const PyrFrame& F, int L, const Le
         }
         const LevelGeom& g = geo[l];
         const int rw = RW >> l, rh = RH >> l, pw = RW >> (l - 1);
-        const int ox = (X0 >> l) - (h >> l), oy = (Y0 >> l) - (h >> l);  // region origin at level l
+        const int hl = h >> l;
+        const int ox = (X0 >> l) - hl, oy = (Y0 >> l) - hl;  // region origin at level l
         float* cur = reinterpret_cast<float*>(smem + cur_off);
         const float* prev = reinterpret_cast<const float*>(smem + prev_off);
-        for (int ry = warp; ry < rh; ry += nwarps) {
-            for (int rx = lane; rx < rw; rx += 32) {
-                float v = 0.f;
-                if (INTERIOR || (ox + rx >= 0 && ox + rx < g.W && oy + ry >= 0 && oy + ry < g.H)) {
-                    if (l == 1) {
-                        const unsigned char* b = raw + (2 * ry) * RW + 2 * rx;
-                        v = (float)(((int)b[0] + b[1]) + ((int)b[RW] + b[RW + 1])) * 0.25f;
-                    } else {
-                        const float* b = prev + (2 * ry) * pw + 2 * rx;
-                        v = ((b[0] + b[1]) + (b[pw] + b[pw + 1])) * 0.25f;
-                    }
+        for (int i = threadIdx.x; i < rw * rh; i += kThreads) {
+            const int ry = i / rw, rx = i - ry * rw;
+            float v = 0.f;
+            if (INTERIOR || (ox + rx >= 0 && ox + rx < g.W && oy + ry >= 0 && oy + ry < g.H)) {
+                if (l == 1) {
+                    const unsigned char* b = raw + (2 * ry) * RW + 2 * rx;
+                    v = (float)(((int)b[0] + b[1]) + ((int)b[RW] + b[RW + 1])) * 0.25f;
+                } else {
+                    const float* b = prev + (2 * ry) * pw + 2 * rx;
+                    v = ((b[0] + b[1]) + (b[pw] + b[pw + 1])) * 0.25f;
                 }
-                cur[ry * rw + rx] = v;
             }
+            cur[i] = v;
         }
         __syncthreads();
         TS* I = reinterpret_cast<TS*>(F.base + g.off_I);
         TS* Ix = reinterpret_cast<TS*>(F.base + g.off_Ix);
         TS* Iy = reinterpret_cast<TS*>(F.base + g.off_Iy);
-        const int tws = 6 - l, tw = kTX >> l, th = kTY >> l, hl = h >> l;  // kTX = 2^6
-        for (int i = threadIdx.x; i < tw * th; i += blockDim.x) {
-            const int ty = i >> tws, tx = i & (tw - 1);
+        const int tw = kTX >> l, th = kTY >> l;
+        for (int i = threadIdx.x; i < tw * th; i += kThreads) {
+            const int ty = i / tw, tx = i - ty * tw;
             const int x = (X0 >> l) + tx, y = (Y0 >> l) + ty;
             if (!INTERIOR && (x >= g.W || y >= g.H)) continue;
             const int xc = tx + hl, yc = ty + hl;
@@ -224,30 +227,59 @@ __global__ void __launch_bounds__(kThreads) pyramid_kernel(const __grid_constant
     // 1. frame bytes under the tile and its halo (outside the frame: 0, never used);
     // every thread issues all of its loads before its first shared-memory store,
     // so the CTA waits for one round trip rather than one per byte
-    for (int k0 = 0; k0 < NB; k0 += 16) {  // up to 16 loads in flight per thread
-        unsigned char v[16];
+    if (interior && RW % 4 == 0) {
+        // rows as aligned 32-bit words: the word under each 4-byte group of the row
+        // and the next one, funnel-shifted by the row's misalignment (an aligned
+        // word that holds any byte of the frame lies inside its allocation)
+        constexpr int NW = RW / 4;                           // words per region row (<= 32)
+        constexpr int NR = (RH + kThreads / 32 - 1) / (kThreads / 32);  // rows per warp
+        static_assert(NW <= 32, "one word per lane and row");
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        unsigned lo[NR], hi[NR], shift[NR];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int i = threadIdx.x + (k0 + k) * kThreads;
-            const int ry = i / RW, rx = i - ry * RW;
-            const int gx = gx0 + rx, gy = gy0 + ry;
-            const bool in = k0 + k < NB && i < RW * RH && (interior || (gx >= 0 && gx < F.W && gy >= 0 && gy < F.H));
-            v[k] = in ? __ldg(F.img + (size_t)gy * F.pitch + gx) : 0;
+        for (int i = 0; i < NR; ++i) {  // every load of the warp in flight before any store
+            const int ry = warp + i * (kThreads / 32);
+            lo[i] = hi[i] = shift[i] = 0u;
+            if (ry < RH && lane < NW) {
+                const uintptr_t src = reinterpret_cast<uintptr_t>(F.img + (size_t)(gy0 + ry) * F.pitch + gx0);
+                const unsigned* w = reinterpret_cast<const unsigned*>(src & ~(uintptr_t)3);
+                shift[i] = (unsigned)(src & 3u) * 8u;
+                lo[i] = __ldg(w + lane);
+                if (shift[i]) hi[i] = __ldg(w + lane + 1);
+            }
         }
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int i = threadIdx.x + (k0 + k) * kThreads;
-            if (k0 + k < NB && i < RW * RH) smem[i] = v[k];
+        for (int i = 0; i < NR; ++i) {
+            const int ry = warp + i * (kThreads / 32);
+            if (ry < RH && lane < NW)
+                reinterpret_cast<unsigned*>(smem + ry * RW)[lane] = __funnelshift_r(lo[i], hi[i], shift[i]);
+        }
+    } else {
+        for (int k0 = 0; k0 < NB; k0 += 16) {  // up to 16 byte loads in flight per thread
+            unsigned char v[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int i = threadIdx.x + (k0 + k) * kThreads;
+                const int ry = i / RW, rx = i - ry * RW;
+                const int gx = gx0 + rx, gy = gy0 + ry;
+                const bool in = k0 + k < NB && i < RW * RH && (interior || (gx >= 0 && gx < F.W && gy >= 0 && gy < F.H));
+                v[k] = in ? __ldg(F.img + (size_t)gy * F.pitch + gx) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int i = threadIdx.x + (k0 + k) * kThreads;
+                if (k0 + k < NB && i < RW * RH) smem[i] = v[k];
+            }
         }
     }
     __syncthreads();
 
     if (interior) {
         level0<TS, true>(F, geo[0], smem, RW, X0, Y0, h);
-        coarse_levels<TS, true>(F, L, geo, smem, RW, RH, X0, Y0, h);
+        coarse_levels<TS, true, L>(F, geo, smem, X0, Y0);
     } else {
         level0<TS, false>(F, geo[0], smem, RW, X0, Y0, h);
-        coarse_levels<TS, false>(F, L, geo, smem, RW, RH, X0, Y0, h);
+        coarse_levels<TS, false, L>(F, geo, smem, X0, Y0);
     }
 }
 
