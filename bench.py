@@ -272,6 +272,7 @@ def run_reference(args, rank: int, world: int):
 def run_cuda(args, rank: int, world: int, local_rank: int):
     import torch
     import paper_1901_09971_gb300 as dgf
+    from paper_1901_09971_gb300 import shard
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -318,10 +319,7 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
     step_ms = np.array([e[0].elapsed_time(e[2]) for e in evs])
     rlof_ms = np.array([e[1].elapsed_time(e[2]) for e in evs])
     total_s = step_ms.sum() / 1e3
-    if dist:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = shard.reduce_scalar(total_s, "max", device=dev)  # slowest rank
     n_pts = tr.n
     value = world * n_pts * args.steps / total_s
 
@@ -361,10 +359,7 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
         b.synchronize()
         e_ms.append(a.elapsed_time(b))
     e2e_s = sum(e_ms) / 1e3
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = shard.reduce_scalar(e2e_s, "max", device=dev)
     e2e_value = world * n_pts * args.steps / e2e_s
 
     if rank == 0:
