@@ -269,7 +269,8 @@ class BatchTracker:
     ``specs`` is a list of (W, H, win, step). Outputs (points, flow, status,
     iterations) and the workspace are allocated once; ``run`` takes lists of
     uint8 frames (device tensors of the spec sizes) and enqueues one
-    rlof_track_many call (optionally replayed from a captured CUDA graph).
+    rlof_track_many call (optionally replayed from a captured CUDA graph);
+    ``bind`` + ``run()`` reuse validated descriptors of fixed frame buffers.
     """
 
     def __init__(self, specs, params: RlofParams, device: torch.device | str = "cuda"):
@@ -288,6 +289,7 @@ class BatchTracker:
         if nbytes == 0:
             raise _abi.DegrafError("dgf_track_many_workspace", _abi.DGF_ERR_ARG, "invalid batch")
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self._arr = None
 
     def _descriptors(self, frames1, frames2, probe=False):
         arr = (_abi.PairC * len(self.specs))()
@@ -306,9 +308,19 @@ class BatchTracker:
                                 self.status[i].data_ptr(), self.iters[i].data_ptr())
         return arr
 
-    def run(self, frames1, frames2, use_graph: bool = True, stages: int = _abi.STAGE_ALL):
-        arr = self._descriptors(frames1, frames2)
-        check("rlof_track_many", load().rlof_track_many(arr, len(self.specs), ctypes.byref(self._prm),
+    def bind(self, frames1, frames2):
+        """Validates the frames and builds the pair descriptors once. The tracker
+        keeps references to the frames, so their memory stays valid; later
+        ``run()`` calls without frames track whatever the frames then hold."""
+        self._bound = (list(frames1), list(frames2))
+        self._arr = self._descriptors(*self._bound)
+
+    def run(self, frames1=None, frames2=None, use_graph: bool = True, stages: int = _abi.STAGE_ALL):
+        if frames1 is not None or frames2 is not None:
+            self.bind(frames1, frames2)
+        elif getattr(self, "_arr", None) is None:
+            raise ValueError("run() without frames needs frames bound first")
+        check("rlof_track_many", load().rlof_track_many(self._arr, len(self.specs), ctypes.byref(self._prm),
                                                         _ptr(self.workspace), self.workspace.numel(), int(stages),
                                                         int(use_graph), _stream()))
         return self.pts, self.flow, self.status, self.iters

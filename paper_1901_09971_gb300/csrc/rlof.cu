@@ -3,26 +3,34 @@
 //
 // Work mapping: a group of G consecutive lanes (G = 8, 16 or 32) owns one point
 // for its whole coarse-to-fine trajectory. The (2r+1)^2 support is cut into
-// (2r+1) x (r+1) horizontal sample pairs (the second sample of the last pair
-// column is masked out); lane l of a group owns pairs l, l + G, l + 2G, ... Both
-// samples of a pair share the bilinear weights of the iterate and four of their
-// six taps, so a pair is sampled with four loads (an 8-byte and a 4-byte load per
-// tap row, chosen by the parity of the tap block's first column) and evaluated
-// with packed FP32x2 instructions (fma.rn.f32x2 and friends on sm_100+).
-// The template T, Tx, Ty of the current level stays in registers for all of the
-// level's iterations (shared memory would add to the L1 data-pipe traffic that
-// the tap loads and shuffles already load heavily). Per iteration every lane
-// forms Hampel weights and its partial sums of the 4x4 (or 2x2) normal
-// equations, the group reduces them with xor shuffles (the butterfly leaves
-// bit-identical sums in every lane), and the FP32 Cholesky solve, the update and
-// the convergence test run redundantly, so each group's control flow stays
-// uniform and points converge and exit independently.
+// sample pairs that share the bilinear weights of the iterate and four of their
+// six taps, so a pair is sampled with four loads and evaluated with packed FP32x2
+// instructions (fma.rn.f32x2 and friends on sm_100+). For radius 4 and 5 the
+// first 2r columns form horizontal pairs and the last column vertical ones (radius
+// 5: 61 pairs, four slots of 16 lanes); other radii use (2r+1) x (r+1) horizontal
+// pairs whose last column's second sample is masked out. Lane l of a group owns
+// pairs l, l + G, l + 2G, ...
+//
+// The template T, Tx, Ty of the current level is sampled once per level into
+// shared memory (one 16-byte and one 8-byte slot per pair, read back without
+// bank conflicts), which leaves the registers to the accumulators and the taps in
+// flight. Per iteration every lane forms Hampel weights and its partial sums of
+// the 4x4 (or 2x2) normal equations; the group reduces the 4x4 sums through a
+// per-warp shared-memory scratch (bit-identical totals in every lane), and the
+// FP32 solve, the update and the convergence test run redundantly, so each
+// group's control flow stays uniform and points converge and exit independently.
+//
+// Time per iteration splits roughly 70% per-sample accumulation, 18% group
+// reduction, 5% solve: the kernel is bound by instruction issue and dependency
+// latency on the FP32 and integer pipes, not by memory (the pyramids stay in L1/L2).
 #include "common.cuh"
 #include "batch.cuh"
 
 namespace rlof_detail {
 
 using dgf::TrackBatch;
+
+constexpr int kThreads = 128;
 
 template <int G>
 __device__ __forceinline__ float group_sum(float v, unsigned mask)
@@ -32,38 +40,67 @@ __device__ __forceinline__ float group_sum(float v, unsigned mask)
     return v;
 }
 
-// Sum of 16 values over a group of G lanes, returned in every lane (h[k] = total of
-// v[k] over the group). Reduce-scatter: at each stage the lane keeps the half of its
-// values its partner does not, adding the partner's copy, so 16 + 8 + 4 + ... values
-// cross lanes instead of 16 per butterfly stage; then the 16 totals, spread one or
-// two per lane, are gathered with indexed shuffles. Sums run in a fixed order per
-// value, so every lane receives bit-identical totals.
-template <int G>
-__device__ __forceinline__ void group_allreduce16(float (&v)[16], float (&h)[16], unsigned mask, int lane)
+// Per-warp scratch of the group reduction: one row of 16 partial sums per lane and
+// 16 totals per group. Rows are 20 floats apart, so the 16-byte accesses of eight
+// consecutive lanes start in distinct quads of banks.
+constexpr int kRowStride = 20;
+struct alignas(16) WarpScratch {
+    float rows[32 * kRowStride];
+    float totals[4 * 16];
+};
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b)
 {
+    const float2 lo = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    const float2 hi = __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// Sum of 16 values over a group of G lanes, returned in every lane (h[k] = total of
+// v[k] over the group). Every lane stores its values as a row; lane l adds value
+// block l & 3 (values 4 (l & 3) .. +3) over the four rows 4 (l >> 2) .. +3 of its
+// group; the G / 4 lanes holding the same block combine their partial sums with
+// xor shuffles; lanes 0..3 publish the four block totals, which every lane of the
+// group then reads back, so all lanes receive the same bits. Groups of a warp use
+// disjoint rows and totals, so diverged groups never meet at a barrier.
+template <int G>
+__device__ __forceinline__ void group_allreduce16(const float (&v)[16], float (&h)[16], unsigned mask, int lane,
+                                                  WarpScratch& ws)
+{
+    const int wl = threadIdx.x & 31;
+    const int g0 = wl - lane;  // warp lane of the group's lane 0
+    float4* row = reinterpret_cast<float4*>(ws.rows + wl * kRowStride);
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int o = (G >> 1) >> s;  // partner offset of this stage
-        const int n = 16 >> s;        // values still held per lane
-        if (o >= 1) {
-            const bool up = (lane & o) != 0;
+    for (int i = 0; i < 4; ++i) row[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    __syncwarp(mask);
+    const int blk = lane & 3;
+    const float* src = ws.rows + (g0 + 4 * (lane >> 2)) * kRowStride + 4 * blk;
+    float4 s = *reinterpret_cast<const float4*>(src);
 #pragma unroll
-            for (int i = 0; i < n / 2; ++i) {
-                const float send = up ? v[i] : v[i + n / 2];
-                const float keep = up ? v[i + n / 2] : v[i];
-                v[i] = keep + __shfl_xor_sync(mask, send, o);
-            }
-        }
+    for (int i = 1; i < 4; ++i) s = add4(s, *reinterpret_cast<const float4*>(src + i * kRowStride));
+#pragma unroll
+    for (int o = 4; o < G; o <<= 1) {
+        float4 t;
+        t.x = __shfl_xor_sync(mask, s.x, o);
+        t.y = __shfl_xor_sync(mask, s.y, o);
+        t.z = __shfl_xor_sync(mask, s.z, o);
+        t.w = __shfl_xor_sync(mask, s.w, o);
+        s = add4(s, t);
     }
-    if (G == 32) v[0] += __shfl_xor_sync(mask, v[0], 1);
-    // total k now sits in lane k (G = 16), in lane k / 2 element k % 2 (G = 8), or
-    // in lanes 2k and 2k + 1 (G = 32)
+    float4* tot = reinterpret_cast<float4*>(ws.totals + (g0 / G) * 16);
+    if (lane < 4) tot[blk] = s;
+    __syncwarp(mask);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        if (G == 16) h[k] = __shfl_sync(mask, v[0], k, 16);
-        if (G == 8) h[k] = __shfl_sync(mask, v[k & 1], k >> 1, 8);
-        if (G == 32) h[k] = __shfl_sync(mask, v[0], 2 * k, 32);
+    for (int i = 0; i < 4; ++i) {
+        const float4 t = tot[i];
+        h[4 * i] = t.x;
+        h[4 * i + 1] = t.y;
+        h[4 * i + 2] = t.z;
+        h[4 * i + 3] = t.w;
     }
+    // ordering across calls: each lane reads the rows before the second
+    // __syncwarp above, which precedes the next call's row stores, and reads the
+    // totals before the next call's first __syncwarp, which precedes their rewrite
 }
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
@@ -126,6 +163,29 @@ __device__ __forceinline__ float2 pair_clamped(const TS* P, int pitch, int W, in
                          dgf::ld(r1 + xb), dgf::ld(r1 + xc));
 }
 
+// Two vertically adjacent bilinear samples from their 3x2 taps (a0 a1 / b0 b1 / c0 c1).
+__device__ __forceinline__ float2 bilinear_vpair(const PairWeights& w, float a0, float a1, float b0, float b1,
+                                                 float c0, float c1)
+{
+    float2 J = __fmul2_rn(w.w00, make_float2(a0, b0));
+    J = __ffma2_rn(w.w01, make_float2(a1, b1), J);
+    J = __ffma2_rn(w.w10, make_float2(b0, c0), J);
+    return __ffma2_rn(w.w11, make_float2(b1, c1), J);
+}
+
+// Vertical sample pair at integer tap origin (xi, yi) with every tap clamped.
+template <typename TS>
+__device__ __forceinline__ float2 vpair_clamped(const TS* P, int pitch, int W, int H, int xi, int yi,
+                                                const PairWeights& w)
+{
+    const int xa = min(max(xi, 0), W - 1), xb = min(max(xi + 1, 0), W - 1);
+    const TS* r0 = P + (size_t)min(max(yi, 0), H - 1) * pitch;
+    const TS* r1 = P + (size_t)min(max(yi + 1, 0), H - 1) * pitch;
+    const TS* r2 = P + (size_t)min(max(yi + 2, 0), H - 1) * pitch;
+    return bilinear_vpair(w, dgf::ld(r0 + xa), dgf::ld(r0 + xb), dgf::ld(r1 + xa), dgf::ld(r1 + xb), dgf::ld(r2 + xa),
+                          dgf::ld(r2 + xb));
+}
+
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float y;
@@ -141,6 +201,44 @@ __device__ __forceinline__ float hampel_weight(float r, float ha, float icb, flo
     const float ar = fabsf(r);
     const float w = __saturatef(ha * rcp_approx(ar));
     return w * __saturatef(fmaf(-ar, icb, hc_icb));
+}
+
+__device__ __forceinline__ float rcp_approx_denorm(float x)
+{
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Solve of the symmetric positive definite 4 x 4 system [[A, B], [B^T, C]] x = r
+// (2 x 2 blocks) by block elimination: with the Schur complement S = C - B^T A^-1 B,
+// x1 = S^-1 (r1 - B^T A^-1 r0) and x0 = A^-1 r0 - (A^-1 B) x1, the 2 x 2 inverses
+// taken from their adjugates. The Cholesky pivots are a00, det A / a00, s00 and
+// det S / s00, so the positivity test is the same as Cholesky's; returns false on
+// failure. Its dependency chain is shorter than the sequential factorisation's.
+__device__ __forceinline__ bool block_solve4(const float (&H)[4][4], const float (&r)[4], float (&x)[4])
+{
+    const float a00 = H[0][0], a01 = H[0][1], a11 = H[1][1];
+    const float dA = fmaf(a00, a11, -a01 * a01);
+    if (!(a00 > 0.f) || !(dA > 0.f)) return false;
+    const float iA = rcp_approx_denorm(dA);
+    const float i00 = a11 * iA, i01 = -a01 * iA, i11 = a00 * iA;  // A^-1
+    const float b00 = H[0][2], b01 = H[0][3], b10 = H[1][2], b11 = H[1][3];
+    const float x00 = fmaf(i00, b00, i01 * b10), x01 = fmaf(i00, b01, i01 * b11);  // X = A^-1 B
+    const float x10 = fmaf(i01, b00, i11 * b10), x11 = fmaf(i01, b01, i11 * b11);
+    const float s00 = H[2][2] - fmaf(b00, x00, b10 * x10);  // S = C - B^T X
+    const float s01 = H[2][3] - fmaf(b00, x01, b10 * x11);
+    const float s11 = H[3][3] - fmaf(b01, x01, b11 * x11);
+    const float dS = fmaf(s00, s11, -s01 * s01);
+    if (!(s00 > 0.f) || !(dS > 0.f)) return false;
+    const float iS = rcp_approx_denorm(dS);
+    const float y0 = fmaf(i00, r[0], i01 * r[1]), y1 = fmaf(i01, r[0], i11 * r[1]);  // A^-1 r0
+    const float t0 = r[2] - fmaf(b00, y0, b10 * y1), t1 = r[3] - fmaf(b01, y0, b11 * y1);
+    x[2] = fmaf(s11, t0, -s01 * t1) * iS;
+    x[3] = fmaf(s00, t1, -s01 * t0) * iS;
+    x[0] = y0 - fmaf(x00, x[2], x01 * x[3]);
+    x[1] = y1 - fmaf(x10, x[2], x11 * x[3]);
+    return true;
 }
 
 // Cholesky solve of the symmetric positive definite N x N system H x = rhs.
@@ -184,27 +282,65 @@ __device__ __forceinline__ bool chol_solve(float (&H)[N][N], const float (&rhs)[
     return true;
 }
 
-constexpr int kThreads = 128;
+// Support layouts. Runtime radius R: (2R+1) x (R+1) horizontal sample pairs, the
+// second sample of each row's last pair masked out. Compile-time radius RC (4, 5):
+// the first 2RC columns form (2RC+1) x RC horizontal pairs and the last column
+// RC + 1 vertical pairs (rows 2k, 2k+1; the last one's second sample masked out),
+// 2RC^2 + 2RC + 1 pairs in all, so 16 lanes cover radius 5 in 4 pair slots
+// instead of 5. Pairs are numbered horizontal first; lane l owns l, l + G, ...
+template <int RC>
+struct Layout {
+    static constexpr int side = 2 * RC + 1;
+    static constexpr int nh = side * RC;     // horizontal pairs
+    static constexpr int np = nh + RC + 1;   // all pairs
+};
 
 // Per-lane state of one point's support at the current level: the template
-// T, Tx, Ty of each owned pair, the pair's tap offset in the tap block and the
-// mask of its second sample (0 for the column past the support).
+// T, Tx, Ty of each owned pair (in shared memory: (T, Tx) of slot j at tq[32 j],
+// Ty at ty[32 j], so a warp's 16- and 8-byte accesses are conflict-free), the
+// pair's tap offset in the tap block and the mask of its second sample (0 where
+// it lies past the support). Slots that can hold vertical pairs (compile-time
+// layout only; at most the last two) also keep the offsets of the two taps the
+// second sample adds, and a bit per such slot set for a vertical pair.
 template <int SLP>
 struct Support {
-    float2 T[SLP], Tx[SLP], Ty[SLP];
+    float4* tq;
+    float2* ty;
+    __device__ __forceinline__ void put(int j, float2 T, float2 Tx, float2 Ty)
+    {
+        tq[32 * j] = make_float4(T.x, T.y, Tx.x, Tx.y);
+        ty[32 * j] = Ty;
+    }
+    __device__ __forceinline__ void get(int j, float2& T, float2& Tx, float2& Ty) const
+    {
+        const float4 q = tq[32 * j];
+        T = make_float2(q.x, q.y);
+        Tx = make_float2(q.z, q.w);
+        Ty = ty[32 * j];
+    }
     int off[SLP];
     float msk[SLP];
+    int eo0[2], eo1[2];
+    unsigned vbits;
 };
+
+// First slot that can hold a vertical pair (SLP for the runtime layout).
+template <int G, int SLP, int RC>
+__host__ __device__ constexpr int first_generic_slot()
+{
+    return RC ? Layout<RC>::nh / G : SLP;
+}
 
 // Accumulates the weighted normal equations of the lane's pairs at one iterate.
 // acc[0..9] = sum w (TxTx, TxTy, TxT, Tx, TyTy, TyT, Ty, TT, T, 1); acc[10..13] =
 // sum w r (Tx, Ty, T, 1), each as .x/.y partial sums of a pair's two samples.
 // MODE 0: taps inside, even first column; 1: inside, odd; 2: clamped taps.
-template <typename TS, int G, int SLP, int MODEL, int MODE>
+template <typename TS, int G, int SLP, int MODEL, int MODE, int RC>
 __device__ __forceinline__ void accumulate(const Support<SLP>& S, float2 (&acc)[14], const TS* I2, int pitch, int W,
                                            int H, int bx, int by, const PairWeights& pw, int lane, int np, int pc,
                                            float g1, float c, float ha, float icb, float hc_icb)
 {
+    constexpr int FG = first_generic_slot<G, SLP, RC>();
     const TS* base = I2 + (ptrdiff_t)by * pitch + bx;
     const float2 ng1 = f2(-g1), nc = f2(-c);
 #pragma unroll
@@ -213,14 +349,45 @@ __device__ __forceinline__ void accumulate(const Support<SLP>& S, float2 (&acc)[
         // SLP = ceil(np / G), so only the last slot can hold pairs past the support;
         // testing it there alone leaves the loads of all other slots free to be hoisted
         if (j == SLP - 1 && q >= np) break;
-        const float2 T = S.T[j], Tx = S.Tx[j], Ty = S.Ty[j];
+        float2 T, Tx, Ty;
+        S.get(j, T, Tx, Ty);
         float2 J;
-        if (MODE == 0) {
+        if (j >= FG) {
+            // slot with vertical pairs: sample A's four taps, then the two taps
+            // sample B adds (right column for a horizontal pair, row below for a
+            // vertical one) from their stored offsets
+            const bool vert = (S.vbits >> (j - FG)) & 1u;
+            if (MODE == 2) {
+                if (q < Layout<RC>::nh) {
+                    const int ky = q / RC, kp = q - ky * RC;
+                    J = pair_clamped(I2, pitch, W, H, bx + 2 * kp, by + ky, pw);
+                } else {
+                    J = vpair_clamped(I2, pitch, W, H, bx + 2 * RC, by + 2 * (q - Layout<RC>::nh), pw);
+                }
+            } else {
+                const TS* p = base + S.off[j];
+                float a0, a1, b0, b1;
+                if (MODE == 0) {
+                    const float2 a = ld2(p), b = ld2(p + pitch);
+                    a0 = a.x; a1 = a.y; b0 = b.x; b1 = b.y;
+                } else {
+                    const float2 a = ld2(p + 1), b = ld2(p + pitch + 1);
+                    a0 = dgf::ld(p); a1 = a.x; b0 = dgf::ld(p + pitch); b1 = b.x;
+                }
+                const float e0 = dgf::ld(base + S.eo0[j - FG]), e1 = dgf::ld(base + S.eo1[j - FG]);
+                const float t0 = vert ? b0 : a1, t1 = vert ? b1 : e0, t2 = vert ? e0 : b1;
+                float2 Jp = __fmul2_rn(pw.w00, make_float2(a0, t0));
+                Jp = __ffma2_rn(pw.w01, make_float2(a1, t1), Jp);
+                Jp = __ffma2_rn(pw.w10, make_float2(b0, t2), Jp);
+                J = __ffma2_rn(pw.w11, make_float2(b1, e1), Jp);
+            }
+        } else if (MODE == 0) {
             J = pair_inside<TS, true>(base + S.off[j], pitch, pw);
         } else if (MODE == 1) {
             J = pair_inside<TS, false>(base + S.off[j], pitch, pw);
         } else {
-            const int ky = q / pc, kp = q - ky * pc;
+            const int ppr = RC ? RC : pc;  // horizontal pairs per row
+            const int ky = q / ppr, kp = q - ky * ppr;
             J = pair_clamped(I2, pitch, W, H, bx + 2 * kp, by + ky, pw);
         }
         float2 r;
@@ -298,33 +465,64 @@ struct LevelView {
 
 // Level set-up: samples the template T, Tx, Ty at p_l + k into the lane's pairs
 // and applies the minimum-eigenvalue test. Returns false for SMALL_EIG.
-template <typename TS, int G, int SLP>
+template <typename TS, int G, int SLP, int RC>
 __device__ __forceinline__ bool setup_level(Support<SLP>& S, const LevelView<TS>& L, float plx, float ply, int lane,
                                             unsigned mask, int R, float min_eig)
 {
-    const int side = 2 * R + 1, pc = R + 1, np = side * pc;
+    constexpr int FG = first_generic_slot<G, SLP, RC>();
+    const int side = 2 * R + 1, pc = R + 1, np = RC ? Layout<RC>::np : side * pc;
     const float fx0 = floorf(plx), fy0 = floorf(ply);
     const int bx = (int)fx0 - R, by = (int)fy0 - R;
     const PairWeights pw(plx - fx0, ply - fy0);
     float2 g00 = f2(0.f), g01 = f2(0.f), g11 = f2(0.f);
+    S.vbits = 0u;
 #pragma unroll
     for (int j = 0; j < SLP; ++j) {
         const int q = lane + G * j;
-        const int ky = q / pc, kp = q - ky * pc;
         float2 T = f2(0.f), Tx = f2(0.f), Ty = f2(0.f);
         float msk = 0.f;
         int off = 0;
         if (q < np) {
-            off = ky * L.pitch + 2 * kp;
-            msk = 2 * kp + 1 < side ? 1.f : 0.f;
-            T = pair_clamped(L.I1, L.pitch, L.W, L.H, bx + 2 * kp, by + ky, pw);
-            Tx = pair_clamped(L.I1x, L.pitch, L.W, L.H, bx + 2 * kp, by + ky, pw);
-            Ty = pair_clamped(L.I1y, L.pitch, L.W, L.H, bx + 2 * kp, by + ky, pw);
+            bool vert = false;
+            int x, y;  // tap origin of sample A in the support
+            if (RC == 0) {
+                y = q / pc;
+                x = 2 * (q - y * pc);
+            } else if (q < Layout<RC>::nh) {
+                y = q / RC;
+                x = 2 * (q - y * RC);
+            } else {
+                vert = true;
+                x = 2 * RC;
+                y = 2 * (q - Layout<RC>::nh);
+            }
+            off = y * L.pitch + x;
+            if (vert) {
+                msk = y + 1 < side ? 1.f : 0.f;
+                T = vpair_clamped(L.I1, L.pitch, L.W, L.H, bx + x, by + y, pw);
+                Tx = vpair_clamped(L.I1x, L.pitch, L.W, L.H, bx + x, by + y, pw);
+                Ty = vpair_clamped(L.I1y, L.pitch, L.W, L.H, bx + x, by + y, pw);
+            } else {
+                msk = x + 1 < side ? 1.f : 0.f;
+                T = pair_clamped(L.I1, L.pitch, L.W, L.H, bx + x, by + y, pw);
+                Tx = pair_clamped(L.I1x, L.pitch, L.W, L.H, bx + x, by + y, pw);
+                Ty = pair_clamped(L.I1y, L.pitch, L.W, L.H, bx + x, by + y, pw);
+            }
             if (msk == 0.f) T.y = Tx.y = Ty.y = 0.f;
+            if (j >= FG) {
+                // taps sample B adds: right column (horizontal), row below
+                // (vertical), or, for the masked sample, two of A's own taps so
+                // that every load stays inside the tap block
+                const int e0 = vert ? (msk != 0.f ? off + 2 * L.pitch : off) : off + 2;
+                const int e1 = vert ? e0 + 1 : off + L.pitch + 2;
+                S.eo0[j - FG] = e0;
+                S.eo1[j - FG] = e1;
+                if (vert) S.vbits |= 1u << (j - FG);
+            }
+        } else if (j >= FG) {
+            S.eo0[j - FG] = S.eo1[j - FG] = 0;
         }
-        S.T[j] = T;
-        S.Tx[j] = Tx;
-        S.Ty[j] = Ty;
+        S.put(j, T, Tx, Ty);
         S.off[j] = off;
         S.msk[j] = msk;
         g00 = __ffma2_rn(Tx, Tx, g00);
@@ -341,12 +539,12 @@ __device__ __forceinline__ bool setup_level(Support<SLP>& S, const LevelView<TS>
 
 // One Gauss-Newton step at iterate q (inside the level): accumulates, reduces and
 // solves the weighted normal equations. Returns false on a non-positive pivot.
-template <typename TS, int G, int SLP, int MODEL>
+template <typename TS, int G, int SLP, int MODEL, int RC>
 __device__ __forceinline__ bool gn_step(const Support<SLP>& S, const LevelView<TS>& L, float qx, float qy, float m,
                                         float c, int lane, unsigned mask, int R, float ha, float icb, float hc_icb,
-                                        float (&delta)[4])
+                                        WarpScratch& ws, float (&delta)[4])
 {
-    const int side = 2 * R + 1, pc = R + 1, np = side * pc;
+    const int side = 2 * R + 1, pc = R + 1, np = RC ? Layout<RC>::np : side * pc;
     const float fx0 = floorf(qx), fy0 = floorf(qy);
     const int bx = (int)fx0 - R, by = (int)fy0 - R;
     const PairWeights pw(qx - fx0, qy - fy0);
@@ -358,13 +556,13 @@ __device__ __forceinline__ bool gn_step(const Support<SLP>& S, const LevelView<T
     for (int k = 0; k < 14; ++k) acc[k] = f2(0.f);
     const float g1 = 1.f + m;
     if (inside && (bx & 1) == 0)
-        accumulate<TS, G, SLP, MODEL, 0>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
+        accumulate<TS, G, SLP, MODEL, 0, RC>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
                                          hc_icb);
     else if (inside)
-        accumulate<TS, G, SLP, MODEL, 1>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
+        accumulate<TS, G, SLP, MODEL, 1, RC>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
                                          hc_icb);
     else
-        accumulate<TS, G, SLP, MODEL, 2>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
+        accumulate<TS, G, SLP, MODEL, 2, RC>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
                                          hc_icb);
     float h[16];
     if (MODEL == 4) {
@@ -372,14 +570,14 @@ __device__ __forceinline__ bool gn_step(const Support<SLP>& S, const LevelView<T
 #pragma unroll
         for (int k = 0; k < 14; ++k) v[k] = acc[k].x + acc[k].y;
         v[14] = v[15] = 0.f;
-        group_allreduce16<G>(v, h, mask, lane);
+        group_allreduce16<G>(v, h, mask, lane, ws);
         // a = (Tx, Ty, -T, -1): fold the signs of the T and constant columns
         float Hm[4][4] = {{h[0], h[1], -h[2], -h[3]},
                           {h[1], h[4], -h[5], -h[6]},
                           {-h[2], -h[5], h[7], h[8]},
                           {-h[3], -h[6], h[8], h[9]}};
         const float rhs[4] = {-h[10], -h[11], h[12], h[13]};
-        return chol_solve<4>(Hm, rhs, delta);
+        return block_solve4(Hm, rhs, delta);
     }
     const float h0 = group_sum<G>(acc[0].x + acc[0].y, mask);
     const float h1 = group_sum<G>(acc[1].x + acc[1].y, mask);
@@ -401,18 +599,24 @@ __device__ __forceinline__ bool gn_step(const Support<SLP>& S, const LevelView<T
 // uneven iteration counts and pairs of uneven size; a persistent variant that
 // pulled points from a work counter through a per-group state machine measured
 // slower on both the single-pair and the 64-pair workloads.
-template <typename TS, int G, int SLP, int MODEL, int MINB>
+template <typename TS, int G, int SLP, int MODEL, int MINB, int RC>
 __global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const __grid_constant__ TrackBatch a)
 {
     const int gp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     if (gp >= a.total) return;
     const int lane = threadIdx.x & (G - 1);
     const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-    const int R = a.radius;
+    const int R = RC ? RC : a.radius;
     const float icb = a.inv_cb, hc_icb = a.hc * a.inv_cb;
     const dgf::TrackJob& J = a.jobs[find_job(a, gp)];
     const int pt = gp - J.pt_begin;
+    __shared__ WarpScratch s_ws[kThreads / 32];
+    WarpScratch& ws = s_ws[threadIdx.x >> 5];
     Support<SLP> S;
+    __shared__ float4 s_tq[kThreads / 32][SLP][32];
+    __shared__ float2 s_ty[kThreads / 32][SLP][32];
+    S.tq = &s_tq[threadIdx.x >> 5][0][threadIdx.x & 31];
+    S.ty = &s_ty[threadIdx.x >> 5][0][threadIdx.x & 31];
 
     const float2 p = reinterpret_cast<const float2*>(J.pts)[pt];
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f, m = 0.f, c = 0.f;
@@ -422,7 +626,7 @@ __global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const __grid_const
         const LevelView<TS> L(J, a.levels, l);
         const float scale = __int_as_float((127 - l) << 23);  // 2^-l
         const float plx = (p.x + 0.5f) * scale - 0.5f, ply = (p.y + 0.5f) * scale - 0.5f;
-        if (!setup_level<TS, G, SLP>(S, L, plx, ply, lane, mask, R, a.min_eig)) {
+        if (!setup_level<TS, G, SLP, RC>(S, L, plx, ply, lane, mask, R, a.min_eig)) {
             status = DGF_SMALL_EIG;
             break;
         }
@@ -436,7 +640,7 @@ __global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const __grid_const
                 break;
             }
             float delta[4];
-            if (!gn_step<TS, G, SLP, MODEL>(S, L, qx, qy, m, c, lane, mask, R, a.ha, icb, hc_icb, delta)) {
+            if (!gn_step<TS, G, SLP, MODEL, RC>(S, L, qx, qy, m, c, lane, mask, R, a.ha, icb, hc_icb, ws, delta)) {
                 status = DGF_SINGULAR;
                 break;
             }
@@ -465,27 +669,34 @@ __global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const __grid_const
 
 int g_lanes_override = 0;
 
-template <typename TS, int MODEL, int G, int SLP>
+template <typename TS, int MODEL, int G, int SLP, int RC>
 int launch_one(const TrackBatch& a, cudaStream_t stream)
 {
+    // four blocks of 128 threads per SM (128 registers a thread)
     const long long total = (long long)a.total * G;
-    rlof_kernel<TS, G, SLP, MODEL, 4><<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, stream>>>(a);
+    rlof_kernel<TS, G, SLP, MODEL, 4, RC><<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, stream>>>(a);
     return dgf::launch_status();
 }
 
 template <typename TS, int MODEL>
 int launch(const TrackBatch& a, int lanes, cudaStream_t stream)
 {
+    // radius 4 and 5: compile-time layout with the vertical last column
+#define DGF_LAUNCH_RC(G, RC) \
+    if (lanes == G && a.radius == RC) return launch_one<TS, MODEL, G, (Layout<RC>::np + G - 1) / G, RC>(a, stream);
+    DGF_LAUNCH_RC(8, 4)
+    DGF_LAUNCH_RC(8, 5)
+    DGF_LAUNCH_RC(16, 4)
+    DGF_LAUNCH_RC(16, 5)
+    DGF_LAUNCH_RC(32, 4)
+    DGF_LAUNCH_RC(32, 5)
+#undef DGF_LAUNCH_RC
+    // other radii: runtime layout, 32 lanes
     const int np = (2 * a.radius + 1) * (a.radius + 1);  // sample pairs in the support
 #define DGF_LAUNCH(G, SLP) \
-    if (lanes == G && (np + G - 1) / G == SLP) return launch_one<TS, MODEL, G, SLP>(a, stream);
-    DGF_LAUNCH(8, 6)    // radius 4 (45 pairs)
-    DGF_LAUNCH(8, 9)    // radius 5 (66 pairs)
-    DGF_LAUNCH(16, 3)   // radius 4
-    DGF_LAUNCH(16, 5)   // radius 5
+    if (lanes == G && (np + G - 1) / G == SLP) return launch_one<TS, MODEL, G, SLP, 0>(a, stream);
     DGF_LAUNCH(32, 1)   // radius 1..3
-    DGF_LAUNCH(32, 2)   // radius 4
-    DGF_LAUNCH(32, 3)   // radius 5, 6
+    DGF_LAUNCH(32, 3)   // radius 6
     DGF_LAUNCH(32, 4)   // radius 7
 #undef DGF_LAUNCH
     return DGF_ERR_ARG;
@@ -493,9 +704,11 @@ int launch(const TrackBatch& a, int lanes, cudaStream_t stream)
 
 int choose_lanes(int radius)
 {
-    // 8 and 16 lanes are built for radius 4 and 5 only; other radii use 32 lanes
+    // 8 and 16 lanes are built for radius 4 and 5 only; other radii use 32 lanes.
+    // Measured on GB300: radius 5 fastest at 16 lanes, radius 4 at 8.
     if (radius != 4 && radius != 5) return 32;
-    return g_lanes_override ? g_lanes_override : 16;
+    if (g_lanes_override) return g_lanes_override;
+    return radius == 5 ? 16 : 8;
 }
 
 }  // namespace rlof_detail

@@ -121,6 +121,12 @@ def test_batch_host_checks_return_before_launch():
     assert lib.rlof_track_many(pairs, 2, ctypes.byref(prm), ctypes.c_void_p(fake), need, 8, 0, None) == -1
 
 
+def test_batch_tracker_run_needs_bound_frames():
+    bt = dgf.BatchTracker([(64, 48, 8, 4)], dgf.RlofParams(levels=2, radius=4), device="cpu")
+    with pytest.raises(ValueError):
+        bt.run()
+
+
 def test_product_package_never_loads_the_oracle():
     code = ("import sys; sys.path.insert(0, %r); import paper_1901_09971_gb300 as d; d.load(); "
             "import bench; assert 'oracle' not in sys.modules, 'oracle imported'" % ROOT)

@@ -98,6 +98,29 @@ def test_graph_replay_sees_new_frame_contents(dgf):
     assert_same_as_single(dgf, bt, frames2, specs, prm)
 
 
+def test_bound_frames_run_without_arguments(dgf):
+    """bind() + run(): descriptors built once; new contents written into the bound
+    buffers are tracked, and the results equal an explicit run on the same frames."""
+    prm = dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)
+    specs = SMALL_SPECS[:3]
+    frames = frames_for(specs, 3500)
+    bt, d1, d2 = run_batch(dgf, specs, frames, prm, True)
+    bt.bind(d1, d2)
+    frames2 = frames_for(specs, 3600)
+    for k, (a, b) in enumerate(frames2):
+        d1[k].copy_(torch.from_numpy(a))
+        d2[k].copy_(torch.from_numpy(b))
+    bt.run(use_graph=True)
+    torch.cuda.synchronize()
+    bound = [(f.cpu().numpy().copy(), s.cpu().numpy().copy()) for f, s in zip(bt.flow, bt.status)]
+    bt.run(d1, d2, use_graph=False)
+    torch.cuda.synchronize()
+    for k in range(len(specs)):
+        np.testing.assert_array_equal(bound[k][0], bt.flow[k].cpu().numpy())
+        np.testing.assert_array_equal(bound[k][1], bt.status[k].cpu().numpy())
+    assert_same_as_single(dgf, bt, frames2, specs, prm)
+
+
 def test_more_pairs_than_one_chunk(dgf):
     """70 pairs: two chunks of the persistent launch, each with its own counter."""
     prm = dgf.RlofParams(levels=2, radius=4, max_iter=20, model=2)
