@@ -35,7 +35,7 @@ struct DetectJob {
 };
 
 struct DetectBatch {
-    int ww, wh, by, staged, tile_w, tile_h, n_jobs;
+    int ww, wh, by, vr, staged, tile_w, tile_h, n_jobs;  // vr: windows per thread along y
     DetectJob jobs[kMaxBatchPairs];
 };
 

@@ -17,6 +17,15 @@ __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg
 __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 
+// Asynchronous 4-byte global-to-shared copy (cp.async, sm_80+) and the wait for all of
+// the thread's outstanding copies. Both addresses must be 4-byte aligned.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Rounds v up to a multiple of a, a power of two.
 __host__ __device__ __forceinline__ size_t round_up(size_t v, size_t a) { return (v + a - 1) & ~(a - 1); }
 

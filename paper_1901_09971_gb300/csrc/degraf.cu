@@ -1,9 +1,10 @@
 // DeGraF key-point detection (arXiv 1901.09971, Section 2, Eq. 1-2).
 //
-// One thread per window. A CTA covers 32 x BY windows of one frame (a launch may
-// cover the frames of a whole batch); when they overlap (step < window) the union
-// of their pixels is staged once in shared memory, otherwise each thread reads its
-// window straight from global memory. The window
+// One thread per window column and vr (4) consecutive windows along it; a CTA covers
+// 32 x (by vr) windows of one frame (a launch may cover the frames of a whole batch).
+// When windows overlap (step < window) the union of their pixels is staged once in
+// shared memory with asynchronous copies, otherwise each thread reads its windows
+// straight from global memory. The window
 // sums S = sum I, X = sum j I, Y = sum i I and the maximum m are exact int32; the
 // negative-centroid sums follow from them in closed form,
 //   S_neg = n (1+m) - S,  X_neg = (1+m) h w (w-1)/2 - X,  Y_neg = (1+m) w h (h-1)/2 - Y,
@@ -54,21 +55,33 @@ __device__ __forceinline__ void emit(const DetectJob& J, int ww, int wh, int u, 
     if (J.sums) reinterpret_cast<int4*>(J.sums)[k] = make_int4(S, X, Y, m);
 }
 
-// Window sums of a window of width <= 8 from a staged tile whose rows start on
-// 4-byte boundaries: per row, the window's bytes become two 32-bit words (funnel
-// shifts of three aligned loads), bytes past the window are masked off, and
-// dp4a forms the row sum and the column-weighted row sum while a bytewise max
-// tracks m.
-__device__ __forceinline__ void window_sums_packed(const uint8_t* tile, int stride, int c0, int r0, int ww, int wh,
-                                                   int& S, int& X, int& Y, int& m)
+// Staged tile rows: byte (r, c) of the tile (frame pixel (x0 + c, y0 + r)) sits at
+// tile[r * stride + mis(r) + c], where mis(r) is the misalignment of that frame row's
+// byte x0 (rows advance by the pitch, so it steps by pitch mod 4).
+struct Tile {
+    const uint8_t* bytes;
+    int stride;
+    unsigned mis0, pmod;
+    __device__ __forceinline__ unsigned mis(int r) const { return (mis0 + (unsigned)r * pmod) & 3u; }
+};
+
+// Window sums of a window of width <= 8 at tile column c0, row r0: per row, the
+// window's bytes become two 32-bit words (funnel shifts of three aligned loads),
+// bytes past the window are masked off, and dp4a forms the row sum and the
+// column-weighted row sum while a bytewise max tracks m.
+__device__ __forceinline__ void window_sums_packed(const Tile& T, int c0, int r0, int ww, int wh, int& S, int& X,
+                                                   int& Y, int& m)
 {
-    const unsigned shift = (c0 & 3) * 8;
     const unsigned mlo = ww >= 4 ? 0xffffffffu : (1u << (8 * ww)) - 1u;
     const unsigned mhi = ww >= 8 ? 0xffffffffu : ww <= 4 ? 0u : (1u << (8 * (ww - 4))) - 1u;
-    const unsigned* row = reinterpret_cast<const unsigned*>(tile + r0 * stride) + (c0 >> 2);
+    const unsigned* base = reinterpret_cast<const unsigned*>(T.bytes + r0 * T.stride);
+    unsigned mis = T.mis(r0);
     unsigned mx = 0;
     int s = 0, x = 0, y = 0;
     for (int i = 0; i < wh; ++i) {
+        const unsigned c = (unsigned)c0 + mis;
+        const unsigned* row = base + (c >> 2);
+        const unsigned shift = (c & 3u) * 8u;
         const unsigned w0 = row[0], w1 = row[1], w2 = row[2];
         const unsigned lo = __funnelshift_r(w0, w1, shift) & mlo;
         const unsigned hi = __funnelshift_r(w1, w2, shift) & mhi;
@@ -77,7 +90,8 @@ __device__ __forceinline__ void window_sums_packed(const uint8_t* tile, int stri
         s += rs;
         y += i * rs;
         mx = __vmaxu4(mx, __vmaxu4(lo, hi));
-        row += stride >> 2;
+        base += T.stride >> 2;
+        mis = (mis + T.pmod) & 3u;  // next row's misalignment
     }
     mx = __vmaxu4(mx, mx >> 16);
     mx = __vmaxu4(mx, mx >> 8);
@@ -87,7 +101,31 @@ __device__ __forceinline__ void window_sums_packed(const uint8_t* tile, int stri
     m = (int)(mx & 0xffu);
 }
 
-// One thread per window; CTAs of all frames of the batch in one grid.
+// Window sums of any window size, byte by byte (staged tile or frame rows).
+__device__ __forceinline__ void window_sums_bytes(const uint8_t* w0, int rstride, const Tile* T, int r0, int ww,
+                                                  int wh, int& S, int& X, int& Y, int& m)
+{
+    S = X = Y = m = 0;
+    for (int i = 0; i < wh; ++i) {
+        const uint8_t* row = w0 + (size_t)i * rstride + (T ? T->mis(r0 + i) : 0u);
+        int rs = 0, rx = 0;
+        for (int j = 0; j < ww; ++j) {
+            const int I = row[j];
+            rs += I;
+            rx += j * I;
+            m = max(m, I);
+        }
+        S += rs;
+        X += rx;
+        Y += i * rs;
+    }
+}
+
+// Each thread owns a window column and vr consecutive windows along it; a CTA covers
+// 32 x (by vr) windows of one frame, and the CTAs of all frames of the batch share
+// one grid. When windows overlap (step < window) the CTA stages the union of their
+// pixels with asynchronous 4-byte copies of the aligned words holding them (large
+// tiles: few staging round trips per SM), otherwise threads read the frame directly.
 __global__ void __launch_bounds__(256) degraf_detect_kernel(const __grid_constant__ DetectBatch a)
 {
     extern __shared__ __align__(16) uint8_t tile[];
@@ -103,90 +141,50 @@ __global__ void __launch_bounds__(256) degraf_detect_kernel(const __grid_constan
     }
     const DetectJob& J = a.jobs[f];
     const int t = blockIdx.x - J.cta_begin;
-    const int u0 = (t % J.tiles_x) * kBX, v0 = (t / J.tiles_x) * blockDim.y;
+    const int wy = (int)blockDim.y * a.vr;  // windows per CTA along y
+    const int u0 = (t % J.tiles_x) * kBX, v0 = (t / J.tiles_x) * wy;
     const int x0 = u0 * J.step, y0 = v0 * J.step;
-    const int tile_w = (kBX - 1) * J.step + a.ww, tile_h = ((int)blockDim.y - 1) * J.step + a.wh;
-    const int stride = a.tile_w;  // row stride of the staged tile (multiple of 4)
+    const long long org = (long long)(uintptr_t)J.img + (long long)y0 * J.pitch + x0;
+    const Tile T{tile, a.tile_w, (unsigned)org & 3u, (unsigned)J.pitch & 3u};
     if (a.staged) {
-        // stage the pixels under the CTA's windows as aligned 32-bit words: per row
-        // the word under each 4-byte group and, for a misaligned row, the next word
-        // (only if it still holds a byte of the tile, so no load leaves the frame),
-        // funnel-shifted; 4 rows x 2 words per thread in flight at a time
-        const int tw = min(tile_w, J.W - x0), th = min(tile_h, J.H - y0);
-        const int nw = (tw + 3) >> 2;
-        unsigned* tile32 = reinterpret_cast<unsigned*>(tile);
-        for (int r0 = threadIdx.y; r0 < th; r0 += 4 * blockDim.y) {
-            unsigned lo[4][2], hi[4][2], sh[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = r0 + i * blockDim.y;
-                const uintptr_t src = reinterpret_cast<uintptr_t>(J.img + (size_t)(y0 + min(r, th - 1)) * J.pitch + x0);
-                const unsigned a = (unsigned)(src & 3u);
-                const unsigned* w = reinterpret_cast<const unsigned*>(src & ~(uintptr_t)3);
-                sh[i] = a * 8u;
-#pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    const int k = threadIdx.x + 32 * m;
-                    const bool ok = r < th && k < nw;
-                    lo[i][m] = ok ? __ldg(w + k) : 0u;
-                    hi[i][m] = ok && a && 4 * (k + 1) - (int)a < tw ? __ldg(w + k + 1) : 0u;
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = r0 + i * blockDim.y;
-#pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    const int k = threadIdx.x + 32 * m;
-                    if (r < th && k < nw) tile32[r * (stride >> 2) + k] = __funnelshift_r(lo[i][m], hi[i][m], sh[i]);
-                }
-            }
+        // every aligned word holding a byte of the tile (such a word lies inside the
+        // frame's allocation); tile rows past the frame are never read
+        const int tw = min((kBX - 1) * J.step + a.ww, J.W - x0);
+        const int th = min((wy - 1) * J.step + a.wh, J.H - y0);
+        const int nwr = (tw + 3 + 3) >> 2;  // words per row, misalignment included
+        const int nthr = kBX * blockDim.y;
+        for (int i = threadIdx.y * kBX + threadIdx.x; i < th * nwr; i += nthr) {
+            const int r = i / nwr, k = i - r * nwr;
+            const int c_lo = 4 * k - (int)T.mis(r);  // tile column of the word's first byte
+            if (c_lo >= tw) continue;
+            cp_async4(tile + r * a.tile_w + 4 * k, J.img + (long long)(y0 + r) * J.pitch + x0 + c_lo);
         }
-        for (int k = 64 + threadIdx.x; k < nw; k += 32)  // rows wider than 256 bytes (large steps)
-            for (int r = threadIdx.y; r < th; r += blockDim.y) {
-                const uintptr_t src = reinterpret_cast<uintptr_t>(J.img + (size_t)(y0 + r) * J.pitch + x0);
-                const unsigned a = (unsigned)(src & 3u);
-                const unsigned* w = reinterpret_cast<const unsigned*>(src & ~(uintptr_t)3);
-                const unsigned lo = __ldg(w + k), hi = a && 4 * (k + 1) - (int)a < tw ? __ldg(w + k + 1) : 0u;
-                tile32[r * (stride >> 2) + k] = __funnelshift_r(lo, hi, a * 8u);
-            }
+        cp_async_wait_all();
         __syncthreads();
     }
-    const int u = u0 + threadIdx.x, v = v0 + threadIdx.y;
-    if (u >= J.nu || v >= J.nv) return;
-    int S = 0, X = 0, Y = 0, m = 0;
-    if (a.staged && a.ww <= 8) {
-        window_sums_packed(tile, stride, threadIdx.x * J.step, threadIdx.y * J.step, a.ww, a.wh, S, X, Y, m);
-    } else {
-        const uint8_t* w0;
-        int rstride;
-        if (a.staged) {
-            w0 = tile + threadIdx.y * J.step * stride + threadIdx.x * J.step;
-            rstride = stride;
+    const int u = u0 + threadIdx.x;
+    if (u >= J.nu) return;
+    for (int k = 0; k < a.vr; ++k) {
+        const int wv = threadIdx.y * a.vr + k;  // window row inside the CTA
+        const int v = v0 + wv;
+        if (v >= J.nv) return;
+        int S, X, Y, m;
+        if (a.staged && a.ww <= 8) {
+            window_sums_packed(T, threadIdx.x * J.step, wv * J.step, a.ww, a.wh, S, X, Y, m);
+        } else if (a.staged) {
+            window_sums_bytes(tile + wv * J.step * a.tile_w + threadIdx.x * J.step, a.tile_w, &T, wv * J.step, a.ww,
+                              a.wh, S, X, Y, m);
         } else {
-            w0 = J.img + (size_t)(v * J.step) * J.pitch + u * J.step;
-            rstride = J.pitch;
+            window_sums_bytes(J.img + (size_t)(v * J.step) * J.pitch + u * J.step, J.pitch, nullptr, 0, a.ww, a.wh, S,
+                              X, Y, m);
         }
-        for (int i = 0; i < a.wh; ++i) {
-            const uint8_t* row = w0 + (size_t)i * rstride;
-            int rs = 0, rx = 0;
-            for (int j = 0; j < a.ww; ++j) {
-                const int I = row[j];
-                rs += I;
-                rx += j * I;
-                m = max(m, I);
-            }
-            S += rs;
-            X += rx;
-            Y += i * rs;
-        }
+        emit(J, a.ww, a.wh, u, v, S, X, Y, m);
     }
-    emit(J, a.ww, a.wh, u, v, S, X, Y, m);
 }
 
-// Chooses the CTA shape (32 x by windows, staged through shared memory when the
-// windows overlap and every frame's tile fits), fills the CTA prefix counts and
-// launches detection for every frame of the batch.
+// Chooses the CTA shape (32 x by threads, vr windows per thread along y; staged
+// through shared memory when the windows overlap and every frame's tile fits),
+// fills the CTA prefix counts and launches detection for every frame of the batch.
 int launch_detect(DetectBatch& a, cudaStream_t stream)
 {
     int max_step = 1;
@@ -195,29 +193,32 @@ int launch_detect(DetectBatch& a, cudaStream_t stream)
         max_step = a.jobs[f].step > max_step ? a.jobs[f].step : max_step;
         overlap = overlap && (a.jobs[f].step < a.ww || a.jobs[f].step < a.wh);
     }
-    int by = 8;
-    // rows padded to 4 bytes plus two words, so the packed path's three aligned
-    // word loads past a window start stay inside the row
-    const int tile_w = ((kBX - 1) * max_step + a.ww + 3) / 4 * 4 + 8;
-    int tile_h = (by - 1) * max_step + a.wh;
-    while (by > 1 && tile_w * tile_h > kSmemMax) {
-        by /= 2;
-        tile_h = (by - 1) * max_step + a.wh;
+    // row stride: the tile's bytes, up to 3 bytes of row misalignment, and room for
+    // the packed path's three aligned word loads from a window's first byte
+    const int tile_w = ((kBX - 1) * max_step + a.ww + 3 + 12 + 3) / 4 * 4;
+    int by = 8, vr = 4;
+    auto tile_h = [&]() { return (by * vr - 1) * max_step + a.wh; };
+    while (tile_w * tile_h() > kSmemMax && (vr > 1 || by > 1)) {
+        if (vr > 1)
+            vr /= 2;
+        else
+            by /= 2;
     }
     a.by = by;
-    a.staged = overlap && tile_w * tile_h <= kSmemMax;
+    a.vr = vr;
+    a.staged = overlap && tile_w * tile_h() <= kSmemMax;
     a.tile_w = tile_w;  // row stride of the staged tile
-    a.tile_h = tile_h;
+    a.tile_h = tile_h();
     long long ctas = 0;
     for (int f = 0; f < a.n_jobs; ++f) {
         DetectJob& J = a.jobs[f];
         J.tiles_x = (J.nu + kBX - 1) / kBX;
         J.cta_begin = (int)ctas;
-        ctas += (long long)J.tiles_x * ((J.nv + by - 1) / by);
+        ctas += (long long)J.tiles_x * ((J.nv + by * vr - 1) / (by * vr));
     }
     if (ctas == 0) return DGF_OK;
     if (ctas > 0x7fffffffLL) return DGF_ERR_ARG;
-    degraf_detect_kernel<<<(unsigned)ctas, dim3(kBX, by), a.staged ? (size_t)tile_w * tile_h : 0, stream>>>(a);
+    degraf_detect_kernel<<<(unsigned)ctas, dim3(kBX, by), a.staged ? (size_t)a.tile_w * a.tile_h : 0, stream>>>(a);
     return launch_status();
 }
 

@@ -7,33 +7,43 @@
 // integer byte sum times 4^-l and every Sobel sum a small multiple of it, so all of
 // them are exact in FP32 (FP16 storage rounds each exact value once).
 //
-// One CTA owns a 64 x 32 tile of level 0 and produces the matching tile of every
-// level: it stages the frame bytes under the tile plus a halo of 2^(L-1) pixels in
-// shared memory (enough for a one-pixel halo at the coarsest level), then walks
+// One CTA owns a 64 x TY tile of level 0 (TY = 128 for up to 4 levels, 32 beyond)
+// and produces the matching tile of every level. It stages the frame bytes under
+// the tile plus a halo of 2^(L-1) pixels (enough for a one-pixel halo at the
+// coarsest level) with asynchronous 4-byte copies (cp.async) of the aligned words
+// that hold them: frame rows need not start on any boundary, so each staged row
+// keeps its own misalignment (0..3 bytes) and every read adds it. Then the CTA walks
 // down the levels, forming each level's values on its halo'd region from the
-// previous one with 2x2 means and writing I, Ix, Iy of the tile with coalesced
-// rows (16-byte stores at level 0). The frame is read about once from DRAM and
-// every output byte is written once, which makes the kernel a streaming one.
+// previous one with 2x2 means and writing I, Ix, Iy of the tile with coalesced rows
+// (16-byte stores at level 0). Tall tiles mean few staging round trips per SM; the
+// frame is read about once from DRAM and every output byte is written once.
 #include "common.cuh"
 #include "batch.cuh"
 
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kTX = 64, kTY = 32;  // level-0 tile
+constexpr int kTX = 64;  // level-0 tile width
 
-__host__ __device__ inline int halo(int levels) { return levels >= 2 ? 1 << (levels - 1) : 1; }
+__host__ __device__ constexpr int tile_h(int levels) { return levels <= 4 ? 128 : 32; }
+__host__ __device__ constexpr int halo(int levels) { return levels >= 2 ? 1 << (levels - 1) : 1; }
+__host__ __device__ constexpr int region_w(int levels) { return kTX + 2 * halo(levels); }
+__host__ __device__ constexpr int region_h(int levels) { return tile_h(levels) + 2 * halo(levels); }
+// staged row pitch: the region's bytes plus up to 3 bytes of row misalignment
+__host__ __device__ constexpr int region_pitch(int levels) { return (region_w(levels) + 3 + 3) & ~3; }
 
-__host__ __device__ inline int frame_ctas(int W, int H) { return ((W + kTX - 1) / kTX) * ((H + kTY - 1) / kTY); }
+__host__ __device__ inline int frame_ctas(int W, int H, int levels)
+{
+    return ((W + kTX - 1) / kTX) * ((H + tile_h(levels) - 1) / tile_h(levels));
+}
 
 __host__ __device__ inline size_t round16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-// Shared memory of one CTA: the byte region, then the float regions of levels 1..L-1.
+// Shared memory of one CTA: the staged byte rows, then the float regions of levels 1..L-1.
 inline size_t smem_bytes(int levels)
 {
-    const int h = halo(levels);
-    const int RW = kTX + 2 * h, RH = kTY + 2 * h;
-    size_t off = round16((size_t)RW * RH);
+    const int RW = region_w(levels), RH = region_h(levels);
+    size_t off = round16((size_t)region_pitch(levels) * RH);
     for (int l = 1; l < levels; ++l) off += round16((size_t)(RW >> l) * (RH >> l) * 4);
     return off;
 }
@@ -55,6 +65,19 @@ __device__ __forceinline__ void store4<__half>(__half* p, float a, float b, floa
     *reinterpret_cast<uint2*>(p) = v;
 }
 
+// Staged region rows: byte (r, c) of the halo'd region (frame pixel (gx0 + c,
+// gy0 + r)) sits at raw[r * RWP + mis(r) + c], where mis(r) is the misalignment of
+// that frame row's byte gx0 (rows advance by the pitch, so it steps by pitch mod 4).
+struct Staged {
+    const unsigned char* raw;
+    unsigned mis0, pmod;
+    int RWP;
+    __device__ __forceinline__ const unsigned char* row(int r) const
+    {
+        return raw + r * RWP + ((mis0 + (unsigned)r * pmod) & 3u);
+    }
+};
+
 }  // namespace
 
 namespace dgf {
@@ -62,23 +85,22 @@ namespace dgf {
 // Level 0 of the tile: I and Sobel / 8 straight from the staged bytes, four
 // pixels per item. INTERIOR: the halo'd region lies inside the frame, so no
 // neighbour needs clamping.
-template <typename TS, bool INTERIOR>
-__device__ __forceinline__ void level0(const PyrFrame& F, const LevelGeom& g, const unsigned char* raw, int RW,
-                                       int X0, int Y0, int h)
+template <typename TS, bool INTERIOR, int TY>
+__device__ __forceinline__ void level0(const PyrFrame& F, const LevelGeom& g, const Staged& R, int X0, int Y0, int h)
 {
     TS* I = reinterpret_cast<TS*>(F.base + g.off_I);
     TS* Ix = reinterpret_cast<TS*>(F.base + g.off_Ix);
     TS* Iy = reinterpret_cast<TS*>(F.base + g.off_Iy);
     const int gx0 = X0 - h, gy0 = Y0 - h;
-    for (int i = threadIdx.x; i < kTY * (kTX / 4); i += blockDim.x) {
+    for (int i = threadIdx.x; i < TY * (kTX / 4); i += blockDim.x) {
         const int ty = i >> 4, tx = (i & 15) << 2;  // kTX / 4 = 16 items per row
         const int y = Y0 + ty;
         if (!INTERIOR && (y >= F.H || X0 + tx >= F.W)) continue;
         float vI[4], vx[4], vy[4];
         if (INTERIOR) {
-            const unsigned char* rc = raw + (ty + h) * RW + tx + h - 1;  // columns x-1 .. x+4
-            const unsigned char* rm = rc - RW;
-            const unsigned char* rp = rc + RW;
+            const unsigned char* rm = R.row(ty + h - 1) + tx + h - 1;  // columns x-1 .. x+4
+            const unsigned char* rc = R.row(ty + h) + tx + h - 1;
+            const unsigned char* rp = R.row(ty + h + 1) + tx + h - 1;
             int a[6], b[6], c[6];
 #pragma unroll
             for (int j = 0; j < 6; ++j) {
@@ -95,14 +117,13 @@ __device__ __forceinline__ void level0(const PyrFrame& F, const LevelGeom& g, co
                 vy[k] = (float)sy * 0.125f;
             }
         } else {
-            const int ym = max(y - 1, 0) - gy0, yc = y - gy0, yp = min(y + 1, F.H - 1) - gy0;
+            const unsigned char* rm = R.row(max(y - 1, 0) - gy0);
+            const unsigned char* rc = R.row(y - gy0);
+            const unsigned char* rp = R.row(min(y + 1, F.H - 1) - gy0);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int x = min(X0 + tx + k, F.W - 1);  // past the edge: recomputed, not stored
                 const int xm = max(x - 1, 0) - gx0, xc = x - gx0, xp = min(x + 1, F.W - 1) - gx0;
-                const unsigned char* rm = raw + ym * RW;
-                const unsigned char* rc = raw + yc * RW;
-                const unsigned char* rp = raw + yp * RW;
                 const int sx = ((int)rm[xp] - rm[xm]) + 2 * ((int)rc[xp] - rc[xm]) + ((int)rp[xp] - rp[xm]);
                 const int sy = ((int)rp[xm] - rm[xm]) + 2 * ((int)rp[xc] - rm[xc]) + ((int)rp[xp] - rm[xp]);
                 vI[k] = (float)rc[xc];
@@ -133,13 +154,12 @@ __device__ __forceinline__ void level0(const PyrFrame& F, const LevelGeom& g, co
 // previous one, then the tile's I, Ix, Iy from it. The level loop unrolls, so every
 // region size is a compile-time constant (flat loops, constant divisors).
 template <typename TS, bool INTERIOR, int L>
-__device__ __forceinline__ void coarse_levels(const PyrFrame& F, const LevelGeom* geo, unsigned char* smem, int X0,
-                                              int Y0)
+__device__ __forceinline__ void coarse_levels(const PyrFrame& F, const LevelGeom* geo, const Staged& R,
+                                              unsigned char* smem, int X0, int Y0)
 {
-    constexpr int h = L >= 2 ? 1 << (L - 1) : 1;
-    constexpr int RW = kTX + 2 * h, RH = kTY + 2 * h;
-    const unsigned char* raw = smem;
-    size_t prev_off = 0, cur_off = round16((size_t)RW * RH);
+    constexpr int h = halo(L), TY = tile_h(L);
+    constexpr int RW = region_w(L), RH = region_h(L);
+    size_t prev_off = 0, cur_off = round16((size_t)region_pitch(L) * RH);
 #pragma unroll
     for (int l = 1; l < L; ++l) {
         if (l > 1) {
@@ -157,8 +177,9 @@ __device__ __forceinline__ void coarse_levels(const PyrFrame& F, const LevelGeom
             float v = 0.f;
             if (INTERIOR || (ox + rx >= 0 && ox + rx < g.W && oy + ry >= 0 && oy + ry < g.H)) {
                 if (l == 1) {
-                    const unsigned char* b = raw + (2 * ry) * RW + 2 * rx;
-                    v = (float)(((int)b[0] + b[1]) + ((int)b[RW] + b[RW + 1])) * 0.25f;
+                    const unsigned char* b0 = R.row(2 * ry) + 2 * rx;
+                    const unsigned char* b1 = R.row(2 * ry + 1) + 2 * rx;
+                    v = (float)(((int)b0[0] + b0[1]) + ((int)b1[0] + b1[1])) * 0.25f;
                 } else {
                     const float* b = prev + (2 * ry) * pw + 2 * rx;
                     v = ((b[0] + b[1]) + (b[pw] + b[pw + 1])) * 0.25f;
@@ -170,7 +191,7 @@ __device__ __forceinline__ void coarse_levels(const PyrFrame& F, const LevelGeom
         TS* I = reinterpret_cast<TS*>(F.base + g.off_I);
         TS* Ix = reinterpret_cast<TS*>(F.base + g.off_Ix);
         TS* Iy = reinterpret_cast<TS*>(F.base + g.off_Iy);
-        const int tw = kTX >> l, th = kTY >> l;
+        const int tw = kTX >> l, th = TY >> l;
         for (int i = threadIdx.x; i < tw * th; i += kThreads) {
             const int ty = i / tw, tx = i - ty * tw;
             const int x = (X0 >> l) + tx, y = (Y0 >> l) + ty;
@@ -192,8 +213,15 @@ __device__ __forceinline__ void coarse_levels(const PyrFrame& F, const LevelGeom
     }
 }
 
+// Four blocks per SM for up to four levels (tall tiles, 64 registers), at least two beyond.
+template <int L>
+constexpr int pyramid_min_blocks()
+{
+    return L <= 4 ? 4 : 2;
+}
+
 template <typename TS, int L>
-__global__ void __launch_bounds__(kThreads) pyramid_kernel(const __grid_constant__ PyrBatch a)
+__global__ void __launch_bounds__(kThreads, pyramid_min_blocks<L>()) pyramid_kernel(const __grid_constant__ PyrBatch a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LevelGeom geo[DGF_MAX_LEVELS];
@@ -214,72 +242,37 @@ __global__ void __launch_bounds__(kThreads) pyramid_kernel(const __grid_constant
     }
     __syncthreads();
     const PyrFrame& F = a.frames[frame];
+    constexpr int h = halo(L), TY = tile_h(L);
+    constexpr int RW = region_w(L), RH = region_h(L), RWP = region_pitch(L), NWR = RWP / 4;
     const int t = blockIdx.x - F.cta_begin;
     const int tiles_x = (F.W + kTX - 1) / kTX;
-    const int X0 = (t % tiles_x) * kTX, Y0 = (t / tiles_x) * kTY;
-    constexpr int h = L >= 2 ? 1 << (L - 1) : 1;
-    constexpr int RW = kTX + 2 * h, RH = kTY + 2 * h;
-    constexpr int NB = (RW * RH + kThreads - 1) / kThreads;  // staged bytes per thread
+    const int X0 = (t % tiles_x) * kTX, Y0 = (t / tiles_x) * TY;
     const int gx0 = X0 - h, gy0 = Y0 - h;
     // the halo'd region inside the frame: no clamping at any level
     const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + RW <= F.W && gy0 + RH <= F.H;
 
-    // 1. frame bytes under the tile and its halo (outside the frame: 0, never used);
-    // every thread issues all of its loads before its first shared-memory store,
-    // so the CTA waits for one round trip rather than one per byte
-    if (interior && RW % 4 == 0) {
-        // rows as aligned 32-bit words: the word under each 4-byte group of the row
-        // and the next one, funnel-shifted by the row's misalignment (an aligned
-        // word that holds any byte of the frame lies inside its allocation)
-        constexpr int NW = RW / 4;                           // words per region row (<= 32)
-        constexpr int NR = (RH + kThreads / 32 - 1) / (kThreads / 32);  // rows per warp
-        static_assert(NW <= 32, "one word per lane and row");
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        unsigned lo[NR], hi[NR], shift[NR];
-#pragma unroll
-        for (int i = 0; i < NR; ++i) {  // every load of the warp in flight before any store
-            const int ry = warp + i * (kThreads / 32);
-            lo[i] = hi[i] = shift[i] = 0u;
-            if (ry < RH && lane < NW) {
-                const uintptr_t src = reinterpret_cast<uintptr_t>(F.img + (size_t)(gy0 + ry) * F.pitch + gx0);
-                const unsigned* w = reinterpret_cast<const unsigned*>(src & ~(uintptr_t)3);
-                shift[i] = (unsigned)(src & 3u) * 8u;
-                lo[i] = __ldg(w + lane);
-                if (shift[i]) hi[i] = __ldg(w + lane + 1);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < NR; ++i) {
-            const int ry = warp + i * (kThreads / 32);
-            if (ry < RH && lane < NW)
-                reinterpret_cast<unsigned*>(smem + ry * RW)[lane] = __funnelshift_r(lo[i], hi[i], shift[i]);
-        }
-    } else {
-        for (int k0 = 0; k0 < NB; k0 += 16) {  // up to 16 byte loads in flight per thread
-            unsigned char v[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int i = threadIdx.x + (k0 + k) * kThreads;
-                const int ry = i / RW, rx = i - ry * RW;
-                const int gx = gx0 + rx, gy = gy0 + ry;
-                const bool in = k0 + k < NB && i < RW * RH && (interior || (gx >= 0 && gx < F.W && gy >= 0 && gy < F.H));
-                v[k] = in ? __ldg(F.img + (size_t)gy * F.pitch + gx) : 0;
-            }
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int i = threadIdx.x + (k0 + k) * kThreads;
-                if (k0 + k < NB && i < RW * RH) smem[i] = v[k];
-            }
-        }
+    // 1. stage the frame bytes under the tile and its halo: every aligned 4-byte word
+    // that holds a byte of the region inside the frame (such a word lies inside the
+    // frame's allocation), copied asynchronously; bytes outside the frame are never read
+    const long long org = (long long)(uintptr_t)F.img + (long long)gy0 * F.pitch + gx0;
+    Staged R{smem, (unsigned)org & 3u, (unsigned)F.pitch & 3u, RWP};
+    const int cx0 = max(gx0, 0) - gx0, cx1 = min(gx0 + RW, F.W) - gx0;  // region columns inside the frame
+    for (int i = threadIdx.x; i < RH * NWR; i += kThreads) {
+        const int r = i / NWR, k = i - r * NWR;
+        const int gy = gy0 + r;
+        const int c_lo = 4 * k - (int)((R.mis0 + (unsigned)r * R.pmod) & 3u);  // region column of the word's first byte
+        if (gy < 0 || gy >= F.H || c_lo + 3 < cx0 || c_lo >= cx1) continue;
+        cp_async4(smem + r * RWP + 4 * k, F.img + (long long)gy * F.pitch + gx0 + c_lo);
     }
+    cp_async_wait_all();
     __syncthreads();
 
     if (interior) {
-        level0<TS, true>(F, geo[0], smem, RW, X0, Y0, h);
-        coarse_levels<TS, true, L>(F, geo, smem, X0, Y0);
+        level0<TS, true, TY>(F, geo[0], R, X0, Y0, h);
+        coarse_levels<TS, true, L>(F, geo, R, smem, X0, Y0);
     } else {
-        level0<TS, false>(F, geo[0], smem, RW, X0, Y0, h);
-        coarse_levels<TS, false, L>(F, geo, smem, X0, Y0);
+        level0<TS, false, TY>(F, geo[0], R, X0, Y0, h);
+        coarse_levels<TS, false, L>(F, geo, R, smem, X0, Y0);
     }
 }
 
@@ -289,7 +282,7 @@ int launch_pyramids(PyrBatch& a, int storage, cudaStream_t stream)
     long long ctas = 0;
     for (int f = 0; f < a.n_frames; ++f) {
         a.frames[f].cta_begin = (int)ctas;
-        ctas += frame_ctas(a.frames[f].W, a.frames[f].H);
+        ctas += frame_ctas(a.frames[f].W, a.frames[f].H, a.levels);
     }
     if (ctas == 0) return DGF_OK;
     if (ctas > 0x7fffffffLL) return DGF_ERR_ARG;
@@ -317,6 +310,7 @@ int launch_pyramids(PyrBatch& a, int storage, cudaStream_t stream)
 }
 
 }  // namespace dgf
+
 
 extern "C" int dgf_pyramid_layout_get(int W, int H, int levels, int storage, int with_grad,
                                       dgf_pyramid_layout* out)
