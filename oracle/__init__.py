@@ -84,6 +84,11 @@ def lib():
         _lib.oracle_degraf_vjp.restype = I
         _lib.oracle_rlof_vjp.argtypes = [P, P, I, I, P, I, ctypes.POINTER(_RlofParams), P, P, P, P, P, P, P]
         _lib.oracle_rlof_vjp.restype = I
+        _lib.oracle_rlof_track_init.argtypes = [P, P, I, I, P, I, ctypes.POINTER(_RlofParams), P, P, P, P,
+                                                P, I]
+        _lib.oracle_rlof_track_init.restype = I
+        _lib.oracle_gm_fit_affine.argtypes = [P, P, P, I, I, D, D, P]
+        _lib.oracle_gm_fit_affine.restype = I
         _lib.oracle_max_threads.argtypes = []
         _lib.oracle_max_threads.restype = I
     return _lib
@@ -144,8 +149,11 @@ def hampel_psi(r: float, a: float, b: float, c: float) -> float:
 
 
 def rlof_track(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofParams,
-               nthreads: int = 0):
-    """Track pts [n,2] from I1 to I2: (flow [n,2], status [n] u8, iters [n] i32, illum [n,2])."""
+               nthreads: int = 0, init_flow: np.ndarray | None = None):
+    """Track pts [n,2] from I1 to I2: (flow [n,2], status [n] u8, iters [n] i32, illum [n,2]).
+
+    init_flow [n,2] (optional): initial level-0 flow per point (the global-motion
+    prior); tracking then starts the coarsest level at init_flow / 2^(levels-1)."""
     I1 = np.ascontiguousarray(I1, dtype=np.float64)
     I2 = np.ascontiguousarray(I2, dtype=np.float64)
     pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
@@ -156,11 +164,55 @@ def rlof_track(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofPara
     iters = np.zeros(n, np.int32)
     illum = np.zeros((n, 2), np.float64)
     prm = params._c()
-    rc = lib().oracle_rlof_track(_ptr(I1), _ptr(I2), W, H, _ptr(pts), n, ctypes.byref(prm),
-                                 _ptr(flow), _ptr(status), _ptr(iters), _ptr(illum), int(nthreads))
+    init = None if init_flow is None else np.ascontiguousarray(init_flow, dtype=np.float64).reshape(n, 2)
+    rc = lib().oracle_rlof_track_init(_ptr(I1), _ptr(I2), W, H, _ptr(pts), n, ctypes.byref(prm),
+                                      _ptr(init) if init is not None else None, _ptr(flow), _ptr(status),
+                                      _ptr(iters), _ptr(illum), int(nthreads))
     if rc:
         raise ValueError("oracle_rlof_track: bad arguments")
     return flow, status, iters, illum
+
+
+def gm_fit_affine(pts: np.ndarray, flow: np.ndarray, status: np.ndarray, iters: int = 8, c0: float = 32.0,
+                  c_min: float = 2.0):
+    """Global affine motion q = A p + t from first-pass tracks (Tukey IRLS, annealed
+    threshold; see the C source). Returns (a [6] float64, made) with
+    q_x = a0 x + a1 y + a2, q_y = a3 x + a4 y + a5; made is False when no estimate
+    could be formed (a is then the identity motion)."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+    n = pts.shape[0]
+    flow = np.ascontiguousarray(flow, dtype=np.float64).reshape(n, 2)
+    status = np.ascontiguousarray(status, dtype=np.uint8).reshape(n)
+    a = np.zeros(6, np.float64)
+    rc = lib().oracle_gm_fit_affine(_ptr(pts), _ptr(flow), _ptr(status), n, int(iters), float(c0), float(c_min),
+                                    _ptr(a))
+    if rc < 0:
+        raise ValueError("oracle_gm_fit_affine: bad arguments")
+    return a, rc == 0
+
+
+def rlof_track_gm(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofParams, stride: int = 4,
+                  extra_levels: int = 2, iters: int = 8, c0: float = 32.0, c_min: float = 2.0, nthreads: int = 0):
+    """Tracking with the global-motion prior (Section 3, RLOF(IM-GM); the paper
+    gives no formula, so this is the reading): (1) a sparse first pass tracks
+    every stride-th point with extra_levels more pyramid levels, which reaches
+    large motions; (2) gm_fit_affine fits the global affine motion to its converged
+    points; (3) every point is tracked with the configured levels, starting from
+    the prior's flow A p + t - p. Returns (flow, status, iters, illum, a, made)."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+    sub = pts[::stride]
+    deep = dataclasses.replace(params, levels=params.levels + extra_levels)
+    fs, ss, _, _ = rlof_track(I1, I2, sub, deep, nthreads)
+    a, made = gm_fit_affine(sub, fs, ss, iters, c0, c_min)
+    flow, status, its, illum = rlof_track(I1, I2, pts, params, nthreads, init_flow=gm_prior_flow(a, pts))
+    return flow, status, its, illum, a, made
+
+
+def gm_prior_flow(a: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """Initial level-0 flow of each point under the affine motion a: A p + t - p."""
+    pts = np.asarray(pts, dtype=np.float64).reshape(-1, 2)
+    x, y = pts[:, 0], pts[:, 1]
+    return np.stack([a[0] * x + a[1] * y + a[2] - x, a[3] * x + a[4] * y + a[5] - y], 1)
 
 
 def degraf_detect_f64(img: np.ndarray, win_w: int, win_h: int | None = None, step: int = 1):

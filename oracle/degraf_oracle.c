@@ -277,6 +277,7 @@ static void pyramid_views(const double* pyr, int W, int H, int levels, level_vie
  * Tracks one point p (level-0 pixel coordinates) from frame 1 into frame 2.
  * Reading of RLOF used here (the paper gives only the method's name and its
  * options, Section 2 and Section 3 "Parameters"):
+ *   g = 0 (or a given initial level-0 flow divided by 2^(L-1)), m = c = 0
  *   for l = L-1 .. 0:
  *     p_l = (p + 1/2) / 2^l - 1/2                      (centre-aligned pyramid map)
  *     template T_k, Tx_k, Ty_k = bilinear(I1_l, I1x_l, I1y_l) at p_l + k,
@@ -299,13 +300,15 @@ static void pyramid_views(const double* pyr, int W, int H, int levels, level_vie
  * Returns the status; *iters counts the Gauss-Newton updates over all levels.
  */
 static int track_point(const level_view* P1, const level_view* P2, const oracle_rlof_params* prm,
-                       double px, double py, double* flow, double* illum, int* iters)
+                       double px, double py, const double* init, double* flow, double* illum, int* iters)
 {
     const int r = prm->radius, side = 2 * r + 1, npx = side * side;
     const int nm = prm->model == 4 ? 4 : 2;
     double* T = malloc(sizeof(double) * 3 * npx);
     double *Tx = T + npx, *Ty = T + 2 * npx;
-    double gx = 0, gy = 0, dx = 0, dy = 0, m = 0, c = 0;
+    /* an initial level-0 flow u starts the coarsest level at g = u / 2^(L-1) */
+    const double s0 = ldexp(1.0, -(prm->levels - 1));
+    double gx = init ? init[0] * s0 : 0, gy = init ? init[1] * s0 : 0, dx = 0, dy = 0, m = 0, c = 0;
     int status = OR_TRACKED;
     *iters = 0;
     for (int l = prm->levels - 1; l >= 0 && status == OR_TRACKED; --l) {
@@ -389,12 +392,14 @@ static int rlof_params_ok(const oracle_rlof_params* p)
 
 /*
  * Tracks n points from frame I1 to frame I2 (both W x H doubles, row-major).
+ * init_flow [n][2] (nullable): an initial level-0 flow per point (the global-motion
+ * prior); NULL starts every point at zero motion.
  * Outputs: flow [n][2], status [n], iters [n] (nullable), illum [n][2] (gain m and
  * offset c; nullable). nthreads <= 0 uses the OpenMP default.
  */
-int oracle_rlof_track(const double* I1, const double* I2, int W, int H, const double* pts, int n,
-                      const oracle_rlof_params* prm, double* flow, uint8_t* status, int32_t* iters,
-                      double* illum, int nthreads)
+int oracle_rlof_track_init(const double* I1, const double* I2, int W, int H, const double* pts, int n,
+                           const oracle_rlof_params* prm, const double* init_flow, double* flow,
+                           uint8_t* status, int32_t* iters, double* illum, int nthreads)
 {
     if (!I1 || !I2 || W < 1 || H < 1 || n < 0 || (n > 0 && (!pts || !flow || !status)) ||
         !rlof_params_ok(prm))
@@ -417,7 +422,8 @@ int oracle_rlof_track(const double* I1, const double* I2, int W, int H, const do
 #endif
     for (int k = 0; k < n; ++k) {
         int it = 0;
-        status[k] = (uint8_t)track_point(v1, v2, prm, pts[2 * k], pts[2 * k + 1], flow + 2 * k,
+        status[k] = (uint8_t)track_point(v1, v2, prm, pts[2 * k], pts[2 * k + 1],
+                                         init_flow ? init_flow + 2 * k : NULL, flow + 2 * k,
                                          illum ? illum + 2 * k : NULL, &it);
         if (iters) iters[k] = it;
     }
@@ -425,6 +431,13 @@ done:
     free(pyr1);
     free(pyr2);
     return rc;
+}
+
+int oracle_rlof_track(const double* I1, const double* I2, int W, int H, const double* pts, int n,
+                      const oracle_rlof_params* prm, double* flow, uint8_t* status, int32_t* iters,
+                      double* illum, int nthreads)
+{
+    return oracle_rlof_track_init(I1, I2, W, H, pts, n, prm, NULL, flow, status, iters, illum, nthreads);
 }
 
 int oracle_max_threads(void)
@@ -673,4 +686,96 @@ int oracle_rlof_vjp(const double* I1, const double* I2, int W, int H, const doub
         }
     free(gT); free(gTx); free(gTy); free(Ix); free(Iy); free(lev0);
     return 0;
+}
+
+/* ------------------------------------------------------ global-motion prior */
+
+/*
+ * Global-motion prior (Section 3 "Parameters": RLOF with the global motion model,
+ * RLOF(IM-GM); the paper gives no formula, so the model is read as a global affine
+ * motion q = A p + t fitted robustly to a first pass of tracked points and used as
+ * every point's initial flow for a second pass).
+ *
+ * Affine parameters a[6]: q_x = a0 x + a1 y + a2, q_y = a3 x + a4 y + a5.
+ * Points used: status TRACKED (converged) only; q_i = p_i + flow_i.
+ * Iteratively reweighted least squares, iterations k = 0 .. iters-1:
+ *   k = 0: all weights 1 (least squares);
+ *   k > 0: e_i = |A p_i + t - q_i| with the previous estimate, Tukey biweight
+ *          w_i = (1 - (e_i / c_k)^2)^2 for e_i < c_k, else 0,
+ *          c_k = max(c_min, c0 / 2^(k-1));
+ *   minimise sum w_i |A p_i + t - q_i|^2: the x and y rows share the normal matrix
+ *   M = sum w [x y 1]^T [x y 1] with right-hand sides sum w [x y 1]^T q_x, q_y,
+ *   solved by Cholesky.
+ * A step with fewer than 3 weighted points or a singular normal matrix (a pivot
+ * below 1e-10 of its diagonal entry) keeps the previous estimate and ends the
+ * iterations. Returns 0 on success, 1 when no
+ * estimate was made (then a = identity motion), -1 on bad arguments.
+ */
+/* Cholesky solve of the 3 x 3 normal equations; a pivot below 1e-10 of its
+ * diagonal entry (collinear or repeated points) counts as singular: returns 0. */
+static int solve3(const double M[3][3], const double b[3], double x[3])
+{
+    double L[3][3] = {{0}}, z[3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = M[i][j];
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 1e-10 * M[i][i])) return 0;
+                L[i][i] = sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    for (int i = 0; i < 3; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[i][k] * z[k];
+        z[i] = s / L[i][i];
+    }
+    for (int i = 2; i >= 0; --i) {
+        double s = z[i];
+        for (int k = i + 1; k < 3; ++k) s -= L[k][i] * x[k];
+        x[i] = s / L[i][i];
+    }
+    return 1;
+}
+
+int oracle_gm_fit_affine(const double* pts, const double* flow, const uint8_t* status, int n, int iters,
+                         double c0, double c_min, double* a)
+{
+    if (!a || n < 0 || (n > 0 && (!pts || !flow || !status)) || iters < 1 || !(c0 > 0) || !(c_min > 0)) return -1;
+    const double ident[6] = {1, 0, 0, 0, 1, 0};
+    for (int i = 0; i < 6; ++i) a[i] = ident[i];
+    int made = 0;
+    for (int k = 0; k < iters; ++k) {
+        const double ck = fmax(c_min, ldexp(c0, -(k - 1)));
+        double M[3][3] = {{0}}, bx[3] = {0}, by[3] = {0};
+        int used = 0;
+        for (int i = 0; i < n; ++i) {
+            if (status[i] != OR_TRACKED) continue;
+            const double x = pts[2 * i], y = pts[2 * i + 1];
+            const double qx = x + flow[2 * i], qy = y + flow[2 * i + 1];
+            double w = 1.0;
+            if (k > 0) {
+                const double ex = a[0] * x + a[1] * y + a[2] - qx, ey = a[3] * x + a[4] * y + a[5] - qy;
+                const double e = sqrt(ex * ex + ey * ey);
+                if (e >= ck) continue;
+                const double u = 1.0 - (e / ck) * (e / ck);
+                w = u * u;
+            }
+            const double v[3] = {x, y, 1.0};
+            for (int r = 0; r < 3; ++r) {
+                for (int c = 0; c < 3; ++c) M[r][c] += w * v[r] * v[c];
+                bx[r] += w * v[r] * qx;
+                by[r] += w * v[r] * qy;
+            }
+            ++used;
+        }
+        double sx[3], sy[3];
+        if (used < 3 || !solve3(M, bx, sx) || !solve3(M, by, sy)) break;
+        a[0] = sx[0]; a[1] = sx[1]; a[2] = sx[2];
+        a[3] = sy[0]; a[4] = sy[1]; a[5] = sy[2];
+        made = 1;
+    }
+    return made ? 0 : 1;
 }
