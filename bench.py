@@ -221,6 +221,44 @@ def run_adjoint(dgf, torch, dev, reps: int = 5):
             "ms_per_8_pairs": t, "pairs_per_s": 8 / (t / 1e3)}
 
 
+def run_gm_prior(dgf, torch, dev, pair, reps: int = 20):
+    """The global-motion prior on the 1242x375 pair: plain tracking against
+    rlof_track_gm (sparse first pass every 4th point, affine fit, main pass), both
+    on device-resident pyramids; quality = fraction of non-occluded points tracked
+    (TRACKED) within 2 px of the ground-truth flow."""
+    prm = dgf.RlofParams(levels=WORKLOAD["levels"], radius=WORKLOAD["radius"], max_iter=WORKLOAD["max_iter"],
+                         model=WORKLOAD["model"])
+    gm = dgf.GmParams(extra_levels=0)  # 5 levels already reach the frame's coarsest usable size
+    f1 = torch.from_numpy(pair.I1).to(dev)
+    p1 = dgf.build_pyramid(f1, prm.levels, prm.storage, True)
+    p2 = dgf.build_pyramid(torch.from_numpy(pair.I2).to(dev), prm.levels, prm.storage, False)
+    pts = dgf.detect(f1, WORKLOAD["win"], WORKLOAD["step"])
+    n = pts.shape[0]
+    ws = torch.zeros(dgf.gm_workspace_bytes(n, gm), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    plain = lambda: dgf.track(p1, p2, pair.W, pair.H, pts, prm)
+    prior = lambda: dgf.track_gm(p1, p2, pair.W, pair.H, prm.levels, pts, prm, gm, workspace=ws)
+    t_plain = _timed(torch, dev, plain, reps, flush)
+    t_gm = _timed(torch, dev, prior, reps, flush)
+    P = pts.cpu().numpy()
+    ix = np.clip(np.rint(P[:, 0]), 0, pair.W - 1).astype(int)
+    iy = np.clip(np.rint(P[:, 1]), 0, pair.H - 1).astype(int)
+    gt = pair.flow_gt[iy, ix].astype(np.float64)
+    vis = ~pair.occluded[iy, ix]
+
+    def good(flow, status):
+        f, st = flow.cpu().numpy(), status.cpu().numpy()
+        return float(np.mean(((st == dgf.TRACKED) & (np.hypot(*(f - gt).T) < 2.0))[vis]))
+
+    fp, sp = plain()
+    fg, sg, a, made = prior()
+    return {"workload": "1242x375 driving-scene pair, 5 levels, 11x11: plain tracking vs the global-motion prior "
+                        "(first pass every 4th point, affine Tukey IRLS, main pass from the prior)",
+            "plain_ms": t_plain, "gm_ms": t_gm, "gm_points_per_s": n / (t_gm / 1e3),
+            "within_2px_of_truth": {"plain": good(fp, sp), "gm": good(fg, sg)},
+            "affine": [float(v) for v in a.cpu().numpy()], "fitted": bool(int(made.item()))}
+
+
 def cpu_baseline(pair, reps: int = 2):
     """The FP64 oracle as it stands, on this host's cores, over the full pair."""
     import oracle
@@ -388,6 +426,7 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
             line["batched"] = run_batched(dgf, torch, dev)
             line["fp16_storage"] = run_fp16(dgf, torch, dev)
             line["adjoint"] = run_adjoint(dgf, torch, dev)
+            line["gm_prior"] = run_gm_prior(dgf, torch, dev, pair)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pair)
         print(json.dumps(line), flush=True)

@@ -185,6 +185,53 @@ int rlof_track(const void* pyr1, const void* pyr2, int W, int H, const float* pt
                const dgf_rlof_params* p, float* flow, uint8_t* status, uint8_t* iters,
                float* illum, cudaStream_t stream);
 
+/* ---- global-motion prior (Section 3 "Parameters": RLOF(IM-GM)) ------------ */
+
+#define DGF_GM_PARAMS_VERSION 1
+
+/* The paper runs RLOF with a global motion model and prints no formula. The model
+ * used: a global affine motion q = A p + t (a[6]: q_x = a0 x + a1 y + a2,
+ * q_y = a3 x + a4 y + a5), fitted to a sparse first pass and used as every point's
+ * initial flow (A p + t - p, divided by 2^(levels - 1) at the coarsest level). */
+typedef struct {
+    int version;       /* DGF_GM_PARAMS_VERSION */
+    int stride;        /* first pass tracks points 0, stride, 2 stride, ... (>= 1) */
+    int extra_levels;  /* first pass uses levels + extra_levels pyramid levels (>= 0) */
+    int iters;         /* IRLS iterations of the fit (1 .. 64; 1 = least squares) */
+    double c0, c_min;  /* Tukey threshold c_k = max(c_min, c0 / 2^(k-1)) in pixels, 0 < c_min */
+} dgf_gm_params;
+
+/* Defaults: stride 4, extra_levels 2, iters 8, c0 32, c_min 2. */
+void dgf_gm_params_default(dgf_gm_params* g);
+
+/* Workspace bytes of rlof_track_gm for n points (0 for invalid arguments). Its first
+ * 64 bytes hold, after the call, the fitted affine a[6] (doubles) and an int flag at
+ * byte 48 (1 = fitted; 0 = fewer than 3 converged first-pass points or a singular
+ * fit, a = identity motion). */
+size_t dgf_gm_workspace(int n, const dgf_gm_params* g);
+
+/*
+ * Tracking with the global-motion prior, all on `stream`:
+ *   1. first pass: points k * stride tracked with levels + extra_levels levels;
+ *   2. fit: iteratively reweighted least squares over the first-pass points with
+ *      status DGF_TRACKED: iteration 0 least squares, then Tukey biweights
+ *      (1 - (e / c_k)^2)^2 of the residual distance e (0 beyond c_k); each step
+ *      solves the 3 x 3 normal equations shared by the x and y rows in FP64 (a
+ *      pivot below 1e-10 of its diagonal entry, or fewer than 3 weighted points,
+ *      keeps the previous estimate and ends the fit);
+ *   3. main pass: every point tracked with p->levels levels from the prior's flow.
+ *   pyr1, pyr2  device pyramids built with pyr_levels >= p->levels + extra_levels
+ *               levels (frame 1 with gradients).
+ *   pts, n, flow, status, iters, illum: as for rlof_track (main-pass results).
+ *   workspace   device, >= dgf_gm_workspace(n, g) bytes, 256-byte aligned.
+ * Returns DGF_ERR_ARG for bad parameters or pyr_levels, DGF_ERR_LEVELS when the
+ * first pass's coarsest level is smaller than 2 radius + 2 pixels,
+ * DGF_ERR_WORKSPACE for a short workspace, else the rlof_track codes.
+ */
+int rlof_track_gm(const void* pyr1, const void* pyr2, int W, int H, int pyr_levels, const float* pts, int n,
+                  const dgf_rlof_params* p, const dgf_gm_params* g, float* flow, uint8_t* status,
+                  uint8_t* iters, float* illum, void* workspace, size_t ws_bytes, cudaStream_t stream);
+
 /* ---- adjoints (gradients with respect to the frames; the paper has none) ---- */
 
 /* Workspace bytes of degraf_detect_backward (one record per key-point). */

@@ -23,6 +23,7 @@ STAGE_DETECT, STAGE_PYRAMID, STAGE_TRACK, STAGE_ALL = 1, 2, 4, 7
 MAX_LEVELS = 6
 MAX_RADIUS = 7
 RLOF_PARAMS_VERSION = 1
+GM_PARAMS_VERSION = 1
 
 # Every entry point that include/degraf.h declares.
 EXPORTS = (
@@ -30,6 +31,7 @@ EXPORTS = (
     "dgf_pyramid_bytes", "pyramid_build", "dgf_rlof_params_default", "dgf_rlof_set_lanes", "rlof_track",
     "dgf_track_many_workspace", "rlof_track_many", "rlof_track_pair_noalloc",
     "dgf_degraf_backward_workspace", "degraf_detect_backward", "dgf_rlof_backward_workspace", "rlof_track_backward",
+    "dgf_gm_params_default", "dgf_gm_workspace", "rlof_track_gm",
 )
 
 
@@ -46,6 +48,11 @@ class RlofParamsC(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("model", ctypes.c_int), ("storage", ctypes.c_int),
                 ("eps", ctypes.c_float), ("hampel_a", ctypes.c_float), ("hampel_b", ctypes.c_float),
                 ("hampel_c", ctypes.c_float), ("min_eig", ctypes.c_float)]
+
+
+class GmParamsC(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_int), ("stride", ctypes.c_int), ("extra_levels", ctypes.c_int),
+                ("iters", ctypes.c_int), ("c0", ctypes.c_double), ("c_min", ctypes.c_double)]
 
 
 class PairC(ctypes.Structure):
@@ -105,6 +112,12 @@ def load(build_if_missing: bool = True):
     L.rlof_track_backward.restype = I
     L.rlof_track_pair_noalloc.argtypes = [ctypes.POINTER(PairC), ctypes.POINTER(RlofParamsC), P]
     L.rlof_track_pair_noalloc.restype = I
+    L.dgf_gm_params_default.argtypes = [ctypes.POINTER(GmParamsC)]
+    L.dgf_gm_params_default.restype = None
+    L.dgf_gm_workspace.argtypes, L.dgf_gm_workspace.restype = [I, ctypes.POINTER(GmParamsC)], Z
+    L.rlof_track_gm.argtypes = [P, P, I, I, I, P, I, ctypes.POINTER(RlofParamsC), ctypes.POINTER(GmParamsC), P, P, P,
+                                P, P, Z, P]
+    L.rlof_track_gm.restype = I
     _lib = L
     return L
 

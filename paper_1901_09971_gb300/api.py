@@ -53,6 +53,21 @@ class RlofParams:
                                 self.hampel_c, self.min_eig)
 
 
+@dataclasses.dataclass
+class GmParams:
+    """Global-motion prior parameters (mirror of dgf_gm_params)."""
+
+    stride: int = 4
+    extra_levels: int = 2
+    iters: int = 8
+    c0: float = 32.0
+    c_min: float = 2.0
+
+    def c(self) -> _abi.GmParamsC:
+        return _abi.GmParamsC(_abi.GM_PARAMS_VERSION, self.stride, self.extra_levels, self.iters, self.c0,
+                              self.c_min)
+
+
 def version() -> int:
     return int(load().dgf_version())
 
@@ -147,6 +162,44 @@ def track(pyr1: torch.Tensor, pyr2: torch.Tensor, W: int, H: int, pts: torch.Ten
         res.append(iters)
     if with_illum:
         res.append(illum)
+    return tuple(res)
+
+
+def gm_workspace_bytes(n: int, gm: GmParams) -> int:
+    return int(load().dgf_gm_workspace(n, ctypes.byref(gm.c())))
+
+
+def track_gm(pyr1: torch.Tensor, pyr2: torch.Tensor, W: int, H: int, pyr_levels: int, pts: torch.Tensor,
+             params: RlofParams, gm: GmParams | None = None, with_iters: bool = False, with_illum: bool = False,
+             workspace: torch.Tensor | None = None):
+    """Tracking with the global-motion prior (rlof_track_gm): the pyramids were built
+    with pyr_levels >= params.levels + gm.extra_levels levels. Returns flow, status
+    [, iters][, illum], then the fitted affine (float64 [6], device) and its flag
+    (int32 [1], device; 1 = fitted)."""
+    gm = gm or GmParams()
+    if pts.dtype != torch.float32 or not pts.is_contiguous():
+        raise ValueError("pts must be a contiguous float32 tensor [n, 2]")
+    n = pts.shape[0]
+    dev = pts.device
+    flow = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    status = torch.empty(n, dtype=torch.uint8, device=dev)
+    iters = torch.empty(n, dtype=torch.uint8, device=dev) if with_iters else None
+    illum = torch.empty((n, 2), dtype=torch.float32, device=dev) if with_illum else None
+    need = gm_workspace_bytes(n, gm)
+    if workspace is None:
+        workspace = torch.zeros(max(need, 256), dtype=torch.uint8, device=dev)
+    prm, g = params.c(), gm.c()
+    check("rlof_track_gm", load().rlof_track_gm(_ptr(pyr1), _ptr(pyr2), W, H, pyr_levels, _ptr(pts), n,
+                                                ctypes.byref(prm), ctypes.byref(g), _ptr(flow), _ptr(status),
+                                                _ptr(iters), _ptr(illum), _ptr(workspace), workspace.numel(),
+                                                _stream()))
+    res = [flow, status]
+    if with_iters:
+        res.append(iters)
+    if with_illum:
+        res.append(illum)
+    res.append(workspace[:48].view(torch.float64))
+    res.append(workspace[48:52].view(torch.int32))
     return tuple(res)
 
 

@@ -51,12 +51,14 @@ struct TrackJob {
     uint8_t* status;
     uint8_t* iters;
     float* illum;
-    int pt_begin;  // prefix count of points over the jobs of the launch
+    int pt_begin;         // prefix count of points over the jobs of the launch
+    int pt_stride;        // point k of the job is pts[k * pt_stride] (1: all points)
+    const double* prior;  // global affine motion (6 doubles, device) or null
 };
 
 // Parameters and jobs of one tracking launch (a single pair or a batch).
 struct TrackBatch {
-    int levels, radius, max_iter, es;
+    int levels, pyr_levels, radius, max_iter, es;  // pyr_levels: levels the pyramids were built with
     float eps2, ha, hc, inv_cb, min_eig;
     int n_jobs, total;  // jobs, and points over all jobs
     TrackJob jobs[kMaxBatchPairs];

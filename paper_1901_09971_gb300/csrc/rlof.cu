@@ -618,12 +618,19 @@ __global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const __grid_const
     S.tq = &s_tq[threadIdx.x >> 5][0][threadIdx.x & 31];
     S.ty = &s_ty[threadIdx.x >> 5][0][threadIdx.x & 31];
 
-    const float2 p = reinterpret_cast<const float2*>(J.pts)[pt];
+    const float2 p = reinterpret_cast<const float2*>(J.pts)[(long long)pt * J.pt_stride];
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f, m = 0.f, c = 0.f;
+    if (J.prior) {
+        // global-motion prior: level-0 flow A p + t - p, scaled to the coarsest level
+        const double* q = J.prior;
+        const double x = p.x, y = p.y, s0 = ldexp(1.0, -(a.levels - 1));
+        gx = (float)((q[0] * x + q[1] * y + q[2] - x) * s0);
+        gy = (float)((q[3] * x + q[4] * y + q[5] - y) * s0);
+    }
     int status = DGF_TRACKED, iters = 0;
 
     for (int l = a.levels - 1; l >= 0; --l) {
-        const LevelView<TS> L(J, a.levels, l);
+        const LevelView<TS> L(J, a.pyr_levels, l);
         const float scale = __int_as_float((127 - l) << 23);  // 2^-l
         const float plx = (p.x + 0.5f) * scale - 0.5f, ply = (p.y + 0.5f) * scale - 0.5f;
         if (!setup_level<TS, G, SLP, RC>(S, L, plx, ply, lane, mask, R, a.min_eig)) {
@@ -753,6 +760,7 @@ int prepare_params(const dgf_rlof_params* p, TrackBatch& a)
         !(p->hampel_b >= p->hampel_a) || !(p->hampel_c > p->hampel_b) || !(p->min_eig >= 0.f))
         return DGF_ERR_ARG;
     a.levels = p->levels;
+    a.pyr_levels = p->levels;
     a.radius = p->radius;
     a.max_iter = p->max_iter;
     a.es = p->storage == DGF_F32 ? 4 : 2;
@@ -801,6 +809,6 @@ extern "C" int rlof_track(const void* pyr1, const void* pyr2, int W, int H, cons
     a.n_jobs = 1;
     a.total = n;
     a.jobs[0] = dgf::TrackJob{static_cast<const char*>(pyr1), static_cast<const char*>(pyr2), W, H, pts, flow, status,
-                              iters, illum, 0};
+                              iters, illum, 0, 1, nullptr};
     return dgf::launch_track(a, p, stream);
 }

@@ -103,7 +103,7 @@ int enqueue(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p, const 
             const dgf_pair& P = pairs[c0 + i];
             if (plans[c0 + i].n == 0) continue;
             t.jobs[t.n_jobs++] = dgf::TrackJob{ws + plans[c0 + i].pyr1, ws + plans[c0 + i].pyr2, P.W, P.H, P.pts,
-                                               P.flow, P.status, P.iters, nullptr, (int)total};
+                                               P.flow, P.status, P.iters, nullptr, (int)total, 1, nullptr};
             total += plans[c0 + i].n;
         }
         if (total > 0x7fffffffLL) return DGF_ERR_ARG;

@@ -127,6 +127,35 @@ def test_batch_tracker_run_needs_bound_frames():
         bt.run()
 
 
+def test_gm_host_checks_return_before_launch():
+    lib = dgf.load()
+    prm = dgf.RlofParams(levels=3, radius=4).c()
+    g = _abi.GmParamsC()
+    lib.dgf_gm_params_default(ctypes.byref(g))
+    assert (g.stride, g.extra_levels, g.iters, g.c0, g.c_min) == (4, 2, 8, 32.0, 2.0)
+    n = 1000
+    need = lib.dgf_gm_workspace(n, ctypes.byref(g))
+    n_sub = (n + 3) // 4
+    assert need >= 256 + 8 * n_sub + n_sub and need % 256 == 0
+    fake = ctypes.c_void_p(1 << 20)
+
+    def call(W=640, H=480, pyr_levels=5, ws=need, gp=g, p=prm, npts=n):
+        return lib.rlof_track_gm(fake, fake, W, H, pyr_levels, fake, npts, ctypes.byref(p), ctypes.byref(gp), fake,
+                                 fake, None, None, fake, ws, None)
+
+    assert call(ws=need - 1) == -2                 # short workspace
+    assert call(pyr_levels=4) == -1                # pyramid shallower than levels + extra_levels
+    assert call(pyr_levels=7) == -1                # beyond DGF_MAX_LEVELS
+    assert call(W=100, H=40) == -3                 # first pass's coarsest level too small
+    assert call(npts=0) == 0
+    bad = _abi.GmParamsC(_abi.GM_PARAMS_VERSION, 0, 2, 8, 32.0, 2.0)  # stride 0
+    assert call(gp=bad) == -1 and lib.dgf_gm_workspace(n, ctypes.byref(bad)) == 0
+    bad = _abi.GmParamsC(_abi.GM_PARAMS_VERSION, 4, 2, 0, 32.0, 2.0)  # no iterations
+    assert call(gp=bad) == -1
+    bad = _abi.GmParamsC(_abi.GM_PARAMS_VERSION, 4, 2, 8, 32.0, 0.0)  # c_min 0
+    assert call(gp=bad) == -1
+
+
 def test_product_package_never_loads_the_oracle():
     code = ("import sys; sys.path.insert(0, %r); import paper_1901_09971_gb300 as d; d.load(); "
             "import bench; assert 'oracle' not in sys.modules, 'oracle imported'" % ROOT)
