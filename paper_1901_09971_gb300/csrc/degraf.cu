@@ -101,6 +101,75 @@ __device__ __forceinline__ void window_sums_packed(const Tile& T, int c0, int r0
     m = (int)(mx & 0xffu);
 }
 
+// Sums of the VR consecutive windows of one column (square windows of width W <= 8,
+// step S, all compile-time) from a staged tile: every tile row under the column is
+// read once (rows shared by overlapping windows are not re-summed); row sums, the
+// column-weighted row sums and row-index-weighted row sums become prefix sums over
+// the rows, so a window's S, X and Y are differences of two prefixes
+// (Y = (Q_e - Q_b) - b S for the window's first row b); the maximum comes from a
+// tree of pairwise maxima of the packed row maxima, shared between windows.
+template <int W, int S, int VR>
+__device__ __forceinline__ void column_window_sums(const Tile& T, int c0, int r0, int (&Sv)[VR], int (&Xv)[VR],
+                                                   int (&Yv)[VR], int (&Mv)[VR])
+{
+    static_assert(W >= 1 && W <= 8, "packed rows hold at most 8 bytes");
+    constexpr int R = (VR - 1) * S + W;  // rows under the column's windows
+    constexpr unsigned mlo = W >= 4 ? 0xffffffffu : (1u << (8 * W)) - 1u;
+    constexpr unsigned mhi = W >= 8 ? 0xffffffffu : W <= 4 ? 0u : (1u << (8 * (W - 4))) - 1u;
+    const unsigned* base = reinterpret_cast<const unsigned*>(T.bytes + r0 * T.stride);
+    unsigned mis = T.mis(r0);
+    int P[R + 1], Q[R + 1], PX[R + 1];
+    unsigned rm[R];
+    P[0] = Q[0] = PX[0] = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const unsigned c = (unsigned)c0 + mis;
+        const unsigned* row = base + r * (T.stride >> 2) + (c >> 2);
+        const unsigned shift = (c & 3u) * 8u;
+        const unsigned w0 = row[0], w1 = row[1];
+        const unsigned lo = __funnelshift_r(w0, w1, shift) & mlo;
+        const unsigned hi = W > 4 ? __funnelshift_r(w1, row[2], shift) & mhi : 0u;
+        const int rs = (int)__dp4a(lo, 0x01010101u, __dp4a(hi, 0x01010101u, 0u));
+        const int rx = (int)__dp4a(lo, 0x03020100u, __dp4a(hi, 0x07060504u, 0u));
+        P[r + 1] = P[r] + rs;
+        Q[r + 1] = Q[r] + r * rs;
+        PX[r + 1] = PX[r] + rx;
+        rm[r] = __vmaxu4(lo, hi);
+        mis = (mis + T.pmod) & 3u;
+    }
+    // pairwise maxima over 2 and 4 consecutive rows (unused entries are never formed)
+    unsigned m2[R], m4[R];
+#pragma unroll
+    for (int r = 0; r + 1 < R; ++r) m2[r] = __vmaxu4(rm[r], rm[r + 1]);
+#pragma unroll
+    for (int r = 0; r + 3 < R; ++r) m4[r] = __vmaxu4(m2[r], m2[r + 2]);
+#pragma unroll
+    for (int k = 0; k < VR; ++k) {
+        const int b = k * S, e = b + W;
+        Sv[k] = P[e] - P[b];
+        Xv[k] = PX[e] - PX[b];
+        Yv[k] = (Q[e] - Q[b]) - b * Sv[k];
+        unsigned m = 0u;
+        int i = b;
+        if (W >= 4) {
+            m = m4[i];
+            i += 4;
+        }
+        if (e - i >= 4) {
+            m = __vmaxu4(m, m4[i]);
+            i += 4;
+        }
+        if (e - i >= 2) {
+            m = __vmaxu4(m, m2[i]);
+            i += 2;
+        }
+        if (e - i >= 1) m = __vmaxu4(m, rm[i]);
+        m = __vmaxu4(m, m >> 16);
+        m = __vmaxu4(m, m >> 8);
+        Mv[k] = (int)(m & 0xffu);
+    }
+}
+
 // Window sums of any window size, byte by byte (staged tile or frame rows).
 __device__ __forceinline__ void window_sums_bytes(const uint8_t* w0, int rstride, const Tile* T, int r0, int ww,
                                                   int wh, int& S, int& X, int& Y, int& m)
@@ -164,6 +233,27 @@ __global__ void __launch_bounds__(256) degraf_detect_kernel(const __grid_constan
     }
     const int u = u0 + threadIdx.x;
     if (u >= J.nu) return;
+    // common square windows: the column's four windows at once, rows shared
+    if (a.staged && a.vr == 4 && a.ww == a.wh) {
+        const int key = a.ww * 16 + J.step;
+        if (key == 8 * 16 + 2 || key == 8 * 16 + 3 || key == 8 * 16 + 4 || key == 8 * 16 + 6 || key == 7 * 16 + 3) {
+            int Sv[4], Xv[4], Yv[4], Mv[4];
+            const int c0 = threadIdx.x * J.step, r0 = threadIdx.y * 4 * J.step;
+            switch (key) {
+                case 8 * 16 + 2: column_window_sums<8, 2, 4>(T, c0, r0, Sv, Xv, Yv, Mv); break;
+                case 8 * 16 + 3: column_window_sums<8, 3, 4>(T, c0, r0, Sv, Xv, Yv, Mv); break;
+                case 8 * 16 + 4: column_window_sums<8, 4, 4>(T, c0, r0, Sv, Xv, Yv, Mv); break;
+                case 8 * 16 + 6: column_window_sums<8, 6, 4>(T, c0, r0, Sv, Xv, Yv, Mv); break;
+                default: column_window_sums<7, 3, 4>(T, c0, r0, Sv, Xv, Yv, Mv); break;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int v = v0 + threadIdx.y * 4 + k;
+                if (v < J.nv) emit(J, a.ww, a.wh, u, v, Sv[k], Xv[k], Yv[k], Mv[k]);
+            }
+            return;
+        }
+    }
     for (int k = 0; k < a.vr; ++k) {
         const int wv = threadIdx.y * a.vr + k;  // window row inside the CTA
         const int v = v0 + wv;

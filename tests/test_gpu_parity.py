@@ -41,6 +41,10 @@ DETECT_CASES = [
     ((1242, 375), 7, 7, 3),      # workload 2
     ((1240, 376), 3, 3, 9),      # the paper's KITTI setting (no overlap: direct path)
     ((1280, 720), 8, 8, 2),
+    ((1024, 436), 8, 8, 3),      # batch steps: shared-row column sums
+    ((641, 483), 8, 8, 6),
+    ((333, 211), 7, 7, 3),       # ragged, workload-2 window
+    ((301, 155), 6, 6, 2),       # square window without a column-sum specialisation
     ((97, 61), 5, 9, 2),         # ragged tiles, non-square window
     ((200, 100), 64, 64, 1),     # largest window
     ((300, 90), 64, 33, 70),     # step beyond the window
