@@ -37,7 +37,7 @@ class _RlofParams(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("radius", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("model", ctypes.c_int), ("eps", ctypes.c_double), ("hampel_a", ctypes.c_double),
                 ("hampel_b", ctypes.c_double), ("hampel_c", ctypes.c_double),
-                ("min_eig", ctypes.c_double)]
+                ("min_eig", ctypes.c_double), ("cross_tau", ctypes.c_double)]
 
 
 @dataclasses.dataclass
@@ -51,10 +51,11 @@ class RlofParams:
     hampel_b: float = 16.0
     hampel_c: float = 32.0
     min_eig: float = 1e-3
+    cross_tau: float = 0.0  # adaptive cross-based support threshold; 0: square support
 
     def _c(self) -> _RlofParams:
         return _RlofParams(self.levels, self.radius, self.max_iter, self.model, self.eps,
-                           self.hampel_a, self.hampel_b, self.hampel_c, self.min_eig)
+                           self.hampel_a, self.hampel_b, self.hampel_c, self.min_eig, self.cross_tau)
 
 
 _lib = None
@@ -87,6 +88,8 @@ def lib():
         _lib.oracle_rlof_track_init.argtypes = [P, P, I, I, P, I, ctypes.POINTER(_RlofParams), P, P, P, P,
                                                 P, I]
         _lib.oracle_rlof_track_init.restype = I
+        _lib.oracle_cross_mask.argtypes = [P, I, I, D, D, I, D, P]
+        _lib.oracle_cross_mask.restype = I
         _lib.oracle_gm_fit_affine.argtypes = [P, P, P, I, I, D, D, P]
         _lib.oracle_gm_fit_affine.restype = I
         _lib.oracle_max_threads.argtypes = []
@@ -206,6 +209,18 @@ def rlof_track_gm(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofP
     a, made = gm_fit_affine(sub, fs, ss, iters, c0, c_min)
     flow, status, its, illum = rlof_track(I1, I2, pts, params, nthreads, init_flow=gm_prior_flow(a, pts))
     return flow, status, its, illum, a, made
+
+
+def cross_mask(img: np.ndarray, px: float, py: float, radius: int, tau: float) -> np.ndarray:
+    """The adaptive cross-based support of a point at (px, py) on img (level 0):
+    uint8 [2r+1, 2r+1], 1 for kept support samples (see the C source)."""
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    H, W = img.shape
+    side = 2 * radius + 1
+    m = np.zeros((side, side), np.uint8)
+    if lib().oracle_cross_mask(_ptr(img), W, H, float(px), float(py), int(radius), float(tau), _ptr(m)) < 0:
+        raise ValueError("oracle_cross_mask: bad arguments")
+    return m
 
 
 def gm_prior_flow(a: np.ndarray, pts: np.ndarray) -> np.ndarray:

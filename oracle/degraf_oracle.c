@@ -186,6 +186,7 @@ typedef struct {
     double eps;     /* stop when the translation update is shorter than eps (px) */
     double hampel_a, hampel_b, hampel_c; /* robust norm knots, 0 < a <= b < c */
     double min_eig; /* minimum eigenvalue of the gradient matrix per support pixel */
+    double cross_tau; /* adaptive cross-based support threshold (intensity levels); <= 0: square support */
 } oracle_rlof_params;
 
 /*
@@ -283,6 +284,8 @@ static void pyramid_views(const double* pyr, int W, int H, int levels, level_vie
  *     template T_k, Tx_k, Ty_k = bilinear(I1_l, I1x_l, I1y_l) at p_l + k,
  *       k in [-r, r]^2
  *     if lambda_min(sum_k [Tx Ty]^T [Tx Ty]) / (2r+1)^2 < min_eig: SMALL_EIG, stop
+ *       (with the cross-based support, cross_tau > 0: sums over the kept samples
+ *       only, divided by their number, and every weight w_k below times the mask)
  *     d = 0; for it = 1 .. max_iter:
  *       q = p_l + g + d; if q is outside [0, W_l-1] x [0, H_l-1]: OOB, stop
  *       J_k = bilinear(I2_l) at q + k
@@ -299,13 +302,63 @@ static void pyramid_views(const double* pyr, int W, int H, int levels, level_vie
  * Lost points (OOB, SMALL_EIG, SINGULAR) report flow 0 and illumination 0.
  * Returns the status; *iters counts the Gauss-Newton updates over all levels.
  */
+/*
+ * Adaptive cross-based support (Section 3 "Parameters": RLOF with the adaptive cross
+ * based support region; the paper gives no formula, so this is the reading used).
+ * Around the centre pixel c = p_l rounded half up (clamped into the level), in frame
+ * 1's intensity plane of the level:
+ *   the vertical arm runs from c up and down, at most r pixels each way, while each
+ *   centre-column pixel differs from I(c) by at most tau;
+ *   every row of the vertical arm runs left and right from its centre-column pixel
+ *   a, at most r pixels each way, while each pixel differs from I(a) by at most tau.
+ * Support sample k = (kx, ky) is kept (mask 1) iff pixel c + k lies in the cross: its
+ * row inside the vertical arm and its column inside that row's horizontal arm.
+ * Pixels outside the level are read clamped to the border. Returns the number of
+ * kept samples (at least 1: the centre).
+ */
+static int cross_mask(const level_view* A, double plx, double ply, int r, double tau, unsigned char* mask)
+{
+    const int side = 2 * r + 1;
+    const int cx = clampi((int)floor(plx + 0.5), 0, A->W - 1), cy = clampi((int)floor(ply + 0.5), 0, A->H - 1);
+#define PIX(x, y) A->I[(long)clampi((y), 0, A->H - 1) * A->W + clampi((x), 0, A->W - 1)]
+    const double vc = PIX(cx, cy);
+    int up = 0, dn = 0, n = 0;
+    while (up < r && fabs(PIX(cx, cy - up - 1) - vc) <= tau) ++up;
+    while (dn < r && fabs(PIX(cx, cy + dn + 1) - vc) <= tau) ++dn;
+    for (int ky = -r; ky <= r; ++ky) {
+        int lf = -1, rt = -1;  /* row outside the vertical arm: nothing kept */
+        if (ky >= -up && ky <= dn) {
+            const double va = PIX(cx, cy + ky);
+            lf = rt = 0;
+            while (lf < r && fabs(PIX(cx - lf - 1, cy + ky) - va) <= tau) ++lf;
+            while (rt < r && fabs(PIX(cx + rt + 1, cy + ky) - va) <= tau) ++rt;
+        }
+        for (int kx = -r; kx <= r; ++kx) {
+            const int keep = lf >= 0 && kx >= -lf && kx <= rt;
+            mask[(ky + r) * side + (kx + r)] = (unsigned char)keep;
+            n += keep;
+        }
+    }
+#undef PIX
+    return n;
+}
+
+/* The cross mask of one point at level 0 of frame I1 (W x H doubles), for tests. */
+int oracle_cross_mask(const double* I1, int W, int H, double px, double py, int r, double tau, uint8_t* mask)
+{
+    if (!I1 || W < 1 || H < 1 || r < 1 || r > 15 || !mask) return -1;
+    level_view v = {W, H, I1, NULL, NULL};
+    return cross_mask(&v, px, py, r, tau, mask);
+}
+
 static int track_point(const level_view* P1, const level_view* P2, const oracle_rlof_params* prm,
                        double px, double py, const double* init, double* flow, double* illum, int* iters)
 {
     const int r = prm->radius, side = 2 * r + 1, npx = side * side;
     const int nm = prm->model == 4 ? 4 : 2;
-    double* T = malloc(sizeof(double) * 3 * npx);
-    double *Tx = T + npx, *Ty = T + 2 * npx;
+    double* T = malloc(sizeof(double) * 4 * npx);
+    double *Tx = T + npx, *Ty = T + 2 * npx, *Mk = T + 3 * npx;
+    unsigned char* keep = malloc((size_t)npx);
     /* an initial level-0 flow u starts the coarsest level at g = u / 2^(L-1) */
     const double s0 = ldexp(1.0, -(prm->levels - 1));
     double gx = init ? init[0] * s0 : 0, gy = init ? init[1] * s0 : 0, dx = 0, dy = 0, m = 0, c = 0;
@@ -316,6 +369,12 @@ static int track_point(const level_view* P1, const level_view* P2, const oracle_
         const level_view* B = &P2[l];
         double scale = ldexp(1.0, -l);
         double plx = (px + 0.5) * scale - 0.5, ply = (py + 0.5) * scale - 0.5;
+        /* support mask: the cross (tau > 0) or the whole square */
+        int n_keep = npx;
+        if (prm->cross_tau > 0)
+            n_keep = cross_mask(A, plx, ply, r, prm->cross_tau, keep);
+        else
+            memset(keep, 1, (size_t)npx);
         double G00 = 0, G01 = 0, G11 = 0;
         for (int ky = -r; ky <= r; ++ky)
             for (int kx = -r; kx <= r; ++kx) {
@@ -323,13 +382,14 @@ static int track_point(const level_view* P1, const level_view* P2, const oracle_
                 T[s] = bilinear(A->I, A->W, A->H, plx + kx, ply + ky);
                 Tx[s] = bilinear(A->Ix, A->W, A->H, plx + kx, ply + ky);
                 Ty[s] = bilinear(A->Iy, A->W, A->H, plx + kx, ply + ky);
-                G00 += Tx[s] * Tx[s];
-                G01 += Tx[s] * Ty[s];
-                G11 += Ty[s] * Ty[s];
+                Mk[s] = keep[s];
+                G00 += Mk[s] * Tx[s] * Tx[s];
+                G01 += Mk[s] * Tx[s] * Ty[s];
+                G11 += Mk[s] * Ty[s] * Ty[s];
             }
         double half_tr = 0.5 * (G00 + G11), half_df = 0.5 * (G00 - G11);
         double lam_min = half_tr - sqrt(half_df * half_df + G01 * G01);
-        if (lam_min / npx < prm->min_eig) { status = OR_SMALL_EIG; break; }
+        if (lam_min / n_keep < prm->min_eig) { status = OR_SMALL_EIG; break; }
         dx = dy = 0;
         int converged = 0;
         for (int it = 0; it < prm->max_iter; ++it) {
@@ -348,7 +408,7 @@ static int track_point(const level_view* P1, const level_view* P2, const oracle_
                         res = J - T[s];
                         a[0] = Tx[s]; a[1] = Ty[s];
                     }
-                    double w = hampel_weight(res, prm->hampel_a, prm->hampel_b, prm->hampel_c);
+                    double w = Mk[s] * hampel_weight(res, prm->hampel_a, prm->hampel_b, prm->hampel_c);
                     for (int i = 0; i < nm; ++i) {
                         for (int j = 0; j < nm; ++j) Hm[i][j] += w * a[i] * a[j];
                         bv[i] += w * a[i] * res;
@@ -372,6 +432,7 @@ static int track_point(const level_view* P1, const level_view* P2, const oracle_
         }
     }
     free(T);
+    free(keep);
     if (status == OR_TRACKED || status == OR_MAXITER) {
         flow[0] = gx + dx;
         flow[1] = gy + dy;
@@ -609,7 +670,9 @@ int oracle_rlof_vjp(const double* I1, const double* I2, int W, int H, const doub
                     const oracle_rlof_params* prm, const double* flow, const double* illum, const uint8_t* status,
                     const double* grad_flow, const double* grad_illum, double* grad_I1, double* grad_I2)
 {
-    if (!I1 || !I2 || W < 1 || H < 1 || n < 0 || !rlof_params_ok(prm) || !grad_I1 || !grad_I2) return -1;
+    /* the adjoint is defined for the square support only */
+    if (!I1 || !I2 || W < 1 || H < 1 || n < 0 || !rlof_params_ok(prm) || prm->cross_tau > 0 || !grad_I1 || !grad_I2)
+        return -1;
     const int r = prm->radius, nm = prm->model == 4 ? 4 : 2;
     double* gT = calloc((size_t)W * H, sizeof(double));   /* adjoint of the template plane */
     double* gTx = calloc((size_t)W * H, sizeof(double));  /* adjoint of the Sobel-x plane */
