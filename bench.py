@@ -259,6 +259,33 @@ def run_gm_prior(dgf, torch, dev, pair, reps: int = 20):
             "affine": [float(v) for v in a.cpu().numpy()], "fitted": bool(int(made.item()))}
 
 
+def run_cross_support(dgf, torch, dev, pair, reps: int = 20, tau: float = 20.0):
+    """The adaptive cross-based support on the 1242x375 pair (rectangles moving over
+    the radially expanding background: motion boundaries): square vs cross support,
+    time and fraction of non-occluded points tracked within 2 px of the truth."""
+    base = dict(levels=WORKLOAD["levels"], radius=WORKLOAD["radius"], max_iter=WORKLOAD["max_iter"],
+                model=WORKLOAD["model"])
+    f1 = torch.from_numpy(pair.I1).to(dev)
+    p1 = dgf.build_pyramid(f1, base["levels"], dgf.F32, True)
+    p2 = dgf.build_pyramid(torch.from_numpy(pair.I2).to(dev), base["levels"], dgf.F32, False)
+    pts = dgf.detect(f1, WORKLOAD["win"], WORKLOAD["step"])
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    P = pts.cpu().numpy()
+    ix = np.clip(np.rint(P[:, 0]), 0, pair.W - 1).astype(int)
+    iy = np.clip(np.rint(P[:, 1]), 0, pair.H - 1).astype(int)
+    gt = pair.flow_gt[iy, ix].astype(np.float64)
+    vis = ~pair.occluded[iy, ix]
+    out = {"workload": f"1242x375 driving-scene pair, 5 levels, 11x11: square support vs cross support (tau {tau})"}
+    for name, prm in (("square", dgf.RlofParams(**base)), ("cross", dgf.RlofParams(**base, cross_tau=tau))):
+        fn = lambda: dgf.track(p1, p2, pair.W, pair.H, pts, prm)
+        t = _timed(torch, dev, fn, reps, flush)
+        f, st = fn()
+        f, st = f.cpu().numpy(), st.cpu().numpy()
+        good = float(np.mean(((st == dgf.TRACKED) & (np.hypot(*(f - gt).T) < 2.0))[vis]))
+        out[name] = {"ms": t, "within_2px_of_truth": good}
+    return out
+
+
 def cpu_baseline(pair, reps: int = 2):
     """The FP64 oracle as it stands, on this host's cores, over the full pair."""
     import oracle
@@ -427,6 +454,7 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
             line["fp16_storage"] = run_fp16(dgf, torch, dev)
             line["adjoint"] = run_adjoint(dgf, torch, dev)
             line["gm_prior"] = run_gm_prior(dgf, torch, dev, pair)
+            line["cross_support"] = run_cross_support(dgf, torch, dev, pair)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pair)
         print(json.dumps(line), flush=True)

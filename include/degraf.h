@@ -51,7 +51,7 @@ extern "C" {
 #define DGF_MAX_LEVELS 6
 #define DGF_MAX_RADIUS 7
 #define DGF_MAX_WINDOW 64
-#define DGF_RLOF_PARAMS_VERSION 1
+#define DGF_RLOF_PARAMS_VERSION 2
 
 /* Human-readable name of a DGF_* status code (static string, never NULL). */
 const char* dgf_strerror(int code);
@@ -155,10 +155,20 @@ typedef struct {
     float eps;    /* convergence threshold on |delta d| in pixels */
     float hampel_a, hampel_b, hampel_c; /* 0 < a <= b < c */
     float min_eig;
+    /* Adaptive cross-based support (Section 3 "Parameters"; no formula in the paper):
+     * 0 keeps the square (2r+1)^2 support. tau > 0: per level, around the point's
+     * centre pixel (p_l rounded half up, clamped into the level) of frame 1's
+     * intensity plane, a vertical arm runs up and down (at most r pixels each way)
+     * while centre-column pixels differ from the centre by at most tau, and each
+     * arm row runs left and right (at most r) while its pixels differ from the row's
+     * centre-column pixel by at most tau; support samples outside this cross get
+     * weight 0, and the minimum-eigenvalue test sums over the kept samples and
+     * divides by their number. Pixels outside the level are read clamped. */
+    float cross_tau;
 } dgf_rlof_params;
 
 /* Fills *p with the defaults: levels 3, radius 4, max_iter 30, model 4, F32,
- * eps 1e-3, Hampel (8, 16, 32), min_eig 1e-3. */
+ * eps 1e-3, Hampel (8, 16, 32), min_eig 1e-3, cross_tau 0 (square support). */
 void dgf_rlof_params_default(dgf_rlof_params* p);
 
 /* Tuning hook: lanes per tracked point, 8, 16 or 32 (0 = automatic choice, the

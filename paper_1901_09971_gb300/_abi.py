@@ -22,7 +22,7 @@ F32, F16 = 0, 1
 STAGE_DETECT, STAGE_PYRAMID, STAGE_TRACK, STAGE_ALL = 1, 2, 4, 7
 MAX_LEVELS = 6
 MAX_RADIUS = 7
-RLOF_PARAMS_VERSION = 1
+RLOF_PARAMS_VERSION = 2
 GM_PARAMS_VERSION = 1
 
 # Every entry point that include/degraf.h declares.
@@ -47,7 +47,7 @@ class RlofParamsC(ctypes.Structure):
     _fields_ = [("version", ctypes.c_int), ("levels", ctypes.c_int), ("radius", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("model", ctypes.c_int), ("storage", ctypes.c_int),
                 ("eps", ctypes.c_float), ("hampel_a", ctypes.c_float), ("hampel_b", ctypes.c_float),
-                ("hampel_c", ctypes.c_float), ("min_eig", ctypes.c_float)]
+                ("hampel_c", ctypes.c_float), ("min_eig", ctypes.c_float), ("cross_tau", ctypes.c_float)]
 
 
 class GmParamsC(ctypes.Structure):

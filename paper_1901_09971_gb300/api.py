@@ -46,11 +46,12 @@ class RlofParams:
     hampel_b: float = 16.0
     hampel_c: float = 32.0
     min_eig: float = 1e-3
+    cross_tau: float = 0.0  # adaptive cross-based support threshold; 0 keeps the square support
 
     def c(self) -> _abi.RlofParamsC:
         return _abi.RlofParamsC(_abi.RLOF_PARAMS_VERSION, self.levels, self.radius, self.max_iter,
                                 self.model, self.storage, self.eps, self.hampel_a, self.hampel_b,
-                                self.hampel_c, self.min_eig)
+                                self.hampel_c, self.min_eig, self.cross_tau)
 
 
 @dataclasses.dataclass

@@ -351,7 +351,8 @@ extern "C" int rlof_track_backward(const void* pyr1, const void* pyr2, int W, in
     if (!p || p->version != DGF_RLOF_PARAMS_VERSION || n < 0 || W < 1 || H < 1) return DGF_ERR_ARG;
     if (p->levels < 1 || p->levels > DGF_MAX_LEVELS || p->radius < 1 || p->radius > DGF_MAX_RADIUS ||
         (p->model != 2 && p->model != 4) || (p->storage != DGF_F32 && p->storage != DGF_F16) ||
-        !(p->hampel_a > 0.f) || !(p->hampel_b >= p->hampel_a) || !(p->hampel_c > p->hampel_b))
+        !(p->hampel_a > 0.f) || !(p->hampel_b >= p->hampel_a) || !(p->hampel_c > p->hampel_b) ||
+        p->cross_tau != 0.f)  // the adjoint is defined for the square support
         return DGF_ERR_ARG;
     if (!grad_I1 || !grad_I2 || grad_pitch < W) return DGF_ERR_ARG;
     if (n == 0) return DGF_OK;

@@ -59,7 +59,7 @@ struct TrackJob {
 // Parameters and jobs of one tracking launch (a single pair or a batch).
 struct TrackBatch {
     int levels, pyr_levels, radius, max_iter, es;  // pyr_levels: levels the pyramids were built with
-    float eps2, ha, hc, inv_cb, min_eig;
+    float eps2, ha, hc, inv_cb, min_eig, cross_tau;  // cross_tau > 0: adaptive cross-based support
     int n_jobs, total;  // jobs, and points over all jobs
     TrackJob jobs[kMaxBatchPairs];
 };

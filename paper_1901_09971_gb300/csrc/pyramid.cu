@@ -213,11 +213,13 @@ __device__ __forceinline__ void coarse_levels(const PyrFrame& F, const LevelGeom
     }
 }
 
-// Four blocks per SM for up to four levels (tall tiles, 64 registers), at least two beyond.
+// Six blocks per SM for up to four levels (tall tiles, 40 registers: measured 2.4% faster on the
+// 64-pair batch than four blocks at 64 registers, eight blocks at 32 spill and lose), at least
+// two beyond.
 template <int L>
 constexpr int pyramid_min_blocks()
 {
-    return L <= 4 ? 4 : 2;
+    return L <= 4 ? 6 : 2;
 }
 
 template <typename TS, int L>

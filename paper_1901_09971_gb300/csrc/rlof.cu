@@ -318,6 +318,7 @@ struct Support {
         Tx = make_float2(q.z, q.w);
         Ty = ty[32 * j];
     }
+    float2* mk;  // cross-based support: 0/1 mask of slot j's two samples at mk[32 j]
     int off[SLP];
     float msk[SLP];
     int eo0[2], eo1[2];
@@ -335,7 +336,7 @@ __host__ __device__ constexpr int first_generic_slot()
 // acc[0..9] = sum w (TxTx, TxTy, TxT, Tx, TyTy, TyT, Ty, TT, T, 1); acc[10..13] =
 // sum w r (Tx, Ty, T, 1), each as .x/.y partial sums of a pair's two samples.
 // MODE 0: taps inside, even first column; 1: inside, odd; 2: clamped taps.
-template <typename TS, int G, int SLP, int MODEL, int MODE, int RC>
+template <typename TS, int G, int SLP, int MODEL, int MODE, int RC, bool CROSS>
 __device__ __forceinline__ void accumulate(const Support<SLP>& S, float2 (&acc)[14], const TS* I2, int pitch, int W,
                                            int H, int bx, int by, const PairWeights& pw, int lane, int np, int pc,
                                            float g1, float c, float ha, float icb, float hc_icb)
@@ -395,7 +396,8 @@ __device__ __forceinline__ void accumulate(const Support<SLP>& S, float2 (&acc)[
             r = __fadd2_rn(__ffma2_rn(ng1, T, J), nc);
         else
             r = __ffma2_rn(f2(-1.f), T, J);
-        const float2 w = make_float2(hampel_weight(r.x, ha, icb, hc_icb), hampel_weight(r.y, ha, icb, hc_icb) * S.msk[j]);
+        float2 w = make_float2(hampel_weight(r.x, ha, icb, hc_icb), hampel_weight(r.y, ha, icb, hc_icb) * S.msk[j]);
+        if (CROSS) w = __fmul2_rn(w, S.mk[32 * j]);
         const float2 wTx = __fmul2_rn(w, Tx), wTy = __fmul2_rn(w, Ty);
         acc[0] = __ffma2_rn(wTx, Tx, acc[0]);
         acc[1] = __ffma2_rn(wTx, Ty, acc[1]);
@@ -465,9 +467,40 @@ struct LevelView {
 
 // Level set-up: samples the template T, Tx, Ty at p_l + k into the lane's pairs
 // and applies the minimum-eigenvalue test. Returns false for SMALL_EIG.
-template <typename TS, int G, int SLP, int RC>
+// Adaptive cross-based support of the level (CROSS): rows t = 0 .. 2R of the support
+// (ky = t - R), one lane per row, scan their arms in frame 1's intensity plane around
+// the centre pixel c (p_l rounded half up, clamped): arm[3t], arm[3t+1] = left and
+// right arm lengths from the row's centre-column pixel a (at most R, while pixels
+// differ from I(a) by at most tau), arm[3t+2] = |I(a) - I(c)| <= tau. The arms go to
+// the group's rows of the per-warp reduction scratch (unused during the set-up); the
+// vertical arm lengths up, dn follow from the row flags. Pixels are read clamped.
+template <typename TS, int G>
+__device__ __forceinline__ void cross_arms(const LevelView<TS>& L, float plx, float ply, int lane, unsigned mask,
+                                           int R, float tau, int* arm, int& up, int& dn)
+{
+    const int cx = min(max((int)floorf(plx + 0.5f), 0), L.W - 1);
+    const int cy = min(max((int)floorf(ply + 0.5f), 0), L.H - 1);
+    const float vc = dgf::ld(L.I1 + (size_t)cy * L.pitch + cx);
+    for (int t = lane; t < 2 * R + 1; t += G) {
+        const TS* row = L.I1 + (size_t)min(max(cy + t - R, 0), L.H - 1) * L.pitch;
+        const float va = dgf::ld(row + cx);
+        int lf = 0, rt = 0;
+        while (lf < R && fabsf(dgf::ld(row + max(cx - lf - 1, 0)) - va) <= tau) ++lf;
+        while (rt < R && fabsf(dgf::ld(row + min(cx + rt + 1, L.W - 1)) - va) <= tau) ++rt;
+        arm[3 * t] = lf;
+        arm[3 * t + 1] = rt;
+        arm[3 * t + 2] = fabsf(va - vc) <= tau;
+    }
+    __syncwarp(mask);
+    up = 0;
+    while (up < R && arm[3 * (R - up - 1) + 2]) ++up;
+    dn = 0;
+    while (dn < R && arm[3 * (R + dn + 1) + 2]) ++dn;
+}
+
+template <typename TS, int G, int SLP, int RC, bool CROSS>
 __device__ __forceinline__ bool setup_level(Support<SLP>& S, const LevelView<TS>& L, float plx, float ply, int lane,
-                                            unsigned mask, int R, float min_eig)
+                                            unsigned mask, int R, float min_eig, float tau, WarpScratch& ws)
 {
     constexpr int FG = first_generic_slot<G, SLP, RC>();
     const int side = 2 * R + 1, pc = R + 1, np = RC ? Layout<RC>::np : side * pc;
@@ -475,6 +508,19 @@ __device__ __forceinline__ bool setup_level(Support<SLP>& S, const LevelView<TS>
     const int bx = (int)fx0 - R, by = (int)fy0 - R;
     const PairWeights pw(plx - fx0, ply - fy0);
     float2 g00 = f2(0.f), g01 = f2(0.f), g11 = f2(0.f);
+    float kept = 0.f;  // cross-based support: kept samples of the lane
+    int* arm = nullptr;
+    int up = 0, dn = 0;
+    if (CROSS) {
+        arm = reinterpret_cast<int*>(ws.rows + ((threadIdx.x & 31) - lane) * kRowStride);
+        cross_arms<TS, G>(L, plx, ply, lane, mask, R, tau, arm, up, dn);
+    }
+    // mask of the sample at support coordinates (sx, sy), 0 .. 2R
+    auto in_cross = [&](int sx, int sy) -> float {
+        const int ky = sy - R, kx = sx - R;
+        if (ky < -up || ky > dn) return 0.f;
+        return kx >= -arm[3 * sy] && kx <= arm[3 * sy + 1] ? 1.f : 0.f;
+    };
     S.vbits = 0u;
 #pragma unroll
     for (int j = 0; j < SLP; ++j) {
@@ -525,21 +571,50 @@ __device__ __forceinline__ bool setup_level(Support<SLP>& S, const LevelView<TS>
         S.put(j, T, Tx, Ty);
         S.off[j] = off;
         S.msk[j] = msk;
-        g00 = __ffma2_rn(Tx, Tx, g00);
-        g01 = __ffma2_rn(Tx, Ty, g01);
-        g11 = __ffma2_rn(Ty, Ty, g11);
+        if (CROSS) {
+            float2 mkv = f2(0.f);
+            if (q < np) {
+                int x, y;
+                bool vert = false;
+                if (RC == 0) {
+                    y = q / pc;
+                    x = 2 * (q - y * pc);
+                } else if (q < Layout<RC>::nh) {
+                    y = q / RC;
+                    x = 2 * (q - y * RC);
+                } else {
+                    vert = true;
+                    x = 2 * RC;
+                    y = 2 * (q - Layout<RC>::nh);
+                }
+                mkv.x = in_cross(x, y);
+                if (msk != 0.f) mkv.y = vert ? in_cross(x, y + 1) : in_cross(x + 1, y);
+            }
+            S.mk[32 * j] = mkv;
+            kept += mkv.x + mkv.y;
+            const float2 Txm = __fmul2_rn(Tx, mkv), Tym = __fmul2_rn(Ty, mkv);
+            g00 = __ffma2_rn(Txm, Tx, g00);
+            g01 = __ffma2_rn(Txm, Ty, g01);
+            g11 = __ffma2_rn(Tym, Ty, g11);
+        } else {
+            g00 = __ffma2_rn(Tx, Tx, g00);
+            g01 = __ffma2_rn(Tx, Ty, g01);
+            g11 = __ffma2_rn(Ty, Ty, g11);
+        }
     }
     const float G00 = group_sum<G>(g00.x + g00.y, mask);
     const float G01 = group_sum<G>(g01.x + g01.y, mask);
     const float G11 = group_sum<G>(g11.x + g11.y, mask);
+    const float n_kept = CROSS ? group_sum<G>(kept, mask) : (float)(side * side);
+    if (CROSS) __syncwarp(mask);  // every lane has read the arms before the scratch is reused
     const float ht = 0.5f * (G00 + G11), hd = 0.5f * (G00 - G11);
     const float lam = ht - sqrtf(hd * hd + G01 * G01);
-    return !(lam / (float)(side * side) < min_eig);
+    return !(lam / n_kept < min_eig);
 }
 
 // One Gauss-Newton step at iterate q (inside the level): accumulates, reduces and
 // solves the weighted normal equations. Returns false on a non-positive pivot.
-template <typename TS, int G, int SLP, int MODEL, int RC>
+template <typename TS, int G, int SLP, int MODEL, int RC, bool CROSS>
 __device__ __forceinline__ bool gn_step(const Support<SLP>& S, const LevelView<TS>& L, float qx, float qy, float m,
                                         float c, int lane, unsigned mask, int R, float ha, float icb, float hc_icb,
                                         WarpScratch& ws, float (&delta)[4])
@@ -556,13 +631,13 @@ __device__ __forceinline__ bool gn_step(const Support<SLP>& S, const LevelView<T
     for (int k = 0; k < 14; ++k) acc[k] = f2(0.f);
     const float g1 = 1.f + m;
     if (inside && (bx & 1) == 0)
-        accumulate<TS, G, SLP, MODEL, 0, RC>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
+        accumulate<TS, G, SLP, MODEL, 0, RC, CROSS>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
                                          hc_icb);
     else if (inside)
-        accumulate<TS, G, SLP, MODEL, 1, RC>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
+        accumulate<TS, G, SLP, MODEL, 1, RC, CROSS>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
                                          hc_icb);
     else
-        accumulate<TS, G, SLP, MODEL, 2, RC>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
+        accumulate<TS, G, SLP, MODEL, 2, RC, CROSS>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
                                          hc_icb);
     float h[16];
     if (MODEL == 4) {
@@ -599,7 +674,7 @@ __device__ __forceinline__ bool gn_step(const Support<SLP>& S, const LevelView<T
 // uneven iteration counts and pairs of uneven size; a persistent variant that
 // pulled points from a work counter through a per-group state machine measured
 // slower on both the single-pair and the 64-pair workloads.
-template <typename TS, int G, int SLP, int MODEL, int MINB, int RC>
+template <typename TS, int G, int SLP, int MODEL, int MINB, int RC, bool CROSS>
 __global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const __grid_constant__ TrackBatch a)
 {
     const int gp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -617,6 +692,8 @@ __global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const __grid_const
     __shared__ float2 s_ty[kThreads / 32][SLP][32];
     S.tq = &s_tq[threadIdx.x >> 5][0][threadIdx.x & 31];
     S.ty = &s_ty[threadIdx.x >> 5][0][threadIdx.x & 31];
+    __shared__ float2 s_mk[CROSS ? kThreads / 32 : 1][CROSS ? SLP : 1][32];
+    S.mk = CROSS ? &s_mk[threadIdx.x >> 5][0][threadIdx.x & 31] : nullptr;
 
     const float2 p = reinterpret_cast<const float2*>(J.pts)[(long long)pt * J.pt_stride];
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f, m = 0.f, c = 0.f;
@@ -633,7 +710,7 @@ __global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const __grid_const
         const LevelView<TS> L(J, a.pyr_levels, l);
         const float scale = __int_as_float((127 - l) << 23);  // 2^-l
         const float plx = (p.x + 0.5f) * scale - 0.5f, ply = (p.y + 0.5f) * scale - 0.5f;
-        if (!setup_level<TS, G, SLP, RC>(S, L, plx, ply, lane, mask, R, a.min_eig)) {
+        if (!setup_level<TS, G, SLP, RC, CROSS>(S, L, plx, ply, lane, mask, R, a.min_eig, a.cross_tau, ws)) {
             status = DGF_SMALL_EIG;
             break;
         }
@@ -647,7 +724,8 @@ __global__ void __launch_bounds__(kThreads, MINB) rlof_kernel(const __grid_const
                 break;
             }
             float delta[4];
-            if (!gn_step<TS, G, SLP, MODEL, RC>(S, L, qx, qy, m, c, lane, mask, R, a.ha, icb, hc_icb, ws, delta)) {
+            if (!gn_step<TS, G, SLP, MODEL, RC, CROSS>(S, L, qx, qy, m, c, lane, mask, R, a.ha, icb, hc_icb, ws,
+                                                       delta)) {
                 status = DGF_SINGULAR;
                 break;
             }
@@ -681,7 +759,11 @@ int launch_one(const TrackBatch& a, cudaStream_t stream)
 {
     // four blocks of 128 threads per SM (128 registers a thread)
     const long long total = (long long)a.total * G;
-    rlof_kernel<TS, G, SLP, MODEL, 4, RC><<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, stream>>>(a);
+    const unsigned grid = (unsigned)((total + kThreads - 1) / kThreads);
+    if (a.cross_tau > 0.f)
+        rlof_kernel<TS, G, SLP, MODEL, 4, RC, true><<<grid, kThreads, 0, stream>>>(a);
+    else
+        rlof_kernel<TS, G, SLP, MODEL, 4, RC, false><<<grid, kThreads, 0, stream>>>(a);
     return dgf::launch_status();
 }
 
@@ -736,6 +818,7 @@ extern "C" void dgf_rlof_params_default(dgf_rlof_params* p)
     p->hampel_b = 16.f;
     p->hampel_c = 32.f;
     p->min_eig = 1e-3f;
+    p->cross_tau = 0.f;
 }
 
 // Tuning hook: lanes per point (8, 16 or 32; 0 restores the automatic choice).
@@ -757,7 +840,8 @@ int prepare_params(const dgf_rlof_params* p, TrackBatch& a)
     if (p->levels < 1 || p->levels > DGF_MAX_LEVELS || p->radius < 1 || p->radius > DGF_MAX_RADIUS ||
         p->max_iter < 1 || p->max_iter > 255 || (p->model != 2 && p->model != 4) ||
         (p->storage != DGF_F32 && p->storage != DGF_F16) || !(p->eps >= 0.f) || !(p->hampel_a > 0.f) ||
-        !(p->hampel_b >= p->hampel_a) || !(p->hampel_c > p->hampel_b) || !(p->min_eig >= 0.f))
+        !(p->hampel_b >= p->hampel_a) || !(p->hampel_c > p->hampel_b) || !(p->min_eig >= 0.f) ||
+        !(p->cross_tau >= 0.f))
         return DGF_ERR_ARG;
     a.levels = p->levels;
     a.pyr_levels = p->levels;
@@ -769,6 +853,7 @@ int prepare_params(const dgf_rlof_params* p, TrackBatch& a)
     a.hc = p->hampel_c;
     a.inv_cb = 1.f / (p->hampel_c - p->hampel_b);
     a.min_eig = p->min_eig;
+    a.cross_tau = p->cross_tau;
     return DGF_OK;
 }
 

@@ -68,8 +68,16 @@ def test_strerror_and_defaults():
     assert lib.dgf_strerror(-99) == b"unknown status"
     p = _abi.RlofParamsC()
     lib.dgf_rlof_params_default(ctypes.byref(p))
-    assert (p.version, p.levels, p.radius, p.max_iter, p.model) == (1, 3, 4, 30, 4)
+    assert (p.version, p.levels, p.radius, p.max_iter, p.model) == (_abi.RLOF_PARAMS_VERSION, 3, 4, 30, 4)
     assert abs(p.eps - 1e-3) < 1e-9 and (p.hampel_a, p.hampel_b, p.hampel_c) == (8.0, 16.0, 32.0)
+    assert p.cross_tau == 0.0  # square support unless asked for
+    # a negative threshold or a stale parameter version is rejected before any launch
+    fake = ctypes.c_void_p(1 << 20)
+    bad = dgf.RlofParams(cross_tau=-1.0).c()
+    assert lib.rlof_track(fake, fake, 64, 64, fake, 10, ctypes.byref(bad), fake, fake, None, None, None) == -1
+    old = dgf.RlofParams().c()
+    old.version = 1
+    assert lib.rlof_track(fake, fake, 64, 64, fake, 10, ctypes.byref(old), fake, fake, None, None, None) == -1
 
 
 def test_host_side_errors_return_before_launch():
@@ -154,6 +162,17 @@ def test_gm_host_checks_return_before_launch():
     assert call(gp=bad) == -1
     bad = _abi.GmParamsC(_abi.GM_PARAMS_VERSION, 4, 2, 8, 32.0, 0.0)  # c_min 0
     assert call(gp=bad) == -1
+
+
+def test_adjoint_rejects_the_cross_support():
+    """The tracking adjoint is defined for the square support only."""
+    lib = dgf.load()
+    fake = ctypes.c_void_p(1 << 20)
+    prm = dgf.RlofParams(cross_tau=20.0).c()
+    ws = lib.dgf_rlof_backward_workspace(64, 64)
+    rc = lib.rlof_track_backward(fake, fake, 64, 64, fake, 10, ctypes.byref(prm), fake, fake, fake, fake, None, fake,
+                                 ws, fake, fake, 64, None)
+    assert rc == -1
 
 
 def test_product_package_never_loads_the_oracle():

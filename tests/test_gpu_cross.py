@@ -1,0 +1,100 @@
+"""GPU parity of the adaptive cross-based support (dgf_rlof_params.cross_tau > 0)
+against the oracle's reading (Section 3 "Parameters"): the masks are formed from
+exact pyramid values on both sides, so the tracking bars of the square support
+apply unchanged; a huge tau reproduces the square-support kernel; and at a motion
+boundary the GPU tracks the foreground as the oracle does."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from test_oracle_cross import RECT, two_region_frame
+
+pytestmark = pytest.mark.gpu
+
+TOL_FLOW = 1e-2
+
+
+@pytest.fixture(scope="module")
+def dgf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1901_09971_gb300 as m
+    m.load()
+    return m
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def track_gpu(dgf, I1, I2, pts, prm):
+    H, W = I1.shape
+    p1 = dgf.build_pyramid(to_dev(I1), prm.levels, 0, True)
+    p2 = dgf.build_pyramid(to_dev(I2), prm.levels, 0, False)
+    f, st = dgf.track(p1, p2, W, H, to_dev(pts.astype(np.float32)), prm)
+    torch.cuda.synchronize()
+    return f.cpu().numpy(), st.cpu().numpy()
+
+
+def bars(fg, sg, fo, so, agree_min, within_min):
+    agree = np.mean(sg == so)
+    both = (sg == oracle.TRACKED) & (so == oracle.TRACKED)
+    e = np.hypot(*(fg.astype(np.float64) - fo).T)
+    within = np.mean(e[both] <= TOL_FLOW) if both.any() else 1.0
+    print(f"status agree {agree:.5f}, both tracked {both.sum()}, within {TOL_FLOW}: {within:.5f}")
+    assert agree >= agree_min and within >= within_min
+
+
+# Bars per (workload, tau). Smaller supports are worse conditioned, so FP32 and FP64
+# trajectories part ways more often: an FP32 restatement of the oracle (same masks by
+# construction) agrees with FP64 on 99.90% / 98.55% / 92.41% of statuses and on 100% /
+# 99.76% / 97.83% of both-tracked flows within 1e-2 px for these three cases; the bars
+# sit just below those figures.
+CROSS_BARS = {(1, 20.0): (0.998, 0.999), (2, 20.0): (0.98, 0.995), (2, 8.0): (0.91, 0.97)}
+
+
+@pytest.mark.parametrize("config,tau", list(CROSS_BARS))
+def test_cross_workloads_parity(dgf, config, tau):
+    p = synth.make_pair(config)
+    pts, _, _ = oracle.degraf_detect(p.I1, p.win, p.win, p.step)
+    pts = pts.astype(np.float32).astype(np.float64)
+    prm = dgf.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4, cross_tau=tau)
+    fg, sg = track_gpu(dgf, p.I1, p.I2, pts, prm)
+    fo, so, _, _ = oracle.rlof_track(p.I1, p.I2, pts, oracle.RlofParams(levels=p.levels, radius=p.radius,
+                                                                       max_iter=p.max_iter, model=4, cross_tau=tau))
+    bars(fg, sg, fo, so, *CROSS_BARS[(config, tau)])
+
+
+def test_huge_tau_reproduces_the_square_support_kernel(dgf):
+    p = synth.make_pair(2)
+    pts, _, _ = oracle.degraf_detect(p.I1, p.win, p.win, p.step)
+    base = dict(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4)
+    f0, s0 = track_gpu(dgf, p.I1, p.I2, pts, dgf.RlofParams(**base))
+    f1, s1 = track_gpu(dgf, p.I1, p.I2, pts, dgf.RlofParams(**base, cross_tau=1e9))
+    assert np.mean(s0 == s1) >= 0.999
+    same = (s0 == s1) & (s0 == oracle.TRACKED)
+    assert np.abs(f0[same] - f1[same]).max() <= 1e-4
+
+
+def test_cross_tracks_a_motion_boundary_like_the_oracle(dgf):
+    t = (3.25, 1.5)
+    I1 = two_region_frame(100, 80, RECT)
+    I2 = two_region_frame(100, 80, RECT, shift=t)
+    x0, y0, x1, y1 = RECT
+    pts = []
+    for d in (1.2, 2.4, 3.1):
+        for s in np.linspace(0.3, 0.7, 5):
+            pts += [(x0 + d, y0 + s * (y1 - y0)), (x1 - 1 - d, y0 + s * (y1 - y0)),
+                    (x0 + s * (x1 - x0), y0 + d), (x0 + s * (x1 - x0), y1 - 1 - d)]
+    pts = np.array(pts, np.float32).astype(np.float64)
+    fg, sg = track_gpu(dgf, I1, I2, pts, dgf.RlofParams(levels=2, radius=4, model=2, cross_tau=40.0))
+    fo, so, _, _ = oracle.rlof_track(I1, I2, pts, oracle.RlofParams(levels=2, radius=4, model=2, cross_tau=40.0))
+    e_g = np.hypot(*(fg - np.array(t)).T)
+    e_o = np.hypot(*(fo - np.array(t)).T)
+    print(f"median EPE to the true motion: GPU {np.median(e_g):.3f}, oracle {np.median(e_o):.3f}")
+    assert np.median(e_g) < 0.15
+    assert np.all((sg == oracle.TRACKED) | (sg == oracle.MAXITER))
+    both = (sg == oracle.TRACKED) & (so == oracle.TRACKED)
+    assert np.abs(fg[both] - fo[both]).max() <= TOL_FLOW
