@@ -223,6 +223,29 @@ def cross_mask(img: np.ndarray, px: float, py: float, radius: int, tau: float) -
     return m
 
 
+FB_REJECTED = 5
+
+
+def rlof_track_fb(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofParams, fb_max: float = 0.0,
+                  nthreads: int = 0):
+    """Forward-backward consistency (not in the paper's text; a common filter on
+    sparse tracks): points are tracked from I1 to I2 (flow f), their end points
+    p + f back from I2 to I1 (flow b) with the same parameters; the round-trip error
+    is |f + b| where both passes tracked the point (TRACKED or MAXITER), else +inf.
+    With fb_max > 0, forward-tracked points whose error exceeds fb_max get status
+    FB_REJECTED (5); their flow is kept. Returns (flow, status, fb_err)."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+    f, s, _, _ = rlof_track(I1, I2, pts, params, nthreads)
+    b, sb, _, _ = rlof_track(I2, I1, pts + f, params, nthreads)
+    fwd = (s == TRACKED) | (s == MAXITER)
+    bwd = (sb == TRACKED) | (sb == MAXITER)
+    err = np.where(fwd & bwd, np.hypot(*(f + b).T), np.inf)
+    status = s.copy()
+    if fb_max > 0:
+        status[fwd & (err > fb_max)] = FB_REJECTED
+    return f, status, err
+
+
 def gm_prior_flow(a: np.ndarray, pts: np.ndarray) -> np.ndarray:
     """Initial level-0 flow of each point under the affine motion a: A p + t - p."""
     pts = np.asarray(pts, dtype=np.float64).reshape(-1, 2)
