@@ -286,6 +286,33 @@ def run_cross_support(dgf, torch, dev, pair, reps: int = 20, tau: float = 20.0):
     return out
 
 
+def run_fb_filter(dgf, torch, dev, pair, reps: int = 20, fb_max: float = 1.0):
+    """The forward-backward filter on the 1242x375 pair: its time against one tracking
+    pass, and how often it rejects forward-tracked points that are wrong (more than
+    2 px from the truth) against points that are right."""
+    prm = dgf.RlofParams(levels=WORKLOAD["levels"], radius=WORKLOAD["radius"], max_iter=WORKLOAD["max_iter"],
+                         model=WORKLOAD["model"])
+    f1 = torch.from_numpy(pair.I1).to(dev)
+    p1 = dgf.build_pyramid(f1, prm.levels, dgf.F32, True)
+    p2 = dgf.build_pyramid(torch.from_numpy(pair.I2).to(dev), prm.levels, dgf.F32, True)
+    pts = dgf.detect(f1, WORKLOAD["win"], WORKLOAD["step"])
+    ws = torch.empty(int(dgf.load().dgf_fb_workspace(pts.shape[0])), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    t_one = _timed(torch, dev, lambda: dgf.track(p1, p2, pair.W, pair.H, pts, prm), reps, flush)
+    fb = lambda: dgf.track_fb(p1, p2, pair.W, pair.H, pts, prm, fb_max, workspace=ws)
+    t_fb = _timed(torch, dev, fb, reps, flush)
+    f, st, err = (x.cpu().numpy() for x in fb())
+    P = pts.cpu().numpy()
+    ix = np.clip(np.rint(P[:, 0]), 0, pair.W - 1).astype(int)
+    iy = np.clip(np.rint(P[:, 1]), 0, pair.H - 1).astype(int)
+    wrong = np.hypot(*(f - pair.flow_gt[iy, ix]).T) > 2.0
+    fwd = np.isin(st, [dgf.TRACKED, dgf.MAXITER, dgf.FB_REJECTED])
+    rej = st == dgf.FB_REJECTED
+    return {"workload": f"1242x375 driving-scene pair, 5 levels, 11x11, fb_max {fb_max} px",
+            "one_pass_ms": t_one, "fb_ms": t_fb,
+            "rejected_of_wrong": float(np.mean(rej[fwd & wrong])), "rejected_of_right": float(np.mean(rej[fwd & ~wrong]))}
+
+
 def cpu_baseline(pair, reps: int = 2):
     """The FP64 oracle as it stands, on this host's cores, over the full pair."""
     import oracle
@@ -455,6 +482,7 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
             line["adjoint"] = run_adjoint(dgf, torch, dev)
             line["gm_prior"] = run_gm_prior(dgf, torch, dev, pair)
             line["cross_support"] = run_cross_support(dgf, torch, dev, pair)
+            line["fb_filter"] = run_fb_filter(dgf, torch, dev, pair)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pair)
         print(json.dumps(line), flush=True)

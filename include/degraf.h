@@ -242,6 +242,36 @@ int rlof_track_gm(const void* pyr1, const void* pyr2, int W, int H, int pyr_leve
                   const dgf_rlof_params* p, const dgf_gm_params* g, float* flow, uint8_t* status,
                   uint8_t* iters, float* illum, void* workspace, size_t ws_bytes, cudaStream_t stream);
 
+/* ---- forward-backward consistency (not in the paper's text) ---------------- */
+
+/* Status of a forward-tracked point that failed the forward-backward check. */
+#define DGF_FB_REJECTED 5
+
+/* Workspace bytes of rlof_track_fb for n points (0 for n < 0). */
+size_t dgf_fb_workspace(int n);
+
+/*
+ * Forward-backward consistency filter, a common check on sparse tracks before
+ * interpolation (the paper does not describe one): points are tracked from frame 1
+ * to frame 2 (flow f), their end points p + f back from frame 2 to frame 1 (flow b)
+ * with the same parameters, and the round-trip error is |f + b| where both passes
+ * tracked the point (DGF_TRACKED or DGF_MAXITER), else +inf.
+ *   pyr1, pyr2  device pyramids of both frames, BOTH built with gradients (the
+ *               backward pass uses frame 2 as its template); pyr_bytes is the size
+ *               of each buffer and must be at least dgf_pyramid_bytes(W, H,
+ *               p->levels, p->storage, 1).
+ *   fb_max      > 0: forward-tracked points with an error above fb_max get status
+ *               DGF_FB_REJECTED (their flow is kept); 0: no status changes.
+ *   flow, status  as for rlof_track (forward pass).
+ *   fb_err      device, nullable, float [n]: the round-trip error.
+ *   workspace   device, >= dgf_fb_workspace(n) bytes, 256-byte aligned.
+ * Returns DGF_ERR_ARG for short pyramid buffers or bad arguments,
+ * DGF_ERR_WORKSPACE for a short workspace, else the rlof_track codes.
+ */
+int rlof_track_fb(const void* pyr1, const void* pyr2, size_t pyr_bytes, int W, int H, const float* pts, int n,
+                  const dgf_rlof_params* p, float fb_max, float* flow, uint8_t* status, float* fb_err,
+                  void* workspace, size_t ws_bytes, cudaStream_t stream);
+
 /* ---- adjoints (gradients with respect to the frames; the paper has none) ---- */
 
 /* Workspace bytes of degraf_detect_backward (one record per key-point). */

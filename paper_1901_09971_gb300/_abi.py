@@ -17,7 +17,7 @@ DGF_ERR_CUDA = -4
 DGF_ERR_TIMEOUT = -5
 DGF_ERR_DEVICE = -6
 
-TRACKED, OOB, SMALL_EIG, SINGULAR, MAXITER = 0, 1, 2, 3, 4
+TRACKED, OOB, SMALL_EIG, SINGULAR, MAXITER, FB_REJECTED = 0, 1, 2, 3, 4, 5
 F32, F16 = 0, 1
 STAGE_DETECT, STAGE_PYRAMID, STAGE_TRACK, STAGE_ALL = 1, 2, 4, 7
 MAX_LEVELS = 6
@@ -31,7 +31,7 @@ EXPORTS = (
     "dgf_pyramid_bytes", "pyramid_build", "dgf_rlof_params_default", "dgf_rlof_set_lanes", "rlof_track",
     "dgf_track_many_workspace", "rlof_track_many", "rlof_track_pair_noalloc",
     "dgf_degraf_backward_workspace", "degraf_detect_backward", "dgf_rlof_backward_workspace", "rlof_track_backward",
-    "dgf_gm_params_default", "dgf_gm_workspace", "rlof_track_gm",
+    "dgf_gm_params_default", "dgf_gm_workspace", "rlof_track_gm", "dgf_fb_workspace", "rlof_track_fb",
 )
 
 
@@ -118,6 +118,9 @@ def load(build_if_missing: bool = True):
     L.rlof_track_gm.argtypes = [P, P, I, I, I, P, I, ctypes.POINTER(RlofParamsC), ctypes.POINTER(GmParamsC), P, P, P,
                                 P, P, Z, P]
     L.rlof_track_gm.restype = I
+    L.dgf_fb_workspace.argtypes, L.dgf_fb_workspace.restype = [I], Z
+    L.rlof_track_fb.argtypes = [P, P, Z, I, I, P, I, ctypes.POINTER(RlofParamsC), ctypes.c_float, P, P, P, P, Z, P]
+    L.rlof_track_fb.restype = I
     _lib = L
     return L
 

@@ -204,6 +204,28 @@ def track_gm(pyr1: torch.Tensor, pyr2: torch.Tensor, W: int, H: int, pyr_levels:
     return tuple(res)
 
 
+def track_fb(pyr1: torch.Tensor, pyr2: torch.Tensor, W: int, H: int, pts: torch.Tensor, params: RlofParams,
+             fb_max: float = 0.0, workspace: torch.Tensor | None = None):
+    """Forward-backward consistency filter (rlof_track_fb): both pyramids built with
+    gradients. Returns flow, status (FB_REJECTED where the round-trip error exceeds
+    fb_max > 0) and the round-trip error (float32 [n], +inf where a pass lost the point)."""
+    if pts.dtype != torch.float32 or not pts.is_contiguous():
+        raise ValueError("pts must be a contiguous float32 tensor [n, 2]")
+    n = pts.shape[0]
+    dev = pts.device
+    flow = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    status = torch.empty(n, dtype=torch.uint8, device=dev)
+    err = torch.empty(n, dtype=torch.float32, device=dev)
+    if workspace is None:
+        workspace = torch.empty(max(int(load().dgf_fb_workspace(n)), 256), dtype=torch.uint8, device=dev)
+    nbytes = min(pyr1.numel() * pyr1.element_size(), pyr2.numel() * pyr2.element_size())
+    prm = params.c()
+    check("rlof_track_fb", load().rlof_track_fb(_ptr(pyr1), _ptr(pyr2), nbytes, W, H, _ptr(pts), n, ctypes.byref(prm),
+                                                float(fb_max), _ptr(flow), _ptr(status), _ptr(err), _ptr(workspace),
+                                                workspace.numel(), _stream()))
+    return flow, status, err
+
+
 def detect_backward(frame: torch.Tensor, win: int, step: int, grad_pts: torch.Tensor, win_h: int | None = None,
                     grad_img: torch.Tensor | None = None) -> torch.Tensor:
     """Adds sum_k grad_pts[k] . d(point_k)/d(frame) into grad_img (float32 [H, W])."""

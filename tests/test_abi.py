@@ -164,6 +164,25 @@ def test_gm_host_checks_return_before_launch():
     assert call(gp=bad) == -1
 
 
+def test_fb_host_checks_return_before_launch():
+    lib = dgf.load()
+    prm = dgf.RlofParams(levels=3, radius=4).c()
+    fake = ctypes.c_void_p(1 << 20)
+    W, H, n = 640, 480, 1000
+    full = dgf.pyramid_bytes(W, H, 3, 0, True)
+    ws = lib.dgf_fb_workspace(n)
+    assert ws >= 2 * 8 * n + n and ws % 256 == 0 and lib.dgf_fb_workspace(-1) == 0
+
+    def call(nbytes=full, wsb=ws, fb_max=1.0, npts=n):
+        return lib.rlof_track_fb(fake, fake, nbytes, W, H, fake, npts, ctypes.byref(prm), fb_max, fake, fake, None,
+                                 fake, wsb, None)
+
+    assert call(nbytes=dgf.pyramid_bytes(W, H, 3, 0, False)) == -1  # frame 2 pyramid without gradients
+    assert call(wsb=ws - 1) == -2
+    assert call(fb_max=-1.0) == -1
+    assert call(npts=0) == 0
+
+
 def test_adjoint_rejects_the_cross_support():
     """The tracking adjoint is defined for the square support only."""
     lib = dgf.load()
