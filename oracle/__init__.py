@@ -1,4 +1,4 @@
-"""FP64 CPU oracle of DeGraF detection and RLOF tracking (ctypes wrapper).
+"""FP64 CPU oracle of DeGraF detection, RLOF tracking and EPIC interpolation (ctypes wrapper).
 
 TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the benchmark's
 CPU-baseline leg may use this module; the CUDA product path never imports it.
@@ -92,6 +92,11 @@ def lib():
         _lib.oracle_cross_mask.restype = I
         _lib.oracle_gm_fit_affine.argtypes = [P, P, P, I, I, D, D, P]
         _lib.oracle_gm_fit_affine.restype = I
+        _lib.oracle_epic_cost.argtypes = [P, I, I, I, I, P]
+        _lib.oracle_epic_cost.restype = I
+        _lib.oracle_epic_interpolate.argtypes = [P, I, I, P, P, P, I, ctypes.POINTER(_EpicParams), P, P, P, P, P,
+                                                 P, P, P]
+        _lib.oracle_epic_interpolate.restype = I
         _lib.oracle_max_threads.argtypes = []
         _lib.oracle_max_threads.restype = I
     return _lib
@@ -300,3 +305,69 @@ def rlof_vjp(I1, I2, pts, params: RlofParams, flow, illum, status, grad_flow, gr
 
 def max_threads() -> int:
     return int(lib().oracle_max_threads())
+
+
+class _EpicParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("model", ctypes.c_int), ("cost_base", ctypes.c_int),
+                ("cost_gain", ctypes.c_int), ("a", ctypes.c_double), ("min_spread", ctypes.c_double)]
+
+
+@dataclasses.dataclass
+class EpicParams:
+    k: int = 128           # nearest seeds per fit (Section 3 "Parameters")
+    model: int = 1         # 1: locally affine fit, 0: weighted mean
+    cost_base: int = 4     # edge cost of a flat pixel
+    cost_gain: int = 1     # multiplier of |Gx| + |Gy| (integer Sobel responses)
+    a: float = 0.1         # kernel decay per flat pixel of geodesic travel
+    min_spread: float = 1.0  # px; smallest weighted spread of the neighbours for an affine fit
+
+    def _c(self) -> _EpicParams:
+        return _EpicParams(self.k, self.model, self.cost_base, self.cost_gain, self.a, self.min_spread)
+
+
+@dataclasses.dataclass
+class EpicResult:
+    dense: np.ndarray      # float64 [H, W, 2]
+    labels: np.ndarray     # int32 [H, W], seed of each pixel, -1 where no seed exists
+    dist: np.ndarray       # int64 [H, W], geodesic distance to that seed, -1 where none
+    knn_idx: np.ndarray    # int32 [n, k], the neighbourhood of each seed, nearest first
+    knn_dist: np.ndarray   # int64 [n, k], their seed-graph distances
+    knn_count: np.ndarray  # int32 [n], neighbourhood size (0 for matches that are not seeds)
+    models: np.ndarray     # float64 [n, 6], (A00, A01, A10, A11, b0, b1) per seed
+    fit_kind: np.ndarray   # uint8 [n], 0 not a seed, 1 affine, 2 weighted mean
+
+
+def epic_cost(img: np.ndarray, cost_base: int, cost_gain: int) -> np.ndarray:
+    """Edge cost map of EPIC's geodesic distance (int64 [H, W]; see the C source)."""
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    out = np.zeros((H, W), np.int64)
+    if lib().oracle_epic_cost(_ptr(img), W, H, int(cost_base), int(cost_gain), _ptr(out)) < 0:
+        raise ValueError("oracle_epic_cost: bad arguments")
+    return out
+
+
+def epic_interpolate(img: np.ndarray, pts: np.ndarray, flow: np.ndarray, status: np.ndarray,
+                     params: EpicParams = EpicParams()) -> EpicResult:
+    """Dense flow from sparse matches by edge-preserving interpolation (Section 2,
+    "Interpolation"; the reading is stated in the C source)."""
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+    n = pts.shape[0]
+    flow = np.ascontiguousarray(flow, dtype=np.float64).reshape(n, 2)
+    status = np.ascontiguousarray(status, dtype=np.uint8).reshape(n)
+    k = int(params.k)
+    r = EpicResult(np.zeros((H, W, 2)), np.zeros((H, W), np.int32), np.zeros((H, W), np.int64),
+                   np.full((n, k), -1, np.int32), np.full((n, k), -1, np.int64), np.zeros(n, np.int32),
+                   np.zeros((n, 6)), np.zeros(n, np.uint8))
+    prm = params._c()
+    rc = lib().oracle_epic_interpolate(_ptr(img), W, H, _ptr(pts), _ptr(flow), _ptr(status), n,
+                                       ctypes.byref(prm), _ptr(r.dense), _ptr(r.labels), _ptr(r.dist),
+                                       _ptr(r.knn_idx), _ptr(r.knn_dist), _ptr(r.knn_count), _ptr(r.models),
+                                       _ptr(r.fit_kind))
+    if rc == -1:
+        raise ValueError("oracle_epic_interpolate: bad arguments")
+    if rc < 0:
+        raise MemoryError("oracle_epic_interpolate: out of memory")
+    return r

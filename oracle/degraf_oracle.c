@@ -16,6 +16,8 @@
  *     parameter paragraph of Section 3). The paper gives no formulas for it, so
  *     this file states the reading used (pyramid, gradients, Hampel norm,
  *     illumination model, stopping rule) in the comments of each function.
+ *   - EPIC interpolation of the sparse flow (Section 2, "Interpolation"; k from
+ *     Section 3 "Parameters"): the reading is stated above oracle_epic_interpolate.
  *
  * Parity pins live in tests/test_oracle_*.py; functions without an independent pin
  * are marked "parity unpinned" below.
@@ -841,4 +843,343 @@ int oracle_gm_fit_affine(const double* pts, const double* flow, const uint8_t* s
         made = 1;
     }
     return made ? 0 : 1;
+}
+
+/* ----------------------------------------------------------- EPIC interpolation */
+
+/*
+ * Edge-preserving interpolation of the sparse flow into a dense field (Section 2,
+ * "Interpolation": EPIC with an affine model fitted to the k nearest sparse
+ * vectors under a geodesic distance that penalises crossing image edges, edges
+ * taken from image gradients; Section 3 "Parameters": k = 128). The paper gives no
+ * formulas, so this is the reading used, every distance an exact integer:
+ *
+ *  1. Edge cost of pixel x: C(x) = base + gain (|Gx| + |Gy|), Gx, Gy the integer
+ *     Sobel responses [-1 0 1; -2 0 2; -1 0 1] (and its transpose) of frame 1 with
+ *     clamped borders.
+ *  2. Seeds: the matches with status TRACKED or MAXITER, each at pixel
+ *     (floor(x + 1/2), floor(y + 1/2)) clamped into the image; a seed whose pixel
+ *     holds a lower-index seed is not used.
+ *  3. Geodesic distance on the 4-connected pixel grid, a step between neighbours x
+ *     and y costing C(x) + C(y). Every pixel gets the lexicographically smallest
+ *     (distance, seed index) over all seeds: distance D(x) and label s(x).
+ *  4. Seed graph: 4-adjacent pixels x, y with s(x) != s(y) link the two seeds with
+ *     weight D(x) + C(x) + C(y) + D(y); the edge keeps the smallest such weight.
+ *  5. Neighbourhood of seed s: the k seeds with the smallest (graph distance,
+ *     index), s itself first at distance 0 (all reachable seeds if fewer than k).
+ *  6. Fit: weights w_t = exp(-a d_t / (2 base)) (a per flat pixel of travel).
+ *     model 1 (affine): minimise sum w_t |A (p_t - p_s) + b - f_t|^2; the normal
+ *     matrix M = sum w v v^T, v = (x_t - x_s, y_t - y_s, 1), is solved by Cholesky;
+ *     it is used when there are at least 3 neighbours and the smallest eigenvalue
+ *     of the weighted covariance of their positions is at least min_spread^2
+ *     (px^2); otherwise (too few, or too close to a point or a line for a stable
+ *     slope) the fit falls back to the weighted mean (A = 0). model 0: the
+ *     weighted mean always.
+ *  7. Dense flow of pixel x: A_s(x) (x - p_s(x)) + b_s(x); 0 where no seed exists.
+ */
+typedef struct {
+    int k, model, cost_base, cost_gain;
+    double a, min_spread;
+} oracle_epic_params;
+
+int oracle_epic_cost(const uint8_t* img, int W, int H, int base, int gain, int64_t* cost)
+{
+    if (!img || !cost || W < 1 || H < 1) return -1;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            long gx = 0, gy = 0;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const long v = img[(long)clampi(y + dy, 0, H - 1) * W + clampi(x + dx, 0, W - 1)];
+                    const int wc = dy == 0 ? 2 : 1, wr = dx == 0 ? 2 : 1;  /* smoothing across the axis */
+                    gx += dx * wc * v;
+                    gy += dy * wr * v;
+                }
+            cost[(long)y * W + x] = base + (int64_t)gain * (labs(gx) + labs(gy));
+        }
+    return 0;
+}
+
+/* Binary min-heap of (d, s, v) entries ordered by (d, s). */
+typedef struct {
+    int64_t d;
+    int32_t s, v;
+} ep_item;
+typedef struct {
+    ep_item* a;
+    long n, cap;
+} ep_heap;
+
+static int ep_less(const ep_item* x, const ep_item* y) { return x->d < y->d || (x->d == y->d && x->s < y->s); }
+
+static int ep_push(ep_heap* h, ep_item it)
+{
+    if (h->n == h->cap) {
+        long cap = h->cap ? 2 * h->cap : 1024;
+        ep_item* a = (ep_item*)realloc(h->a, (size_t)cap * sizeof(ep_item));
+        if (!a) return 0;
+        h->a = a;
+        h->cap = cap;
+    }
+    long i = h->n++;
+    while (i > 0) {
+        long p = (i - 1) / 2;
+        if (!ep_less(&it, &h->a[p])) break;
+        h->a[i] = h->a[p];
+        i = p;
+    }
+    h->a[i] = it;
+    return 1;
+}
+
+static ep_item ep_pop(ep_heap* h)
+{
+    ep_item top = h->a[0], last = h->a[--h->n];
+    long i = 0;
+    for (;;) {
+        long c = 2 * i + 1;
+        if (c >= h->n) break;
+        if (c + 1 < h->n && ep_less(&h->a[c + 1], &h->a[c])) ++c;
+        if (!ep_less(&h->a[c], &last)) break;
+        h->a[i] = h->a[c];
+        i = c;
+    }
+    if (h->n > 0) h->a[i] = last;
+    return top;
+}
+
+typedef struct {
+    int32_t s, t;
+    int64_t w;
+} ep_edge;
+
+static int ep_edge_cmp(const void* x, const void* y)
+{
+    const ep_edge *a = (const ep_edge*)x, *b = (const ep_edge*)y;
+    if (a->s != b->s) return a->s < b->s ? -1 : 1;
+    if (a->t != b->t) return a->t < b->t ? -1 : 1;
+    return a->w < b->w ? -1 : (a->w > b->w);
+}
+
+int oracle_epic_interpolate(const uint8_t* img, int W, int H, const double* pts, const double* flow,
+                            const uint8_t* status, int n, const oracle_epic_params* p, double* dense,
+                            int32_t* labels, int64_t* dist, int32_t* knn_idx, int64_t* knn_dist,
+                            int32_t* knn_count, double* models, uint8_t* fit_kind)
+{
+    if (!img || !p || !dense || W < 1 || H < 1 || n < 0 || (n > 0 && (!pts || !flow || !status)) || p->k < 1 ||
+        (p->model != 0 && p->model != 1) || p->cost_base < 1 || p->cost_gain < 0 || !(p->a >= 0) ||
+        !(p->min_spread >= 0))
+        return -1;
+    const long NP = (long)W * H;
+    const int k = p->k;
+    int64_t* C = (int64_t*)malloc((size_t)NP * sizeof(int64_t));
+    int64_t* D = (int64_t*)malloc((size_t)NP * sizeof(int64_t));
+    int32_t* S = (int32_t*)malloc((size_t)NP * sizeof(int32_t));
+    char* done = (char*)calloc((size_t)NP, 1);
+    int32_t* own = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));  /* seed's pixel, -1: not used */
+    ep_heap h = {0};
+    int rc = 0;
+    if (!C || !D || !S || !done || !own) { rc = -2; goto out; }
+    oracle_epic_cost(img, W, H, p->cost_base, p->cost_gain, C);
+
+    /* 2-3. seeds and the multi-source geodesic distance (Dijkstra on (distance, seed)) */
+    for (long i = 0; i < NP; ++i) { D[i] = INT64_MAX; S[i] = -1; }
+    for (int i = 0; i < n; ++i) {
+        own[i] = -1;
+        if (status[i] != OR_TRACKED && status[i] != OR_MAXITER) continue;
+        const int x = clampi((int)floor(pts[2 * i] + 0.5), 0, W - 1);
+        const int y = clampi((int)floor(pts[2 * i + 1] + 0.5), 0, H - 1);
+        const long o = (long)y * W + x;
+        if (S[o] >= 0) continue;  /* a lower-index seed holds the pixel */
+        S[o] = i;
+        D[o] = 0;
+        own[i] = (int32_t)o;
+        if (!ep_push(&h, (ep_item){0, i, (int32_t)o})) { rc = -2; goto out; }
+    }
+    while (h.n > 0) {
+        const ep_item it = ep_pop(&h);
+        if (done[it.v]) continue;
+        if (it.d != D[it.v] || it.s != S[it.v]) continue;  /* superseded entry */
+        done[it.v] = 1;
+        const int x = it.v % W, y = it.v / W;
+        const int nx[4] = {x - 1, x + 1, x, x}, ny[4] = {y, y, y - 1, y + 1};
+        for (int q = 0; q < 4; ++q) {
+            if (nx[q] < 0 || nx[q] >= W || ny[q] < 0 || ny[q] >= H) continue;
+            const long o = (long)ny[q] * W + nx[q];
+            if (done[o]) continue;
+            const ep_item c = {it.d + C[it.v] + C[o], it.s, (int32_t)o};
+            if (S[o] < 0 || c.d < D[o] || (c.d == D[o] && c.s < S[o])) {
+                D[o] = c.d;
+                S[o] = c.s;
+                if (!ep_push(&h, c)) { rc = -2; goto out; }
+            }
+        }
+    }
+
+    /* 4. seed graph: candidate links of 4-adjacent pixels in different cells, the
+     * smallest weight per seed pair kept, stored both ways in CSR form */
+    long ne = 0, ecap = 1024;
+    ep_edge* E = (ep_edge*)malloc((size_t)ecap * sizeof(ep_edge));
+    if (!E) { rc = -2; goto out; }
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const long o = (long)y * W + x;
+            const long nb[2] = {x + 1 < W ? o + 1 : -1, y + 1 < H ? o + W : -1};
+            for (int q = 0; q < 2; ++q) {
+                if (nb[q] < 0 || S[o] < 0 || S[nb[q]] < 0 || S[o] == S[nb[q]]) continue;
+                const int64_t w = D[o] + C[o] + C[nb[q]] + D[nb[q]];
+                if (ne + 2 > ecap) {
+                    ecap *= 2;
+                    ep_edge* e2 = (ep_edge*)realloc(E, (size_t)ecap * sizeof(ep_edge));
+                    if (!e2) { free(E); rc = -2; goto out; }
+                    E = e2;
+                }
+                E[ne++] = (ep_edge){S[o], S[nb[q]], w};
+                E[ne++] = (ep_edge){S[nb[q]], S[o], w};
+            }
+        }
+    qsort(E, (size_t)ne, sizeof(ep_edge), ep_edge_cmp);
+    long nu = 0;  /* keep the first (smallest weight) entry of each (s, t) */
+    for (long i = 0; i < ne; ++i)
+        if (nu == 0 || E[i].s != E[nu - 1].s || E[i].t != E[nu - 1].t) E[nu++] = E[i];
+    long* first = (long*)calloc((size_t)n + 1, sizeof(long));
+    if (!first) { free(E); rc = -2; goto out; }
+    for (long i = 0; i < nu; ++i) first[E[i].s + 1]++;
+    for (int i = 0; i < n; ++i) first[i + 1] += first[i];
+
+    /* 5-6. per-seed neighbourhood (Dijkstra on the seed graph, stopped after k
+     * settled seeds) and the weighted fit; model of seed s in mod[6 s ..]:
+     * (A00, A01, A10, A11, b0, b1) */
+    double* mod = models ? models : (double*)malloc((size_t)(n > 0 ? n : 1) * 6 * sizeof(double));
+    int failed = !mod;
+    if (!failed)
+#pragma omp parallel
+    {
+        ep_heap g = {0};
+        int64_t* best = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+        char* fin = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+        int32_t* touched = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+        if (!best || !fin || !touched) {
+#pragma omp atomic write
+            failed = 1;
+        } else {
+            for (int i = 0; i < n; ++i) best[i] = INT64_MAX;
+#pragma omp for schedule(dynamic, 64)
+            for (int s = 0; s < n; ++s) {
+                double* mo = mod + 6L * s;
+                for (int j = 0; j < 6; ++j) mo[j] = 0.0;
+                if (fit_kind) fit_kind[s] = 0;
+                if (knn_count) knn_count[s] = 0;
+                if (own[s] < 0) continue;
+                int nt = 0, cnt = 0, oom = 0;
+                g.n = 0;
+                best[s] = 0;
+                touched[nt++] = s;
+                if (!ep_push(&g, (ep_item){0, s, s})) oom = 1;
+                double M[3][3] = {{0}}, bu[3] = {0}, bv[3] = {0}, sw = 0, su = 0, sv = 0;
+                const double xs = pts[2 * s], ys = pts[2 * s + 1];
+                while (!oom && g.n > 0 && cnt < k) {
+                    const ep_item it = ep_pop(&g);
+                    if (fin[it.s] || it.d != best[it.s]) continue;  /* superseded entry */
+                    fin[it.s] = 1;
+                    const int t = it.s;
+                    if (knn_idx) knn_idx[(long)s * k + cnt] = t;
+                    if (knn_dist) knn_dist[(long)s * k + cnt] = it.d;
+                    ++cnt;
+                    const double w = exp(-p->a * (double)it.d / (2.0 * p->cost_base));
+                    const double v[3] = {pts[2 * t] - xs, pts[2 * t + 1] - ys, 1.0};
+                    const double fu = flow[2 * t], fv = flow[2 * t + 1];
+                    for (int r = 0; r < 3; ++r) {
+                        for (int c = 0; c < 3; ++c) M[r][c] += w * v[r] * v[c];
+                        bu[r] += w * v[r] * fu;
+                        bv[r] += w * v[r] * fv;
+                    }
+                    sw += w;
+                    su += w * fu;
+                    sv += w * fv;
+                    for (long e = first[t]; e < first[t + 1]; ++e) {
+                        const int u = E[e].t;
+                        const int64_t d = it.d + E[e].w;
+                        if (fin[u] || d >= best[u]) continue;
+                        if (best[u] == INT64_MAX) touched[nt++] = u;
+                        best[u] = d;
+                        if (!ep_push(&g, (ep_item){d, u, u})) { oom = 1; break; }
+                    }
+                }
+                for (int i = 0; i < nt; ++i) { best[touched[i]] = INT64_MAX; fin[touched[i]] = 0; }
+                if (oom) {
+#pragma omp atomic write
+                    failed = 1;
+                    continue;
+                }
+                if (knn_count) knn_count[s] = cnt;
+                double xu[3] = {0, 0, 0}, xv[3] = {0, 0, 0};
+                /* weighted covariance of the neighbours' positions: the Schur
+                 * complement of M's constant term over sum w */
+                int affine = p->model == 1 && cnt >= 3;
+                if (affine) {
+                    const double mx = M[0][2] / sw, my = M[1][2] / sw;
+                    const double cxx = M[0][0] / sw - mx * mx, cxy = M[0][1] / sw - mx * my;
+                    const double cyy = M[1][1] / sw - my * my;
+                    const double h = 0.5 * (cxx - cyy);
+                    const double lmin = 0.5 * (cxx + cyy) - sqrt(h * h + cxy * cxy);
+                    affine = lmin >= p->min_spread * p->min_spread;
+                }
+                if (affine) {
+                    double L[3][3] = {{0}}, zu[3], zv[3];
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j <= i; ++j) {
+                            double a = M[i][j];
+                            for (int q = 0; q < j; ++q) a -= L[i][q] * L[j][q];
+                            if (i == j)
+                                L[i][i] = sqrt(a);
+                            else
+                                L[i][j] = a / L[j][j];
+                        }
+                    for (int i = 0; i < 3; ++i) {
+                        double a = bu[i], b = bv[i];
+                        for (int q = 0; q < i; ++q) { a -= L[i][q] * zu[q]; b -= L[i][q] * zv[q]; }
+                        zu[i] = a / L[i][i];
+                        zv[i] = b / L[i][i];
+                    }
+                    for (int i = 2; i >= 0; --i) {
+                        double a = zu[i], b = zv[i];
+                        for (int q = i + 1; q < 3; ++q) { a -= L[q][i] * xu[q]; b -= L[q][i] * xv[q]; }
+                        xu[i] = a / L[i][i];
+                        xv[i] = b / L[i][i];
+                    }
+                }
+                if (!affine) {
+                    xu[0] = xu[1] = xv[0] = xv[1] = 0.0;
+                    xu[2] = su / sw;
+                    xv[2] = sv / sw;
+                }
+                mo[0] = xu[0]; mo[1] = xu[1]; mo[2] = xv[0]; mo[3] = xv[1]; mo[4] = xu[2]; mo[5] = xv[2];
+                if (fit_kind) fit_kind[s] = affine ? 1 : 2;
+            }
+        }
+        free(g.a); free(best); free(fin); free(touched);
+    }
+    free(first);
+    free(E);
+
+    /* 7. dense flow: every pixel takes its seed's model */
+    if (!failed)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const long o = (long)y * W + x;
+                const int s = S[o];
+                if (labels) labels[o] = s;
+                if (dist) dist[o] = s >= 0 ? D[o] : -1;
+                if (s < 0) { dense[2 * o] = dense[2 * o + 1] = 0.0; continue; }
+                const double* mo = mod + 6L * s;
+                const double dx = x - pts[2 * s], dy = y - pts[2 * s + 1];
+                dense[2 * o] = mo[0] * dx + mo[1] * dy + mo[4];
+                dense[2 * o + 1] = mo[2] * dx + mo[3] * dy + mo[5];
+            }
+    if (mod != models) free(mod);
+    if (failed) rc = -2;
+out:
+    free(h.a); free(C); free(D); free(S); free(done); free(own);
+    return rc;
 }
