@@ -313,6 +313,42 @@ def run_fb_filter(dgf, torch, dev, pair, reps: int = 20, fb_max: float = 1.0):
             "rejected_of_wrong": float(np.mean(rej[fwd & wrong])), "rejected_of_right": float(np.mean(rej[fwd & ~wrong]))}
 
 
+def run_epic(dgf, torch, dev, pair, reps: int = 20):
+    """EPIC interpolation of the 1242x375 pair's sparse flow into a dense field: the
+    time of one epic_interpolate call (k = 128) and the dense end-point error on
+    non-occluded pixels for three sparse inputs: plain tracking, tracking with the
+    global-motion prior, and the ground truth at the key-points (interpolation
+    alone)."""
+    prm = dgf.RlofParams(levels=WORKLOAD["levels"], radius=WORKLOAD["radius"], max_iter=WORKLOAD["max_iter"],
+                         model=WORKLOAD["model"])
+    f1 = torch.from_numpy(pair.I1).to(dev)
+    p1 = dgf.build_pyramid(f1, prm.levels, dgf.F32, True)
+    p2 = dgf.build_pyramid(torch.from_numpy(pair.I2).to(dev), prm.levels, dgf.F32, False)
+    pts = dgf.detect(f1, WORKLOAD["win"], WORKLOAD["step"])
+    n = pts.shape[0]
+    flow, st = dgf.track(p1, p2, pair.W, pair.H, pts, prm)
+    gm = dgf.GmParams(extra_levels=0)  # as in the gm_prior section
+    gflow, gst = dgf.track_gm(p1, p2, pair.W, pair.H, prm.levels, pts, prm, gm)[:2]
+    P = pts.cpu().numpy()
+    ix = np.clip(np.rint(P[:, 0]), 0, pair.W - 1).astype(int)
+    iy = np.clip(np.rint(P[:, 1]), 0, pair.H - 1).astype(int)
+    truth = torch.from_numpy(np.ascontiguousarray(pair.flow_gt[iy, ix], dtype=np.float32)).to(dev)
+    tst = torch.from_numpy(np.where(pair.occluded[iy, ix], dgf.OOB, dgf.TRACKED).astype(np.uint8)).to(dev)
+    ep = dgf.EpicParams()
+    ws = torch.empty(dgf.epic_workspace_bytes(pair.W, pair.H, n), dtype=torch.uint8, device=dev)
+    dense = torch.empty((pair.H, pair.W, 2), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    t = _timed(torch, dev, lambda: dgf.epic_interpolate(f1, pts, flow, st, ep, workspace=ws), reps, flush)
+    vis = ~pair.occluded
+    out = {"workload": f"1242x375 driving-scene pair, {n} key-points, k {ep.k}, affine fits", "ms": t}
+    for name, (fl, ss) in {"plain_tracks": (flow, st), "gm_prior_tracks": (gflow, gst),
+                           "truth_at_keypoints": (truth, tst)}.items():
+        dense = dgf.epic_interpolate(f1, pts, fl.contiguous(), ss.contiguous(), ep, workspace=ws).cpu().numpy()
+        e = np.hypot(*(dense.astype(np.float64) - pair.flow_gt).transpose(2, 0, 1))[vis]
+        out[name] = {"epe_noc_px": float(e.mean()), "fl_noc_over_3px": float(np.mean(e > 3.0))}
+    return out
+
+
 def cpu_baseline(pair, reps: int = 2):
     """The FP64 oracle as it stands, on this host's cores, over the full pair."""
     import oracle
@@ -483,6 +519,7 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
             line["gm_prior"] = run_gm_prior(dgf, torch, dev, pair)
             line["cross_support"] = run_cross_support(dgf, torch, dev, pair)
             line["fb_filter"] = run_fb_filter(dgf, torch, dev, pair)
+            line["epic"] = run_epic(dgf, torch, dev, pair)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pair)
         print(json.dumps(line), flush=True)

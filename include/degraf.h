@@ -272,6 +272,85 @@ int rlof_track_fb(const void* pyr1, const void* pyr2, size_t pyr_bytes, int W, i
                   const dgf_rlof_params* p, float fb_max, float* flow, uint8_t* status, float* fb_err,
                   void* workspace, size_t ws_bytes, cudaStream_t stream);
 
+/* ---- EPIC interpolation (Section 2 "Interpolation"; k from Section 3) ---- */
+
+#define DGF_EPIC_PARAMS_VERSION 1
+#define DGF_EPIC_MAX_K 256
+#define DGF_EPIC_MAX_W_PLUS_H 8192
+#define DGF_EPIC_MAX_POINTS 16777215
+
+/* Parameters of the interpolation (the paper fixes k = 128 and gradient-based
+ * edges; the costs, the kernel and the fallback are this library's reading). */
+typedef struct {
+    int version;       /* DGF_EPIC_PARAMS_VERSION */
+    int k;             /* nearest seeds per fit, 1 .. DGF_EPIC_MAX_K (128) */
+    int model;         /* 1: locally affine fit (default), 0: weighted mean */
+    int cost_base;     /* edge cost of a flat pixel, 1 .. 4096 (4) */
+    int cost_gain;     /* multiplier of |Gx| + |Gy|, 0 .. 32 (1) */
+    double a;          /* kernel decay per flat pixel of geodesic travel, >= 0 (0.1) */
+    double min_spread; /* px; smallest weighted spread of the neighbours for an affine fit (1) */
+} dgf_epic_params;
+
+/* Fills *p with the defaults above. */
+int dgf_epic_params_default(dgf_epic_params* p);
+
+/* Optional device outputs of epic_interpolate, each nullable (for inspection and
+ * tests; knn_idx and knn_dist go together). */
+typedef struct {
+    int32_t* labels;    /* [H][W]: seed of each pixel, -1 where no seed exists */
+    int64_t* dist;      /* [H][W]: geodesic distance to that seed, -1 where none */
+    int32_t* knn_idx;   /* [n][k]: the seed's neighbourhood, nearest first (first knn_count entries) */
+    int64_t* knn_dist;  /* [n][k]: their seed-graph distances */
+    int32_t* knn_count; /* [n]: neighbourhood size, 0 for matches that are not seeds */
+    double* models;     /* [n][6]: (A00, A01, A10, A11, b0, b1), zeros for non-seeds */
+    uint8_t* fit_kind;  /* [n]: 0 not a seed, 1 affine, 2 weighted mean */
+} dgf_epic_debug;
+
+/* Workspace bytes of epic_interpolate (0 for sizes outside the limits). */
+size_t dgf_epic_workspace(int W, int H, int n);
+
+/*
+ * Dense flow from sparse matches by edge-preserving interpolation (Section 2,
+ * "Interpolation": an affine model fitted to the k nearest sparse vectors under a
+ * geodesic distance that penalises crossing image edges, edges from image
+ * gradients). Reading, every distance an exact integer:
+ *   1. edge cost C(x) = cost_base + cost_gain (|Gx| + |Gy|), Gx, Gy the integer
+ *      Sobel responses of frame 1 ([-1 0 1; -2 0 2; -1 0 1] and its transpose,
+ *      clamped borders);
+ *   2. seeds: matches with status DGF_TRACKED or DGF_MAXITER, at pixel
+ *      (floor(x + 1/2), floor(y + 1/2)) clamped into the image; a seed whose pixel
+ *      holds a lower-index seed is not used;
+ *   3. geodesic distance on the 4-connected grid, a step between x and y costing
+ *      C(x) + C(y); every pixel takes the lexicographically smallest (distance,
+ *      seed index) over the seeds: distance D(x), label s(x);
+ *   4. seed graph: 4-adjacent pixels x, y in different cells link s(x) and s(y)
+ *      with weight D(x) + C(x) + C(y) + D(y), the smallest such weight per pair;
+ *   5. neighbourhood of seed s: the k seeds with the smallest (graph distance,
+ *      index), s first;
+ *   6. fit, weights w = exp(-a d / (2 cost_base)): model 1 minimises
+ *      sum w |A (p_t - p_s) + b - f_t|^2 when there are 3+ neighbours and the
+ *      smallest eigenvalue of their weighted position covariance is at least
+ *      min_spread^2, else (and always for model 0) A = 0 and b = the weighted mean;
+ *   7. dense flow of pixel x: A_s(x) (x - p_s(x)) + b_s(x); 0 where no seed exists.
+ *   img         device, uint8 frame 1, row pitch `pitch` bytes (>= W).
+ *   pts, flow   device, float [n][2], 8-byte aligned: match positions and flows.
+ *   status      device, uint8 [n]: the tracking statuses.
+ *   dense       device, float [H][W][2] (contiguous rows of W), 8-byte aligned.
+ *   dbg         host struct of nullable device outputs, or NULL.
+ *   workspace   device, >= dgf_epic_workspace(W, H, n) bytes, 256-byte aligned.
+ * Limits: W + H <= DGF_EPIC_MAX_W_PLUS_H, n <= DGF_EPIC_MAX_POINTS.
+ * Synchronises `stream`: the host reads the labelling's convergence counter every
+ * four relaxation passes and the device status word at the end (so the call
+ * cannot be captured into a CUDA graph).
+ * Returns DGF_ERR_ARG for bad arguments or parameters, DGF_ERR_WORKSPACE for a
+ * short workspace, DGF_ERR_TIMEOUT if the labelling has not converged after 4096
+ * passes, DGF_ERR_DEVICE if a neighbourhood search outgrew its shared-memory
+ * frontier (more than 512 discovered, unsettled seeds), else DGF_OK.
+ */
+int epic_interpolate(const uint8_t* img, int W, int H, int pitch, const float* pts, const float* flow,
+                     const uint8_t* status, int n, const dgf_epic_params* p, float* dense, const dgf_epic_debug* dbg,
+                     void* workspace, size_t ws_bytes, cudaStream_t stream);
+
 /* ---- adjoints (gradients with respect to the frames; the paper has none) ---- */
 
 /* Workspace bytes of degraf_detect_backward (one record per key-point). */

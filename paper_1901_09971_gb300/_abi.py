@@ -24,6 +24,8 @@ MAX_LEVELS = 6
 MAX_RADIUS = 7
 RLOF_PARAMS_VERSION = 2
 GM_PARAMS_VERSION = 1
+EPIC_PARAMS_VERSION = 1
+EPIC_MAX_K = 256
 
 # Every entry point that include/degraf.h declares.
 EXPORTS = (
@@ -32,6 +34,7 @@ EXPORTS = (
     "dgf_track_many_workspace", "rlof_track_many", "rlof_track_pair_noalloc",
     "dgf_degraf_backward_workspace", "degraf_detect_backward", "dgf_rlof_backward_workspace", "rlof_track_backward",
     "dgf_gm_params_default", "dgf_gm_workspace", "rlof_track_gm", "dgf_fb_workspace", "rlof_track_fb",
+    "dgf_epic_params_default", "dgf_epic_workspace", "epic_interpolate",
 )
 
 
@@ -53,6 +56,17 @@ class RlofParamsC(ctypes.Structure):
 class GmParamsC(ctypes.Structure):
     _fields_ = [("version", ctypes.c_int), ("stride", ctypes.c_int), ("extra_levels", ctypes.c_int),
                 ("iters", ctypes.c_int), ("c0", ctypes.c_double), ("c_min", ctypes.c_double)]
+
+
+class EpicParamsC(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_int), ("k", ctypes.c_int), ("model", ctypes.c_int), ("cost_base", ctypes.c_int),
+                ("cost_gain", ctypes.c_int), ("a", ctypes.c_double), ("min_spread", ctypes.c_double)]
+
+
+class EpicDebugC(ctypes.Structure):
+    _fields_ = [("labels", ctypes.c_void_p), ("dist", ctypes.c_void_p), ("knn_idx", ctypes.c_void_p),
+                ("knn_dist", ctypes.c_void_p), ("knn_count", ctypes.c_void_p), ("models", ctypes.c_void_p),
+                ("fit_kind", ctypes.c_void_p)]
 
 
 class PairC(ctypes.Structure):
@@ -121,6 +135,11 @@ def load(build_if_missing: bool = True):
     L.dgf_fb_workspace.argtypes, L.dgf_fb_workspace.restype = [I], Z
     L.rlof_track_fb.argtypes = [P, P, Z, I, I, P, I, ctypes.POINTER(RlofParamsC), ctypes.c_float, P, P, P, P, Z, P]
     L.rlof_track_fb.restype = I
+    L.dgf_epic_params_default.argtypes, L.dgf_epic_params_default.restype = [ctypes.POINTER(EpicParamsC)], I
+    L.dgf_epic_workspace.argtypes, L.dgf_epic_workspace.restype = [I, I, I], Z
+    L.epic_interpolate.argtypes = [P, I, I, I, P, P, P, I, ctypes.POINTER(EpicParamsC), P, ctypes.POINTER(EpicDebugC),
+                                   P, Z, P]
+    L.epic_interpolate.restype = I
     _lib = L
     return L
 

@@ -69,6 +69,22 @@ class GmParams:
                               self.c_min)
 
 
+@dataclasses.dataclass
+class EpicParams:
+    """EPIC interpolation parameters (mirror of dgf_epic_params; k = 128 as in the paper)."""
+
+    k: int = 128
+    model: int = 1  # 1: locally affine, 0: weighted mean
+    cost_base: int = 4
+    cost_gain: int = 1
+    a: float = 0.1
+    min_spread: float = 1.0
+
+    def c(self) -> _abi.EpicParamsC:
+        return _abi.EpicParamsC(_abi.EPIC_PARAMS_VERSION, self.k, self.model, self.cost_base, self.cost_gain, self.a,
+                                self.min_spread)
+
+
 def version() -> int:
     return int(load().dgf_version())
 
@@ -224,6 +240,45 @@ def track_fb(pyr1: torch.Tensor, pyr2: torch.Tensor, W: int, H: int, pts: torch.
                                                 float(fb_max), _ptr(flow), _ptr(status), _ptr(err), _ptr(workspace),
                                                 workspace.numel(), _stream()))
     return flow, status, err
+
+
+def epic_workspace_bytes(W: int, H: int, n: int) -> int:
+    return int(load().dgf_epic_workspace(W, H, n))
+
+
+def epic_interpolate(frame: torch.Tensor, pts: torch.Tensor, flow: torch.Tensor, status: torch.Tensor,
+                     params: EpicParams = EpicParams(), debug: bool = False, workspace: torch.Tensor | None = None):
+    """Dense flow (float32 [H, W, 2]) from sparse matches by EPIC interpolation
+    (epic_interpolate). With debug=True also returns a dict of the labels, geodesic
+    distances, neighbourhoods, per-seed models and fit kinds."""
+    W, H, pitch = _frame(frame)
+    for name, t in (("pts", pts), ("flow", flow)):
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 tensor [n, 2]")
+    if status.dtype != torch.uint8 or not status.is_contiguous():
+        raise ValueError("status must be a contiguous uint8 tensor [n]")
+    n = pts.shape[0]
+    dev = frame.device
+    dense = torch.empty((H, W, 2), dtype=torch.float32, device=dev)
+    if workspace is None:
+        workspace = torch.empty(max(epic_workspace_bytes(W, H, n), 256), dtype=torch.uint8, device=dev)
+    out = None
+    dbg = None
+    if debug:
+        k = params.k
+        out = {"labels": torch.empty((H, W), dtype=torch.int32, device=dev),
+               "dist": torch.empty((H, W), dtype=torch.int64, device=dev),
+               "knn_idx": torch.full((n, k), -1, dtype=torch.int32, device=dev),
+               "knn_dist": torch.full((n, k), -1, dtype=torch.int64, device=dev),
+               "knn_count": torch.empty(n, dtype=torch.int32, device=dev),
+               "models": torch.empty((n, 6), dtype=torch.float64, device=dev),
+               "fit_kind": torch.empty(n, dtype=torch.uint8, device=dev)}
+        dbg = _abi.EpicDebugC(*(_ptr(out[f]) for f, _ in _abi.EpicDebugC._fields_))
+    prm = params.c()
+    check("epic_interpolate", load().epic_interpolate(
+        _ptr(frame), W, H, pitch, _ptr(pts), _ptr(flow), _ptr(status), n, ctypes.byref(prm), _ptr(dense),
+        ctypes.byref(dbg) if dbg is not None else None, _ptr(workspace), workspace.numel(), _stream()))
+    return (dense, out) if debug else dense
 
 
 def detect_backward(frame: torch.Tensor, win: int, step: int, grad_pts: torch.Tensor, win_h: int | None = None,

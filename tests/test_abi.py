@@ -183,6 +183,39 @@ def test_fb_host_checks_return_before_launch():
     assert call(npts=0) == 0
 
 
+def test_epic_host_checks_return_before_launch():
+    lib = dgf.load()
+    d = _abi.EpicParamsC()
+    assert lib.dgf_epic_params_default(ctypes.byref(d)) == 0
+    assert (d.version, d.k, d.model, d.cost_base, d.cost_gain, d.a, d.min_spread) == \
+        (_abi.EPIC_PARAMS_VERSION, 128, 1, 4, 1, 0.1, 1.0)
+    py = dgf.EpicParams()
+    assert (py.k, py.model, py.cost_base, py.cost_gain, py.a, py.min_spread) == (128, 1, 4, 1, 0.1, 1.0)
+    fake = ctypes.c_void_p(1 << 20)
+    W, H, n = 640, 480, 5000
+    ws = lib.dgf_epic_workspace(W, H, n)
+    assert ws % 256 == 0 and ws >= W * H * (8 + 4 + 4 * 12) + n * 48
+    assert lib.dgf_epic_workspace(5000, 3193, 10) == 0 and lib.dgf_epic_workspace(W, H, -1) == 0
+    assert lib.dgf_epic_workspace(W, H, 1 << 24) == 0
+
+    def call(prm=None, w=W, h=H, pitch=W, npts=n, wsb=ws, pts=fake, dense=fake, dbg=None):
+        prm = prm if prm is not None else dgf.EpicParams().c()
+        return lib.epic_interpolate(fake, w, h, pitch, pts, fake, fake, npts, ctypes.byref(prm), dense,
+                                    ctypes.byref(dbg) if dbg is not None else None, fake, wsb, None)
+
+    assert call(wsb=ws - 1) == -2
+    assert call(w=5000, h=3193) == -1 and call(pitch=W - 1) == -1 and call(npts=-1) == -1
+    assert call(pts=None) == -1 and call(dense=ctypes.c_void_p((1 << 20) + 4)) == -1
+    for bad in (dict(k=0), dict(k=257), dict(model=2), dict(cost_base=0), dict(cost_gain=33), dict(a=-1.0),
+                dict(min_spread=float("nan"))):
+        assert call(prm=dgf.EpicParams(**bad).c()) == -1, bad
+    v = dgf.EpicParams().c()
+    v.version = 99
+    assert call(prm=v) == -1
+    half = _abi.EpicDebugC(None, None, fake.value, None, None, None, None)  # knn_idx without knn_dist
+    assert call(dbg=half) == -1
+
+
 def test_adjoint_rejects_the_cross_support():
     """The tracking adjoint is defined for the square support only."""
     lib = dgf.load()
