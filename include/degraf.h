@@ -304,6 +304,7 @@ typedef struct {
     int32_t* knn_count; /* [n]: neighbourhood size, 0 for matches that are not seeds */
     double* models;     /* [n][6]: (A00, A01, A10, A11, b0, b1), zeros for non-seeds */
     uint8_t* fit_kind;  /* [n]: 0 not a seed, 1 affine, 2 weighted mean */
+    int32_t* retried;   /* [1]: searches redone with the large frontier (more than 128 entries) */
 } dgf_epic_debug;
 
 /* Workspace bytes of epic_interpolate (0 for sizes outside the limits). */
@@ -344,8 +345,8 @@ size_t dgf_epic_workspace(int W, int H, int n);
  * cannot be captured into a CUDA graph).
  * Returns DGF_ERR_ARG for bad arguments or parameters, DGF_ERR_WORKSPACE for a
  * short workspace, DGF_ERR_TIMEOUT if the labelling has not converged after 4096
- * passes, DGF_ERR_DEVICE if a neighbourhood search outgrew its shared-memory
- * frontier (more than 512 discovered, unsettled seeds), else DGF_OK.
+ * passes, DGF_ERR_DEVICE if a neighbourhood search outgrew its largest
+ * shared-memory frontier (more than 4096 discovered, unsettled seeds), else DGF_OK.
  */
 int epic_interpolate(const uint8_t* img, int W, int H, int pitch, const float* pts, const float* flow,
                      const uint8_t* status, int n, const dgf_epic_params* p, float* dense, const dgf_epic_debug* dbg,

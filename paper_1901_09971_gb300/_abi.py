@@ -66,7 +66,7 @@ class EpicParamsC(ctypes.Structure):
 class EpicDebugC(ctypes.Structure):
     _fields_ = [("labels", ctypes.c_void_p), ("dist", ctypes.c_void_p), ("knn_idx", ctypes.c_void_p),
                 ("knn_dist", ctypes.c_void_p), ("knn_count", ctypes.c_void_p), ("models", ctypes.c_void_p),
-                ("fit_kind", ctypes.c_void_p)]
+                ("fit_kind", ctypes.c_void_p), ("retried", ctypes.c_void_p)]
 
 
 class PairC(ctypes.Structure):

@@ -272,7 +272,8 @@ def epic_interpolate(frame: torch.Tensor, pts: torch.Tensor, flow: torch.Tensor,
                "knn_dist": torch.full((n, k), -1, dtype=torch.int64, device=dev),
                "knn_count": torch.empty(n, dtype=torch.int32, device=dev),
                "models": torch.empty((n, 6), dtype=torch.float64, device=dev),
-               "fit_kind": torch.empty(n, dtype=torch.uint8, device=dev)}
+               "fit_kind": torch.empty(n, dtype=torch.uint8, device=dev),
+               "retried": torch.zeros(1, dtype=torch.int32, device=dev)}
         dbg = _abi.EpicDebugC(*(_ptr(out[f]) for f, _ in _abi.EpicDebugC._fields_))
     prm = params.c()
     check("epic_interpolate", load().epic_interpolate(

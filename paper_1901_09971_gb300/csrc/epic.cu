@@ -5,7 +5,7 @@
 // the reading, with every distance an exact integer, is stated with
 // epic_interpolate in degraf.h.
 //
-// Seven launches on the caller's stream:
+// Launches on the caller's stream:
 //   1. edge cost C = base + gain (|Gx| + |Gy|) per pixel (integer Sobel), labels cleared;
 //   2. seeds claim their pixels (atomicMin on (distance 0, index)), then keep a
 //      pixel only where they hold it;
@@ -18,12 +18,16 @@
 //   4-6. seed graph: links of 4-adjacent pixels in different cells are counted,
 //      scanned into offsets and filled into per-seed lists (duplicates kept: the
 //      search below takes their minimum);
-//   7. per seed, one warp runs Dijkstra over the seed graph on (distance, index)
-//      keys until k seeds are settled, with the frontier, a hash of discovered
-//      seeds and the settled list in shared memory; then the warp fits the
-//      weighted affine model in FP64 (the 3 x 3 normal equations lose too many
-//      digits in FP32 when a neighbourhood is narrow);
-//   8. dense flow: every pixel evaluates its seed's model.
+//   7-8. each list keeps one link per neighbour (its smallest weight), and every
+//      link records where its neighbour's list lies, so a search reads a popped
+//      seed's links without first loading its list bounds;
+//   9. per seed, one warp runs Dijkstra over the seed graph on (distance, index)
+//      keys until k seeds are settled, with the frontier (128 entries), a hash of
+//      discovered seeds and the settled list in shared memory (32 warps per SM);
+//      then the warp fits the weighted affine model in FP64. A search whose
+//      frontier outgrows 128 entries is queued and redone by a retry kernel with
+//      room for 4096;
+//   10. dense flow: every pixel evaluates its seed's model.
 #include <math.h>
 
 #include "common.cuh"
@@ -37,9 +41,6 @@ constexpr long long kDistLimit = 1ll << 40;  // the distance field of a packed k
 constexpr int kTile = 32;                    // Voronoi tiles: 32 x 32 pixels, 32 x 8 threads
 constexpr int kMaxPasses = 4096;
 constexpr int kPassBatch = 4;
-constexpr int kFCap = 512;   // frontier entries per search
-constexpr int kHCap = 1024;  // hash slots per search (power of two)
-constexpr int kKnnWarps = 4;
 constexpr int kThreads = 256;
 
 // Device status bits (any of them makes the call return DGF_ERR_DEVICE).
@@ -200,30 +201,82 @@ __global__ void __launch_bounds__(kThreads) epic_links_kernel(const unsigned lon
     }
 }
 
-// Exclusive scan of the link counts into offsets (off[n] = total) and cursors.
+// Exclusive scan of the link counts into offsets (off[n] = total) and cursors: one
+// block walks the counts in coalesced tiles of 1024, carrying the running total.
 __global__ void __launch_bounds__(1024) epic_scan_kernel(const int* cnt, int n, int* off, int* cur)
 {
-    __shared__ long long part[1024];
-    const int t = threadIdx.x;
-    const long long per = ((long long)n + 1023) / 1024;
-    const long long b = min((long long)n, t * per), e = min((long long)n, b + per);
-    long long s = 0;
-    for (long long i = b; i < e; ++i) s += cnt[i];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const long long v = t >= o ? part[t - o] : 0;
+    __shared__ int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int carry = 0;
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + t;
+        const int v = i < n ? cnt[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
         __syncthreads();
-        part[t] += v;
+        if (w == 0) {
+            int z = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, z, o);
+                if (lane >= o) z += y;
+            }
+            wsum[lane] = z;
+        }
+        __syncthreads();
+        const int excl = carry + (w ? wsum[w - 1] : 0) + x - v;
+        if (i < n) {
+            off[i] = excl;
+            cur[i] = excl;
+        }
+        carry += wsum[31];
         __syncthreads();
     }
-    long long run = t ? part[t - 1] : 0;
-    for (long long i = b; i < e; ++i) {
-        off[i] = (int)run;
-        cur[i] = (int)run;
-        run += cnt[i];
+    if (t == 0) off[n] = carry;
+}
+
+// Per seed: keeps one link per neighbour (the smallest weight), compacting the list
+// in place; end[s] becomes the end of the compacted list.
+__global__ void __launch_bounds__(kThreads) epic_dedupe_kernel(const int* off, int* end, int* adj_t, long long* adj_w,
+                                                               int n)
+{
+    const int s = blockIdx.x * kThreads + threadIdx.x;
+    if (s >= n) return;
+    const int b = off[s], e = off[s + 1];
+    int out = b;
+    for (int i = b; i < e; ++i) {
+        const int t = adj_t[i];
+        const long long w = adj_w[i];
+        int j = b;
+        for (; j < out; ++j)
+            if (adj_t[j] == t) {
+                if (w < adj_w[j]) adj_w[j] = w;
+                break;
+            }
+        if (j == out) {
+            adj_t[out] = t;
+            adj_w[out] = w;
+            ++out;
+        }
     }
-    if (t == 1023) off[n] = (int)part[1023];
+    end[s] = out;
+}
+
+// Link records for the search: (neighbour, its list begin, its list end).
+__global__ void __launch_bounds__(kThreads) epic_link_meta_kernel(const int* off, const int* end, const int* adj_t,
+                                                                  int4* adj_i, int n)
+{
+    const int s = blockIdx.x * kThreads + threadIdx.x;
+    if (s >= n) return;
+    for (int i = off[s], e = end[s]; i < e; ++i) {
+        const int t = adj_t[i];
+        adj_i[i] = make_int4(t, off[t], end[t], 0);
+    }
 }
 
 struct KnnArgs {
@@ -231,10 +284,13 @@ struct KnnArgs {
     const float2* flow;
     const int* seed_pix;
     const int* off;
-    const int* adj_t;
+    const int* end;
+    const int4* adj_i;
     const long long* adj_w;
     double* models;  // [n][6]
     int* err;
+    int* retry_count;
+    int* retry_list;
     int32_t* knn_idx;
     int64_t* knn_dist;
     int32_t* knn_count;
@@ -242,17 +298,33 @@ struct KnnArgs {
     uint8_t* fit_kind;
     int n, k, model, cost_base;
     double a, min_spread2;
-    size_t warp_bytes;
 };
 
-__device__ __forceinline__ int hslot(int t) { return (int)(((unsigned)t * 0x9E3779B1u) >> (32 - 10)); }
-static_assert(kHCap == 1024, "hslot hashes to 10 bits");
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 
-// Per-warp shared layout: frontier keys, hash keys, hash values (frontier slot of a
-// discovered seed, -2 once settled), the hash slot of each frontier entry, then the
-// settled list (index, distance).
-__host__ __device__ constexpr size_t knn_fixed_bytes() { return kFCap * 8 + kHCap * 4 + kHCap * 2 + kFCap * 2; }
-size_t knn_warp_bytes(int k) { return dgf::round_up(knn_fixed_bytes() + (size_t)k * 4, 8) + (size_t)k * 8; }
+// Per-warp shared layout of one search with a frontier of FCAP entries and a hash
+// of HCAP slots: frontier keys (distance << 24 | index), their link-list bounds and
+// hash slots; hash keys and values (frontier slot of a discovered seed, -2 once
+// settled); then the settled list (index, distance).
+template <int FCAP, int HCAP>
+struct KnnLayout {
+    static_assert((HCAP & (HCAP - 1)) == 0 && HCAP <= 32768 && FCAP <= 32767, "hash and frontier sizes");
+    static constexpr int hash_bits = ilog2(HCAP);
+    static constexpr size_t o_fmeta = (size_t)FCAP * 8;
+    static constexpr size_t o_fhs = o_fmeta + (size_t)FCAP * 8;
+    static constexpr size_t o_hkey = (o_fhs + (size_t)FCAP * 2 + 15) & ~(size_t)15;
+    static constexpr size_t o_hval = o_hkey + (size_t)HCAP * 4;
+    static constexpr size_t fixed = (o_hval + (size_t)HCAP * 2 + 15) & ~(size_t)15;
+    __host__ __device__ static constexpr size_t o_sdist(int k) { return (fixed + (size_t)k * 4 + 7) & ~(size_t)7; }
+    __host__ __device__ static constexpr size_t warp_bytes(int k) { return o_sdist(k) + (size_t)k * 8; }
+};
+
+// The fast search holds every frontier seen on the benchmark scenes (at most 73
+// entries at k = 128); a search that outgrows it is redone by the retry kernel with
+// room for 4096.
+constexpr int kFastF = 128, kFastH = 512, kFastWarps = 8;
+constexpr int kBigF = 4096, kBigH = 8192, kRetryBlocks = 152;
+constexpr int kRetry = 16;  // search status: capacity exceeded, redo with the large layout
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -261,68 +333,76 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-__global__ void __launch_bounds__(kKnnWarps * 32) epic_knn_fit_kernel(KnnArgs a)
+// Dijkstra over the seed graph from seed s on (distance, index) keys until k seeds
+// are settled; the warp's 32 lanes scan the frontier and relax one link each.
+// Returns 0 with the settled list in shared memory, kRetry when the frontier or the
+// hash is full, or kErrRange when a distance leaves the key's 40 bits.
+template <int FCAP, int HCAP>
+__device__ int knn_search(const KnnArgs& a, int s, unsigned char* base, int& cnt_out)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int s = blockIdx.x * kKnnWarps + wid;
-    if (s >= a.n) return;  // warp-uniform
-    unsigned char* base = smem + (size_t)wid * a.warp_bytes;
+    using Lay = KnnLayout<FCAP, HCAP>;
     unsigned long long* fkey = reinterpret_cast<unsigned long long*>(base);
-    int* hkey = reinterpret_cast<int*>(base + kFCap * 8);
-    short* hval = reinterpret_cast<short*>(base + kFCap * 8 + kHCap * 4);
-    short* fhs = reinterpret_cast<short*>(base + kFCap * 8 + kHCap * 6);
-    int* sidx = reinterpret_cast<int*>(base + knn_fixed_bytes());
-    long long* sdist = reinterpret_cast<long long*>(base + dgf::round_up(knn_fixed_bytes() + (size_t)a.k * 4, 8));
+    int2* fmeta = reinterpret_cast<int2*>(base + Lay::o_fmeta);
+    short* fhs = reinterpret_cast<short*>(base + Lay::o_fhs);
+    int* hkey = reinterpret_cast<int*>(base + Lay::o_hkey);
     volatile int* vh = hkey;
-    const int k = a.k;
+    short* hval = reinterpret_cast<short*>(base + Lay::o_hval);
+    int* sidx = reinterpret_cast<int*>(base + Lay::fixed);
+    long long* sdist = reinterpret_cast<long long*>(base + Lay::o_sdist(a.k));
+    const int lane = threadIdx.x & 31;
+    auto slot_of = [](int t) { return (int)(((unsigned)t * 0x9E3779B1u) >> (32 - Lay::hash_bits)); };
 
-    if (a.seed_pix[s] < 0) {
-        if (lane == 0) {
-            if (a.knn_count) a.knn_count[s] = 0;
-            if (a.fit_kind) a.fit_kind[s] = 0;
-        }
-        if (lane < 6) {
-            a.models[6 * (size_t)s + lane] = 0.0;
-            if (a.dbg_models) a.dbg_models[6 * (size_t)s + lane] = 0.0;
-        }
-        return;
-    }
-    for (int j = lane; j < kHCap; j += 32) hkey[j] = -1;
+    for (int j = lane; j < HCAP; j += 32) hkey[j] = -1;
     __syncwarp();
     if (lane == 0) {
-        const int h = hslot(s);
+        const int h = slot_of(s);
         hkey[h] = s;
         hval[h] = 0;
         fkey[0] = (unsigned long long)s;  // distance 0
         fhs[0] = (short)h;
+        fmeta[0] = make_int2(a.off[s], a.end[s]);
     }
     __syncwarp();
-    int fsize = 1, cnt = 0, err = 0;
-    while (cnt < k && fsize > 0) {
-        // pop the smallest (distance, index) key
+    int fsize = 1, cnt = 0, status = 0;
+    while (cnt < a.k && fsize > 0) {
+        // pop the smallest key: lane minima with their slots, then two 32-bit warp minima
         unsigned long long best = kNone;
-        for (int j = lane; j < fsize; j += 32) best = min(best, fkey[j]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-        int slot = -1;
-        for (int j = lane; j < fsize; j += 32)
-            if (fkey[j] == best) slot = j;
-        const unsigned own = __ballot_sync(0xffffffffu, slot >= 0);
-        if (own == 0) {  // every frontier entry holds a key, so this cannot happen
-            if (lane == 0) atomicOr(a.err, kErrFrontier);
-            return;
+        int bslot = -1;
+        for (int j = lane; j < fsize; j += 32) {
+            const unsigned long long v = fkey[j];
+            if (v < best) {
+                best = v;
+                bslot = j;
+            }
         }
-        slot = __shfl_sync(0xffffffffu, slot, __ffs(own) - 1);
-        const int u = (int)(best & kIdxMask);
-        const long long d = (long long)(best >> kIdxBits);
+        const unsigned mhi = __reduce_min_sync(0xffffffffu, (unsigned)(best >> 32));
+        const unsigned mlo = __reduce_min_sync(0xffffffffu, (unsigned)(best >> 32) == mhi ? (unsigned)best : ~0u);
+        const unsigned long long gmin = ((unsigned long long)mhi << 32) | mlo;
+        const unsigned own = __ballot_sync(0xffffffffu, bslot >= 0 && best == gmin);
+        if (own == 0) {  // every frontier entry holds a key, so this cannot happen
+            status = kErrFrontier;
+            break;
+        }
+        const int slot = __shfl_sync(0xffffffffu, bslot, __ffs(own) - 1);
+        const int u = (int)(gmin & kIdxMask);
+        const long long d = (long long)(gmin >> kIdxBits);
+        const int2 m = fmeta[slot];
+        const bool last = cnt + 1 == a.k;  // the k-th seed's links are not needed
+        const int nlk = last ? 0 : m.y - m.x;
+        int4 li = make_int4(-1, 0, 0, 0);
+        long long lw = 0;
+        if (lane < nlk) {  // issue the first links' loads before the bookkeeping
+            li = a.adj_i[m.x + lane];
+            lw = a.adj_w[m.x + lane];
+        }
         __syncwarp();
         if (lane == 0) {
             hval[fhs[slot]] = -2;
-            const int last = fsize - 1;
-            if (slot != last) {
-                fkey[slot] = fkey[last];
-                fhs[slot] = fhs[last];
+            const int L = fsize - 1;
+            if (slot != L) {
+                fkey[slot] = fkey[L];
+                fhs[slot] = fhs[L];
+                fmeta[slot] = fmeta[L];
                 hval[fhs[slot]] = (short)slot;
             }
             sidx[cnt] = u;
@@ -331,20 +411,23 @@ __global__ void __launch_bounds__(kKnnWarps * 32) epic_knn_fit_kernel(KnnArgs a)
         --fsize;
         ++cnt;
         __syncwarp();
-        if (cnt == k) break;  // the k-th settled seed's links are not needed
-        // relax u's links, 32 at a time
-        const int e0 = a.off[u], e1 = a.off[u + 1];
-        for (int e = e0; e < e1; e += 32) {
-            const bool has = e + lane < e1;
-            int t = -1, hs = -1;
+        for (int c0 = 0; c0 < nlk; c0 += 32) {
+            if (c0 > 0) {
+                li = make_int4(-1, 0, 0, 0);
+                if (c0 + lane < nlk) {
+                    li = a.adj_i[m.x + c0 + lane];
+                    lw = a.adj_w[m.x + c0 + lane];
+                }
+            }
+            const bool has = c0 + lane < nlk;
+            const int t = li.x;
+            const long long nd = d + lw;
+            int hs = -1, st = 0;
             bool isnew = false;
-            long long nd = 0;
             if (has) {
-                t = a.adj_t[e + lane];
-                nd = d + a.adj_w[e + lane];
-                if (nd >= kDistLimit) err |= kErrRange;
-                int h = hslot(t);
-                for (int p = 0; p < kHCap; ++p) {
+                if (nd >= kDistLimit) st |= kErrRange;
+                int h = slot_of(t);
+                for (int q = 0; q < HCAP; ++q) {
                     const int c = vh[h];
                     if (c == t) {
                         hs = h;
@@ -358,45 +441,51 @@ __global__ void __launch_bounds__(kKnnWarps * 32) epic_knn_fit_kernel(KnnArgs a)
                             break;
                         }
                     }
-                    h = (h + 1) & (kHCap - 1);
+                    h = (h + 1) & (HCAP - 1);
                 }
-                if (hs < 0) err |= kErrHash;
+                if (hs < 0) st |= kRetry;
             }
             __syncwarp();
             const unsigned nm = __ballot_sync(0xffffffffu, isnew);
             if (isnew) {
                 const int fs = fsize + __popc(nm & ((1u << lane) - 1));
-                if (fs < kFCap) {
+                if (fs < FCAP) {
                     fkey[fs] = kNone;
                     fhs[fs] = (short)hs;
+                    fmeta[fs] = make_int2(li.y, li.z);
                     hval[hs] = (short)fs;
                 } else {
-                    err |= kErrFrontier;
+                    st |= kRetry;
                 }
             }
-            fsize = min(fsize + __popc(nm), kFCap);
+            fsize = min(fsize + __popc(nm), FCAP);
             __syncwarp();
-            if (has && hs >= 0 && !err) {
+            if (has && hs >= 0 && !st) {
                 const int v = hval[hs];
                 if (v >= 0) atomicMin(&fkey[v], ((unsigned long long)nd << kIdxBits) | (unsigned long long)t);
             }
             __syncwarp();
-            if (__any_sync(0xffffffffu, err)) break;
+            status = __reduce_or_sync(0xffffffffu, st);
+            if (status) break;
         }
-        const int any = __reduce_or_sync(0xffffffffu, err);
-        if (any) {
-            if (lane == 0) atomicOr(a.err, any);
-            return;
-        }
+        if (status) break;
     }
-    __syncwarp();
+    cnt_out = cnt;
+    return status & kErrRange ? kErrRange : status;
+}
+
+// The weighted affine fit of seed s over its settled list (FP64; the 3 x 3 normal
+// equations lose too many digits in FP32 when a neighbourhood is narrow) and the
+// outputs. M = sum w v v^T, v = (x_t - x_s, y_t - y_s, 1).
+__device__ void knn_fit_write(const KnnArgs& a, int s, int cnt, const int* sidx, const long long* sdist)
+{
+    const int lane = threadIdx.x & 31, k = a.k;
     if (a.knn_count && lane == 0) a.knn_count[s] = cnt;
     if (a.knn_idx)
         for (int j = lane; j < cnt; j += 32) {
             a.knn_idx[(size_t)s * k + j] = sidx[j];
             a.knn_dist[(size_t)s * k + j] = sdist[j];
         }
-    // weighted normal equations, FP64; M = sum w v v^T, v = (x_t - x_s, y_t - y_s, 1)
     const float2 ps = a.pts[s];
     double m00 = 0, m01 = 0, m02 = 0, m11 = 0, m12 = 0, m22 = 0, u0 = 0, u1 = 0, u2 = 0, v0 = 0, v1 = 0, v2 = 0;
     for (int j = lane; j < cnt; j += 32) {
@@ -448,6 +537,60 @@ __global__ void __launch_bounds__(kKnnWarps * 32) epic_knn_fit_kernel(KnnArgs a)
     if (a.fit_kind) a.fit_kind[s] = affine ? 1 : 2;
 }
 
+// One warp per seed with the fast layout; searches that outgrow it are queued for
+// the retry kernel.
+__global__ void __launch_bounds__(kFastWarps * 32) epic_knn_fit_kernel(KnnArgs a)
+{
+    using Lay = KnnLayout<kFastF, kFastH>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int s = blockIdx.x * kFastWarps + wid;
+    if (s >= a.n) return;  // warp-uniform
+    if (a.seed_pix[s] < 0) {
+        if (lane == 0) {
+            if (a.knn_count) a.knn_count[s] = 0;
+            if (a.fit_kind) a.fit_kind[s] = 0;
+        }
+        if (lane < 6) {
+            a.models[6 * (size_t)s + lane] = 0.0;
+            if (a.dbg_models) a.dbg_models[6 * (size_t)s + lane] = 0.0;
+        }
+        return;
+    }
+    unsigned char* base = smem + (size_t)wid * Lay::warp_bytes(a.k);
+    int cnt = 0;
+    const int st = knn_search<kFastF, kFastH>(a, s, base, cnt);
+    if (st == kRetry) {
+        if (lane == 0) a.retry_list[atomicAdd(a.retry_count, 1)] = s;
+        return;
+    }
+    if (st) {
+        if (lane == 0) atomicOr(a.err, st);
+        return;
+    }
+    knn_fit_write(a, s, cnt, reinterpret_cast<const int*>(base + Lay::fixed),
+                  reinterpret_cast<const long long*>(base + Lay::o_sdist(a.k)));
+}
+
+// The queued searches with room for 4096 frontier entries, one warp per block.
+__global__ void __launch_bounds__(32) epic_knn_retry_kernel(KnnArgs a)
+{
+    using Lay = KnnLayout<kBigF, kBigH>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int total = *a.retry_count;
+    for (int i = blockIdx.x; i < total; i += gridDim.x) {
+        const int s = a.retry_list[i];
+        int cnt = 0;
+        const int st = knn_search<kBigF, kBigH>(a, s, smem, cnt);
+        if (st) {
+            if ((threadIdx.x & 31) == 0) atomicOr(a.err, st == kRetry ? kErrFrontier : st);
+            continue;
+        }
+        knn_fit_write(a, s, cnt, reinterpret_cast<const int*>(smem + Lay::fixed),
+                      reinterpret_cast<const long long*>(smem + Lay::o_sdist(a.k)));
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) epic_dense_kernel(const unsigned long long* key, const double* models,
                                                               const float2* pts, int W, int H, float2* dense,
                                                               int32_t* labels, int64_t* dist)
@@ -473,7 +616,7 @@ __global__ void __launch_bounds__(kThreads) epic_dense_kernel(const unsigned lon
 
 // Workspace layout (256-byte aligned sections).
 struct EpicLayout {
-    size_t key, cost, seed_pix, cnt, off, cur, adj_t, adj_w, models, counters, total;
+    size_t key, cost, seed_pix, cnt, off, cur, adj_t, adj_w, adj_i, models, retry, counters, total;
 };
 
 EpicLayout epic_layout(int W, int H, int n)
@@ -494,8 +637,10 @@ EpicLayout epic_layout(int W, int H, int n)
     L.cur = take((size_t)n * 4);
     L.adj_t = take(nl * 4);
     L.adj_w = take(nl * 8);
+    L.adj_i = take(nl * 16);
     L.models = take((size_t)n * 48);
-    L.counters = take((kMaxPasses + 1) * 4);  // pass counters, then the status word
+    L.retry = take((size_t)n * 4);
+    L.counters = take((kMaxPasses + 2) * 4);  // pass counters, the status word, the retry count
     L.total = at;
     return L;
 }
@@ -542,7 +687,7 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
     if ((d.knn_idx == nullptr) != (d.knn_dist == nullptr)) return DGF_ERR_ARG;
     if ((d.labels && !dgf::aligned(d.labels, 4)) || (d.dist && !dgf::aligned(d.dist, 8)) || (d.knn_idx && !dgf::aligned(d.knn_idx, 4)) ||
         (d.knn_dist && !dgf::aligned(d.knn_dist, 8)) || (d.knn_count && !dgf::aligned(d.knn_count, 4)) ||
-        (d.models && !dgf::aligned(d.models, 8)))
+        (d.models && !dgf::aligned(d.models, 8)) || (d.retried && !dgf::aligned(d.retried, 4)))
         return DGF_ERR_ARG;
     const EpicLayout L = epic_layout(W, H, n);
     if (ws_bytes < L.total) return DGF_ERR_WORKSPACE;
@@ -555,13 +700,16 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
     auto* cur = reinterpret_cast<int*>(ws + L.cur);
     auto* adj_t = reinterpret_cast<int*>(ws + L.adj_t);
     auto* adj_w = reinterpret_cast<long long*>(ws + L.adj_w);
+    auto* adj_i = reinterpret_cast<int4*>(ws + L.adj_i);
+    auto* retry_list = reinterpret_cast<int*>(ws + L.retry);
     auto* models = reinterpret_cast<double*>(ws + L.models);
     auto* changed = reinterpret_cast<int*>(ws + L.counters);
     int* err = changed + kMaxPasses;
+    int* retry_count = err + 1;
     const float2* p2 = reinterpret_cast<const float2*>(pts);
     const float2* f2 = reinterpret_cast<const float2*>(flow);
 
-    if (cudaMemsetAsync(changed, 0, (kMaxPasses + 1) * sizeof(int), stream) != cudaSuccess) return DGF_ERR_CUDA;
+    if (cudaMemsetAsync(changed, 0, (kMaxPasses + 2) * sizeof(int), stream) != cudaSuccess) return DGF_ERR_CUDA;
     if (n > 0 && cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), stream) != cudaSuccess) return DGF_ERR_CUDA;
     const dim3 pix_block(32, 8), pix_grid((W + 31) / 32, (H + 7) / 8);
     const unsigned pt_grid = (unsigned)((n + kThreads - 1) / kThreads);
@@ -594,15 +742,20 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
         epic_scan_kernel<<<1, 1024, 0, stream>>>(cnt, n, off, cur);
         epic_links_kernel<true><<<pix_grid, pix_block, 0, stream>>>(key, cost, W, H, nullptr, off, cur, adj_t, adj_w,
                                                                     err);
+        epic_dedupe_kernel<<<pt_grid, kThreads, 0, stream>>>(off, cur, adj_t, adj_w, n);
+        epic_link_meta_kernel<<<pt_grid, kThreads, 0, stream>>>(off, cur, adj_t, adj_i, n);
         KnnArgs a;
         a.pts = p2;
         a.flow = f2;
         a.seed_pix = seed_pix;
         a.off = off;
-        a.adj_t = adj_t;
+        a.end = cur;
+        a.adj_i = adj_i;
         a.adj_w = adj_w;
         a.models = models;
         a.err = err;
+        a.retry_count = retry_count;
+        a.retry_list = retry_list;
         a.knn_idx = d.knn_idx;
         a.knn_dist = d.knn_dist;
         a.knn_count = d.knn_count;
@@ -614,15 +767,21 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
         a.cost_base = p->cost_base;
         a.a = p->a;
         a.min_spread2 = p->min_spread * p->min_spread;
-        a.warp_bytes = knn_warp_bytes(p->k);
-        const size_t smem = a.warp_bytes * kKnnWarps;
-        if (cudaFuncSetAttribute(epic_knn_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
+        const size_t smem_fast = KnnLayout<kFastF, kFastH>::warp_bytes(p->k) * kFastWarps;
+        const size_t smem_big = KnnLayout<kBigF, kBigH>::warp_bytes(p->k);
+        if (cudaFuncSetAttribute(epic_knn_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fast) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(epic_knn_retry_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_big) !=
+                cudaSuccess)
             return DGF_ERR_CUDA;
-        epic_knn_fit_kernel<<<(unsigned)((n + kKnnWarps - 1) / kKnnWarps), kKnnWarps * 32, smem, stream>>>(a);
+        epic_knn_fit_kernel<<<(unsigned)((n + kFastWarps - 1) / kFastWarps), kFastWarps * 32, smem_fast, stream>>>(a);
+        epic_knn_retry_kernel<<<kRetryBlocks, 32, smem_big, stream>>>(a);
     }
     epic_dense_kernel<<<pix_grid, pix_block, 0, stream>>>(key, models, p2, W, H, reinterpret_cast<float2*>(dense),
                                                           d.labels, d.dist);
+    if (d.retried &&
+        cudaMemcpyAsync(d.retried, retry_count, sizeof(int), cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+        return DGF_ERR_CUDA;
     if ((rc = dgf::launch_status()) != DGF_OK) return rc;
     int status_word = 0;
     if (cudaMemcpyAsync(&status_word, err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||

@@ -212,7 +212,7 @@ def test_epic_host_checks_return_before_launch():
     v = dgf.EpicParams().c()
     v.version = 99
     assert call(prm=v) == -1
-    half = _abi.EpicDebugC(None, None, fake.value, None, None, None, None)  # knn_idx without knn_dist
+    half = _abi.EpicDebugC(None, None, fake.value, None, None, None, None, None)  # knn_idx without knn_dist
     assert call(dbg=half) == -1
 
 
