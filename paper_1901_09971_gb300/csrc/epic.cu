@@ -241,30 +241,50 @@ __global__ void __launch_bounds__(1024) epic_scan_kernel(const int* cnt, int n, 
 }
 
 // Per seed: keeps one link per neighbour (the smallest weight), compacting the list
-// in place; end[s] becomes the end of the compacted list.
+// in place; end[s] becomes the end of the compacted list. One warp per seed walks
+// the list in chunks of 32: lanes holding the same neighbour find each other with
+// match.any and take their minimum weight; the lowest of them either lowers the
+// weight of a link kept from an earlier chunk or appends a new one. The kept prefix
+// never reaches the unread part of the list.
 __global__ void __launch_bounds__(kThreads) epic_dedupe_kernel(const int* off, int* end, int* adj_t, long long* adj_w,
                                                                int n)
 {
-    const int s = blockIdx.x * kThreads + threadIdx.x;
-    if (s >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int s = (int)(((size_t)blockIdx.x * kThreads + threadIdx.x) >> 5);
+    if (s >= n) return;  // warp-uniform
     const int b = off[s], e = off[s + 1];
     int out = b;
-    for (int i = b; i < e; ++i) {
-        const int t = adj_t[i];
-        const long long w = adj_w[i];
-        int j = b;
-        for (; j < out; ++j)
-            if (adj_t[j] == t) {
-                if (w < adj_w[j]) adj_w[j] = w;
-                break;
-            }
-        if (j == out) {
-            adj_t[out] = t;
-            adj_w[out] = w;
-            ++out;
+    for (int c = b; c < e; c += 32) {
+        const bool has = c + lane < e;
+        const int t = has ? adj_t[c + lane] : -1 - lane;  // empty lanes match nobody
+        const long long w = has ? adj_w[c + lane] : 0;
+        const unsigned grp = __match_any_sync(0xffffffffu, t);
+        long long mw = w;
+        for (int j = 0; j < 32; ++j) {
+            const long long wj = __shfl_sync(0xffffffffu, w, j);
+            if ((grp >> j) & 1u) mw = min(mw, wj);
         }
+        const bool leader = has && lane == __ffs(grp) - 1;
+        int found = -1;
+        if (leader)
+            for (int j = b; j < out; ++j)
+                if (adj_t[j] == t) {
+                    found = j;
+                    break;
+                }
+        if (found >= 0 && mw < adj_w[found]) adj_w[found] = mw;  // leaders hold distinct neighbours
+        const bool app = leader && found < 0;
+        const unsigned km = __ballot_sync(0xffffffffu, app);
+        __syncwarp();
+        if (app) {
+            const int pos = out + __popc(km & ((1u << lane) - 1));
+            adj_t[pos] = t;
+            adj_w[pos] = mw;
+        }
+        out += __popc(km);
+        __syncwarp();
     }
-    end[s] = out;
+    if (lane == 0) end[s] = out;
 }
 
 // Link records for the search: (neighbour, its list begin, its list end).
@@ -742,7 +762,8 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
         epic_scan_kernel<<<1, 1024, 0, stream>>>(cnt, n, off, cur);
         epic_links_kernel<true><<<pix_grid, pix_block, 0, stream>>>(key, cost, W, H, nullptr, off, cur, adj_t, adj_w,
                                                                     err);
-        epic_dedupe_kernel<<<pt_grid, kThreads, 0, stream>>>(off, cur, adj_t, adj_w, n);
+        epic_dedupe_kernel<<<(unsigned)((n + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, stream>>>(
+            off, cur, adj_t, adj_w, n);
         epic_link_meta_kernel<<<pt_grid, kThreads, 0, stream>>>(off, cur, adj_t, adj_i, n);
         KnnArgs a;
         a.pts = p2;
