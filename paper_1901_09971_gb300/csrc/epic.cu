@@ -21,12 +21,14 @@
 //   7-8. each list keeps one link per neighbour (its smallest weight), and every
 //      link records where its neighbour's list lies, so a search reads a popped
 //      seed's links without first loading its list bounds;
-//   9. per seed, one warp runs Dijkstra over the seed graph on (distance, index)
-//      keys until k seeds are settled, with the frontier (128 entries), a hash of
-//      discovered seeds and the settled list in shared memory (32 warps per SM);
-//      then the warp fits the weighted affine model in FP64. A search whose
-//      frontier outgrows 128 entries is queued and redone by a retry kernel with
-//      room for 4096;
+//   9. per seed, one warp runs Dijkstra over the seed graph with batch settling
+//      (every frontier seed within its smallest incoming link of the frontier
+//      minimum is final, so about 14 steps settle the 128 nearest instead of 128
+//      pops), a hash of discovered seeds in shared memory, then sorts the settled
+//      (distance, index) keys and fits the weighted affine model to the first k in
+//      FP64. A search that outgrows the hash (512 seeds; 1024 for k > 160) or the
+//      sort buffer (256; 512) is queued and redone by a retry kernel with room for
+//      8192;
 //   10. dense flow: every pixel evaluates its seed's model.
 #include <math.h>
 
@@ -42,6 +44,8 @@ constexpr int kTile = 32;                    // Voronoi tiles: 32 x 32 pixels, 3
 constexpr int kMaxPasses = 4096;
 constexpr int kPassBatch = 4;
 constexpr int kThreads = 256;
+
+constexpr long long kNoLink = 0xffffffffll;  // min link weight of a seed without links
 
 // Device status bits (any of them makes the call return DGF_ERR_DEVICE).
 enum : int { kErrFrontier = 1, kErrHash = 2, kErrFill = 4, kErrRange = 8 };
@@ -247,7 +251,7 @@ __global__ void __launch_bounds__(1024) epic_scan_kernel(const int* cnt, int n, 
 // weight of a link kept from an earlier chunk or appends a new one. The kept prefix
 // never reaches the unread part of the list.
 __global__ void __launch_bounds__(kThreads) epic_dedupe_kernel(const int* off, int* end, int* adj_t, long long* adj_w,
-                                                               int n)
+                                                               unsigned* minin, int n)
 {
     const int lane = threadIdx.x & 31;
     const int s = (int)(((size_t)blockIdx.x * kThreads + threadIdx.x) >> 5);
@@ -284,18 +288,28 @@ __global__ void __launch_bounds__(kThreads) epic_dedupe_kernel(const int* off, i
         out += __popc(km);
         __syncwarp();
     }
-    if (lane == 0) end[s] = out;
+    // smallest link weight (a lower bound on the last step of any path into s),
+    // clamped to 32 bits (a smaller bound stays a bound)
+    long long mn = kNoLink;
+    for (int j = b + lane; j < out; j += 32) mn = min(mn, adj_w[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if (lane == 0) {
+        end[s] = out;
+        minin[s] = (unsigned)min(mn, (long long)kNoLink);
+    }
 }
 
-// Link records for the search: (neighbour, its list begin, its list end).
+// Link records for the search: (neighbour, its list begin, its list end, its
+// smallest link weight).
 __global__ void __launch_bounds__(kThreads) epic_link_meta_kernel(const int* off, const int* end, const int* adj_t,
-                                                                  int4* adj_i, int n)
+                                                                  const unsigned* minin, int4* adj_i, int n)
 {
     const int s = blockIdx.x * kThreads + threadIdx.x;
     if (s >= n) return;
     for (int i = off[s], e = end[s]; i < e; ++i) {
         const int t = adj_t[i];
-        adj_i[i] = make_int4(t, off[t], end[t], 0);
+        adj_i[i] = make_int4(t, off[t], end[t], (int)minin[t]);
     }
 }
 
@@ -305,6 +319,7 @@ struct KnnArgs {
     const int* seed_pix;
     const int* off;
     const int* end;
+    const unsigned* minin;
     const int4* adj_i;
     const long long* adj_w;
     double* models;  // [n][6]
@@ -316,137 +331,226 @@ struct KnnArgs {
     int32_t* knn_count;
     double* dbg_models;
     uint8_t* fit_kind;
-    int n, k, model, cost_base;
-    double a, min_spread2;
+    int n, k, model;
+    double a_per_unit, min_spread2;  // kernel decay per unit of distance: a / (2 cost_base)
 };
 
-constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
-
-// Per-warp shared layout of one search with a frontier of FCAP entries and a hash
-// of HCAP slots: frontier keys (distance << 24 | index), their link-list bounds and
-// hash slots; hash keys and values (frontier slot of a discovered seed, -2 once
-// settled); then the settled list (index, distance).
-template <int FCAP, int HCAP>
+// Per-warp shared layout of one search: a hash of HCAP discovered seeds (index,
+// tentative distance, smallest incoming link weight, settled flag), the frontier
+// as a list of FCAP hash slots, and the settled keys (SCAP, later sorted in place).
+template <int HCAP, int FCAP, int SCAP>
 struct KnnLayout {
-    static_assert((HCAP & (HCAP - 1)) == 0 && HCAP <= 32768 && FCAP <= 32767, "hash and frontier sizes");
-    static constexpr int hash_bits = ilog2(HCAP);
-    static constexpr size_t o_fmeta = (size_t)FCAP * 8;
-    static constexpr size_t o_fhs = o_fmeta + (size_t)FCAP * 8;
-    static constexpr size_t o_hkey = (o_fhs + (size_t)FCAP * 2 + 15) & ~(size_t)15;
-    static constexpr size_t o_hval = o_hkey + (size_t)HCAP * 4;
-    static constexpr size_t fixed = (o_hval + (size_t)HCAP * 2 + 15) & ~(size_t)15;
-    __host__ __device__ static constexpr size_t o_sdist(int k) { return (fixed + (size_t)k * 4 + 7) & ~(size_t)7; }
-    __host__ __device__ static constexpr size_t warp_bytes(int k) { return o_sdist(k) + (size_t)k * 8; }
+    static_assert((HCAP & (HCAP - 1)) == 0 && (SCAP & (SCAP - 1)) == 0 && HCAP <= 32768, "sizes");
+    static constexpr int hash_bits = __builtin_ctz(HCAP);
+    static constexpr size_t o_hdist = (size_t)HCAP * 4;
+    static constexpr size_t o_sort = o_hdist + (size_t)HCAP * 8;
+    static constexpr size_t o_minin = o_sort + (size_t)SCAP * 8;
+    static constexpr size_t o_front = o_minin + (size_t)HCAP * 4;
+    static constexpr size_t o_state = o_front + (size_t)FCAP * 2;
+    static constexpr size_t o_count = (o_state + (size_t)HCAP + 15) & ~(size_t)15;
+    static constexpr size_t bytes = o_count + 16;
 };
 
-// The fast search holds every frontier seen on the benchmark scenes (at most 73
-// entries at k = 128); a search that outgrows it is redone by the retry kernel with
-// room for 4096.
-constexpr int kFastF = 128, kFastH = 512, kFastWarps = 8;
-constexpr int kBigF = 4096, kBigH = 8192, kRetryBlocks = 152;
+// The fast layouts hold every search of the benchmark scenes (at k = 128 at most
+// about 250 discovered and 171 settled seeds; larger k takes the larger one); a
+// search that outgrows them is redone by the retry kernel with room for 8192.
+constexpr int kFastWarps = 4, kSmallK = 160;
+constexpr int kBigH = 8192, kBigF = 8192, kBigS = 8192, kRetryBlocks = 152;
 constexpr int kRetry = 16;  // search status: capacity exceeded, redo with the large layout
+constexpr long long kInf = 0x7fffffffffffffffll;
+enum : unsigned char { kFrontier = 0, kSettled = 1 };
 
-__device__ __forceinline__ double warp_sum(double v)
+// exp(-y) for y >= 0 by the table-driven method of Tang (ACM TOMS 15(2), 1989):
+// y = (32 q + j) ln2 / 32 + r with |r| <= ln2 / 64, so exp(-y) = 2^-q 2^(-j/32)
+// exp(-r), exp(-r) by its degree-6 Taylor polynomial (truncation below 4e-18); the
+// reduction uses a two-part ln2 / 32 and fused multiply-adds; the power of two is
+// built from exponent bits. Relative error about 1e-15; 0 from y = 745.2 on, where
+// exp(-y) underflows to 0 in FP64.
+__device__ const double kExp2Frac[32] = {  // 2^(-j/32), correctly rounded
+    0x1.0000000000000p+0, 0x1.f50765b6e4540p-1, 0x1.ea4afa2a490dap-1, 0x1.dfc97337b9b5fp-1,
+    0x1.d5818dcfba487p-1, 0x1.cb720dcef9069p-1, 0x1.c199bdd85529cp-1, 0x1.b7f76f2fb5e47p-1,
+    0x1.ae89f995ad3adp-1, 0x1.a5503b23e255dp-1, 0x1.9c49182a3f090p-1, 0x1.93737b0cdc5e5p-1,
+    0x1.8ace5422aa0dbp-1, 0x1.82589994cce13p-1, 0x1.7a11473eb0187p-1, 0x1.71f75e8ec5f74p-1,
+    0x1.6a09e667f3bcdp-1, 0x1.6247eb03a5585p-1, 0x1.5ab07dd485429p-1, 0x1.5342b569d4f82p-1,
+    0x1.4bfdad5362a27p-1, 0x1.44e086061892dp-1, 0x1.3dea64c123422p-1, 0x1.371a7373aa9cbp-1,
+    0x1.306fe0a31b715p-1, 0x1.29e9df51fdee1p-1, 0x1.2387a6e756238p-1, 0x1.1d4873168b9aap-1,
+    0x1.172b83c7d517bp-1, 0x1.11301d0125b51p-1, 0x1.0b5586cf9890fp-1, 0x1.059b0d3158574p-1,
+};
+
+__device__ __forceinline__ double exp_neg(double y)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    if (!(y < 745.2)) return 0.0;
+    const double kf = rint(y * 0x1.71547652b82fep+5);  // y * 32 / ln2
+    double r = fma(-kf, 0x1.62e42fefa39efp-6, y);      // ln2 / 32, leading part
+    r = fma(-kf, 0x1.abc9e3b39803fp-61, r);            // and the rest
+    const double x = -r;
+    double e = 1.0 / 720.0;
+    e = fma(e, x, 1.0 / 120.0);
+    e = fma(e, x, 1.0 / 24.0);
+    e = fma(e, x, 1.0 / 6.0);
+    e = fma(e, x, 0.5);
+    e = fma(e, x, 1.0);
+    e = fma(e, x, 1.0);
+    const int k = (int)kf, q = k >> 5;  // q <= 1075: 2^-q as two normal powers of two
+    const double s1 = __longlong_as_double((long long)(1023 - (q >> 1)) << 52);
+    const double s2 = __longlong_as_double((long long)(1023 - (q - (q >> 1))) << 52);
+    return e * __ldg(&kExp2Frac[k & 31]) * s1 * s2;
 }
 
-// Dijkstra over the seed graph from seed s on (distance, index) keys until k seeds
-// are settled; the warp's 32 lanes scan the frontier and relax one link each.
-// Returns 0 with the settled list in shared memory, kRetry when the frontier or the
-// hash is full, or kErrRange when a distance leaves the key's 40 bits.
-template <int FCAP, int HCAP>
+// Sums of 12 values over the warp; the totals land in lane 0. Halving exchanges:
+// lanes 16 apart swap half of their values and keep the sum of the other half, then
+// lanes 8 apart the same with 3 of 6, then xor butterflies finish the 3 sums in each
+// group of 8 lanes; lanes 8, 16 and 24 hand their 3 totals to lane 0.
+__device__ __forceinline__ void warp_sum12(const double (&v)[12], double (&out)[12])
+{
+    const int lane = threadIdx.x & 31;
+    const bool hi16 = lane & 16, hi8 = lane & 8;
+    double h[6], q[3];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double keep = hi16 ? v[6 + i] : v[i], give = hi16 ? v[i] : v[6 + i];
+        h[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double keep = hi8 ? h[3 + i] : h[i], give = hi8 ? h[i] : h[3 + i];
+        q[i] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) q[i] += __shfl_xor_sync(0xffffffffu, q[i], o);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        out[i] = q[i];
+        out[3 + i] = __shfl_sync(0xffffffffu, q[i], 8);
+        out[6 + i] = __shfl_sync(0xffffffffu, q[i], 16);
+        out[9 + i] = __shfl_sync(0xffffffffu, q[i], 24);
+    }
+}
+
+__device__ __forceinline__ long long warp_min64(long long v)  // v >= 0
+{
+    const unsigned hi = __reduce_min_sync(0xffffffffu, (unsigned)((unsigned long long)v >> 32));
+    const unsigned lo = __reduce_min_sync(0xffffffffu, (unsigned)((unsigned long long)v >> 32) == hi ? (unsigned)v : ~0u);
+    return (long long)(((unsigned long long)hi << 32) | lo);
+}
+
+// Ascending bitonic sort of N keys (a power of two) in shared memory by one warp.
+__device__ void warp_bitonic_sort(unsigned long long* key, int N)
+{
+    const int lane = threadIdx.x & 31;
+    for (int size = 2; size <= N; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < N / 2; i += 32) {
+                const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const unsigned long long x = key[lo], y = key[hi];
+                if ((x > y) == asc) {
+                    key[lo] = y;
+                    key[hi] = x;
+                }
+            }
+            __syncwarp();
+        }
+}
+
+// The k nearest seeds of seed s in the seed graph, exactly, by Dijkstra with batch
+// settling: with m the smallest tentative distance on the frontier, every frontier
+// seed v with d(v) <= m + minin(v) is final (a shorter path would have to end with
+// a link from an unsettled seed, at least m away, and that link weighs at least
+// minin(v)); the whole batch is settled (appended to the settled keys and removed
+// from the frontier list), then its links are relaxed, one lane per batch seed;
+// newly discovered seeds join the frontier list. The search stops once k settled
+// seeds lie below m (every unsettled seed is at least m away) or the frontier is
+// empty; the settled keys (distance << 24 | index) are then sorted and the first
+// k kept (cnt_out). Returns 0, kRetry when the hash, the frontier list or the
+// settled list is full, or kErrRange when a distance leaves 40 bits.
+template <int HCAP, int FCAP, int SCAP>
 __device__ int knn_search(const KnnArgs& a, int s, unsigned char* base, int& cnt_out)
 {
-    using Lay = KnnLayout<FCAP, HCAP>;
-    unsigned long long* fkey = reinterpret_cast<unsigned long long*>(base);
-    int2* fmeta = reinterpret_cast<int2*>(base + Lay::o_fmeta);
-    short* fhs = reinterpret_cast<short*>(base + Lay::o_fhs);
-    int* hkey = reinterpret_cast<int*>(base + Lay::o_hkey);
+    using Lay = KnnLayout<HCAP, FCAP, SCAP>;
+    int* hkey = reinterpret_cast<int*>(base);
     volatile int* vh = hkey;
-    short* hval = reinterpret_cast<short*>(base + Lay::o_hval);
-    int* sidx = reinterpret_cast<int*>(base + Lay::fixed);
-    long long* sdist = reinterpret_cast<long long*>(base + Lay::o_sdist(a.k));
+    long long* hdist = reinterpret_cast<long long*>(base + Lay::o_hdist);
+    unsigned long long* skey = reinterpret_cast<unsigned long long*>(base + Lay::o_sort);
+    unsigned* hmin = reinterpret_cast<unsigned*>(base + Lay::o_minin);
+    short* front = reinterpret_cast<short*>(base + Lay::o_front);
+    unsigned char* hst = base + Lay::o_state;
+    int* fcount = reinterpret_cast<int*>(base + Lay::o_count);  // frontier list length
     const int lane = threadIdx.x & 31;
     auto slot_of = [](int t) { return (int)(((unsigned)t * 0x9E3779B1u) >> (32 - Lay::hash_bits)); };
 
-    for (int j = lane; j < HCAP; j += 32) hkey[j] = -1;
+    for (int j = lane; j < HCAP; j += 32) {
+        hkey[j] = -1;
+        hdist[j] = kInf;
+        hst[j] = kFrontier;
+    }
     __syncwarp();
     if (lane == 0) {
         const int h = slot_of(s);
         hkey[h] = s;
-        hval[h] = 0;
-        fkey[0] = (unsigned long long)s;  // distance 0
-        fhs[0] = (short)h;
-        fmeta[0] = make_int2(a.off[s], a.end[s]);
+        hdist[h] = 0;
+        hmin[h] = a.minin[s];
+        front[0] = (short)h;
+        *fcount = 1;
     }
     __syncwarp();
-    int fsize = 1, cnt = 0, status = 0;
-    while (cnt < a.k && fsize > 0) {
-        // pop the smallest key: lane minima with their slots, then two 32-bit warp minima
-        unsigned long long best = kNone;
-        int bslot = -1;
-        for (int j = lane; j < fsize; j += 32) {
-            const unsigned long long v = fkey[j];
-            if (v < best) {
-                best = v;
-                bslot = j;
+    int status = 0, nset = 0;
+    for (int step = 0; step < HCAP; ++step) {  // every step settles at least the frontier minimum
+        const int nf = *fcount;
+        if (nf == 0) break;  // every reachable seed is settled
+        long long m = kInf;
+        for (int i = lane; i < nf; i += 32) m = min(m, hdist[front[i]]);
+        m = warp_min64(m);
+        int below = 0;
+        for (int i = lane; i < nset; i += 32) below += (long long)(skey[i] >> kIdxBits) < m;
+        if ((int)__reduce_add_sync(0xffffffffu, (unsigned)below) >= a.k) break;
+        // settle the batch: compact the frontier list in place (chunks are read
+        // before the kept entries of the chunk are written, and never ahead of them)
+        const int nset0 = nset;
+        int kept = 0;
+        for (int c = 0; c < nf; c += 32) {
+            const int i = c + lane;
+            int h = -1;
+            bool bat = false;
+            if (i < nf) {
+                h = front[i];
+                bat = hdist[h] <= m + (long long)hmin[h];
             }
+            const unsigned bm = __ballot_sync(0xffffffffu, bat), km = __ballot_sync(0xffffffffu, i < nf && !bat);
+            const unsigned lt = (1u << lane) - 1;
+            __syncwarp();
+            if (bat) {
+                const int pos = nset + __popc(bm & lt);
+                if (pos < SCAP) {
+                    skey[pos] = ((unsigned long long)hdist[h] << kIdxBits) | (unsigned long long)hkey[h];
+                    hst[h] = kSettled;
+                }
+            } else if (i < nf) {
+                front[kept + __popc(km & lt)] = (short)h;
+            }
+            nset += __popc(bm);
+            kept += __popc(km);
+            __syncwarp();
         }
-        const unsigned mhi = __reduce_min_sync(0xffffffffu, (unsigned)(best >> 32));
-        const unsigned mlo = __reduce_min_sync(0xffffffffu, (unsigned)(best >> 32) == mhi ? (unsigned)best : ~0u);
-        const unsigned long long gmin = ((unsigned long long)mhi << 32) | mlo;
-        const unsigned own = __ballot_sync(0xffffffffu, bslot >= 0 && best == gmin);
-        if (own == 0) {  // every frontier entry holds a key, so this cannot happen
-            status = kErrFrontier;
+        if (nset > SCAP) {
+            status = kRetry;
             break;
         }
-        const int slot = __shfl_sync(0xffffffffu, bslot, __ffs(own) - 1);
-        const int u = (int)(gmin & kIdxMask);
-        const long long d = (long long)(gmin >> kIdxBits);
-        const int2 m = fmeta[slot];
-        const bool last = cnt + 1 == a.k;  // the k-th seed's links are not needed
-        const int nlk = last ? 0 : m.y - m.x;
-        int4 li = make_int4(-1, 0, 0, 0);
-        long long lw = 0;
-        if (lane < nlk) {  // issue the first links' loads before the bookkeeping
-            li = a.adj_i[m.x + lane];
-            lw = a.adj_w[m.x + lane];
-        }
+        if (lane == 0) *fcount = kept;
         __syncwarp();
-        if (lane == 0) {
-            hval[fhs[slot]] = -2;
-            const int L = fsize - 1;
-            if (slot != L) {
-                fkey[slot] = fkey[L];
-                fhs[slot] = fhs[L];
-                fmeta[slot] = fmeta[L];
-                hval[fhs[slot]] = (short)slot;
-            }
-            sidx[cnt] = u;
-            sdist[cnt] = d;
-        }
-        --fsize;
-        ++cnt;
-        __syncwarp();
-        for (int c0 = 0; c0 < nlk; c0 += 32) {
-            if (c0 > 0) {
-                li = make_int4(-1, 0, 0, 0);
-                if (c0 + lane < nlk) {
-                    li = a.adj_i[m.x + c0 + lane];
-                    lw = a.adj_w[m.x + c0 + lane];
-                }
-            }
-            const bool has = c0 + lane < nlk;
-            const int t = li.x;
-            const long long nd = d + lw;
-            int hs = -1, st = 0;
-            bool isnew = false;
-            if (has) {
+        // relax the batch's links, one lane per batch seed
+        int st = 0;
+        for (int i = nset0 + lane; i < nset; i += 32) {
+            const int u = (int)(skey[i] & kIdxMask);
+            const long long du = (long long)(skey[i] >> kIdxBits);
+            for (int e = a.off[u], e1 = a.end[u]; e < e1; ++e) {
+                const int4 li = a.adj_i[e];
+                const long long nd = du + a.adj_w[e];
                 if (nd >= kDistLimit) st |= kErrRange;
-                int h = slot_of(t);
+                const int t = li.x;
+                int h = slot_of(t), hs = -1;
                 for (int q = 0; q < HCAP; ++q) {
                     const int c = vh[h];
                     if (c == t) {
@@ -455,75 +559,81 @@ __device__ int knn_search(const KnnArgs& a, int s, unsigned char* base, int& cnt
                     }
                     if (c == -1) {
                         const int prev = atomicCAS(&hkey[h], -1, t);
-                        if (prev == -1 || prev == t) {
+                        if (prev == -1) {  // discovered: joins the frontier list
+                            hmin[h] = (unsigned)li.w;
+                            const int f = atomicAdd(fcount, 1);
+                            if (f < FCAP)
+                                front[f] = (short)h;
+                            else
+                                st |= kRetry;
                             hs = h;
-                            isnew = prev == -1;
+                            break;
+                        }
+                        if (prev == t) {
+                            hs = h;
                             break;
                         }
                     }
                     h = (h + 1) & (HCAP - 1);
                 }
-                if (hs < 0) st |= kRetry;
-            }
-            __syncwarp();
-            const unsigned nm = __ballot_sync(0xffffffffu, isnew);
-            if (isnew) {
-                const int fs = fsize + __popc(nm & ((1u << lane) - 1));
-                if (fs < FCAP) {
-                    fkey[fs] = kNone;
-                    fhs[fs] = (short)hs;
-                    fmeta[fs] = make_int2(li.y, li.z);
-                    hval[hs] = (short)fs;
-                } else {
+                if (hs < 0) {
                     st |= kRetry;
+                    break;
                 }
+                // a settled seed keeps its final distance: the minimum is a no-op there
+                if (hst[hs] == kFrontier)
+                    atomicMin(reinterpret_cast<unsigned long long*>(&hdist[hs]), (unsigned long long)nd);
             }
-            fsize = min(fsize + __popc(nm), FCAP);
-            __syncwarp();
-            if (has && hs >= 0 && !st) {
-                const int v = hval[hs];
-                if (v >= 0) atomicMin(&fkey[v], ((unsigned long long)nd << kIdxBits) | (unsigned long long)t);
-            }
-            __syncwarp();
-            status = __reduce_or_sync(0xffffffffu, st);
-            if (status) break;
         }
+        __syncwarp();
+        status = __reduce_or_sync(0xffffffffu, st);
         if (status) break;
     }
-    cnt_out = cnt;
+    if (!status) {
+        int N = 32;
+        while (N < nset) N <<= 1;
+        if (N > SCAP) {
+            status = kRetry;
+        } else {
+            for (int j = nset + lane; j < N; j += 32) skey[j] = kNone;
+            __syncwarp();
+            warp_bitonic_sort(skey, N);
+            cnt_out = min(nset, a.k);
+        }
+    }
     return status & kErrRange ? kErrRange : status;
 }
 
-// The weighted affine fit of seed s over its settled list (FP64; the 3 x 3 normal
-// equations lose too many digits in FP32 when a neighbourhood is narrow) and the
-// outputs. M = sum w v v^T, v = (x_t - x_s, y_t - y_s, 1).
-__device__ void knn_fit_write(const KnnArgs& a, int s, int cnt, const int* sidx, const long long* sdist)
+// The weighted affine fit of seed s over its neighbourhood (sorted keys; FP64, as
+// the 3 x 3 normal equations lose too many digits in FP32 when a neighbourhood is
+// narrow) and the outputs. M = sum w v v^T, v = (x_t - x_s, y_t - y_s, 1).
+__device__ void knn_fit_write(const KnnArgs& a, int s, int cnt, const unsigned long long* key)
 {
     const int lane = threadIdx.x & 31, k = a.k;
     if (a.knn_count && lane == 0) a.knn_count[s] = cnt;
     if (a.knn_idx)
         for (int j = lane; j < cnt; j += 32) {
-            a.knn_idx[(size_t)s * k + j] = sidx[j];
-            a.knn_dist[(size_t)s * k + j] = sdist[j];
+            a.knn_idx[(size_t)s * k + j] = (int)(key[j] & kIdxMask);
+            a.knn_dist[(size_t)s * k + j] = (int64_t)(key[j] >> kIdxBits);
         }
     const float2 ps = a.pts[s];
-    double m00 = 0, m01 = 0, m02 = 0, m11 = 0, m12 = 0, m22 = 0, u0 = 0, u1 = 0, u2 = 0, v0 = 0, v1 = 0, v2 = 0;
+    double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int j = lane; j < cnt; j += 32) {
-        const int t = sidx[j];
-        const double w = exp(-a.a * (double)sdist[j] / (2.0 * a.cost_base));
+        const int t = (int)(key[j] & kIdxMask);
+        const double w = exp_neg(a.a_per_unit * (double)(long long)(key[j] >> kIdxBits));
         const float2 pt = a.pts[t], ft = a.flow[t];
         const double vx = (double)pt.x - (double)ps.x, vy = (double)pt.y - (double)ps.y;
-        const double fu = ft.x, fv = ft.y;
-        m00 += w * vx * vx; m01 += w * vx * vy; m02 += w * vx;
-        m11 += w * vy * vy; m12 += w * vy; m22 += w;
-        u0 += w * vx * fu; u1 += w * vy * fu; u2 += w * fu;
-        v0 += w * vx * fv; v1 += w * vy * fv; v2 += w * fv;
+        const double fu = ft.x, fv = ft.y, wx = w * vx, wy = w * vy;
+        acc[0] = fma(wx, vx, acc[0]); acc[1] = fma(wx, vy, acc[1]); acc[2] += wx;
+        acc[3] = fma(wy, vy, acc[3]); acc[4] += wy; acc[5] += w;
+        acc[6] = fma(wx, fu, acc[6]); acc[7] = fma(wy, fu, acc[7]); acc[8] = fma(w, fu, acc[8]);
+        acc[9] = fma(wx, fv, acc[9]); acc[10] = fma(wy, fv, acc[10]); acc[11] = fma(w, fv, acc[11]);
     }
-    m00 = warp_sum(m00); m01 = warp_sum(m01); m02 = warp_sum(m02);
-    m11 = warp_sum(m11); m12 = warp_sum(m12); m22 = warp_sum(m22);
-    u0 = warp_sum(u0); u1 = warp_sum(u1); u2 = warp_sum(u2);
-    v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
+    double tot[12];
+    warp_sum12(acc, tot);
     if (lane != 0) return;
+    const double m00 = tot[0], m01 = tot[1], m02 = tot[2], m11 = tot[3], m12 = tot[4], m22 = tot[5];
+    const double u0 = tot[6], u1 = tot[7], u2 = tot[8], v0 = tot[9], v1 = tot[10], v2 = tot[11];
     // affine only with 3+ neighbours whose weighted position covariance (the Schur
     // complement of the constant term over sum w) has lambda_min >= min_spread^2
     bool affine = a.model == 1 && cnt >= 3;
@@ -557,11 +667,12 @@ __device__ void knn_fit_write(const KnnArgs& a, int s, int cnt, const int* sidx,
     if (a.fit_kind) a.fit_kind[s] = affine ? 1 : 2;
 }
 
-// One warp per seed with the fast layout; searches that outgrow it are queued for
+// One warp per seed with a fast layout; searches that outgrow it are queued for
 // the retry kernel.
+template <int HCAP, int FCAP, int SCAP>
 __global__ void __launch_bounds__(kFastWarps * 32) epic_knn_fit_kernel(KnnArgs a)
 {
-    using Lay = KnnLayout<kFastF, kFastH>;
+    using Lay = KnnLayout<HCAP, FCAP, SCAP>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int s = blockIdx.x * kFastWarps + wid;
@@ -577,9 +688,9 @@ __global__ void __launch_bounds__(kFastWarps * 32) epic_knn_fit_kernel(KnnArgs a
         }
         return;
     }
-    unsigned char* base = smem + (size_t)wid * Lay::warp_bytes(a.k);
+    unsigned char* base = smem + (size_t)wid * Lay::bytes;
     int cnt = 0;
-    const int st = knn_search<kFastF, kFastH>(a, s, base, cnt);
+    const int st = knn_search<HCAP, FCAP, SCAP>(a, s, base, cnt);
     if (st == kRetry) {
         if (lane == 0) a.retry_list[atomicAdd(a.retry_count, 1)] = s;
         return;
@@ -588,26 +699,24 @@ __global__ void __launch_bounds__(kFastWarps * 32) epic_knn_fit_kernel(KnnArgs a
         if (lane == 0) atomicOr(a.err, st);
         return;
     }
-    knn_fit_write(a, s, cnt, reinterpret_cast<const int*>(base + Lay::fixed),
-                  reinterpret_cast<const long long*>(base + Lay::o_sdist(a.k)));
+    knn_fit_write(a, s, cnt, reinterpret_cast<const unsigned long long*>(base + Lay::o_sort));
 }
 
-// The queued searches with room for 4096 frontier entries, one warp per block.
+// The queued searches with room for 8192 discovered seeds, one warp per block.
 __global__ void __launch_bounds__(32) epic_knn_retry_kernel(KnnArgs a)
 {
-    using Lay = KnnLayout<kBigF, kBigH>;
+    using Lay = KnnLayout<kBigH, kBigF, kBigS>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int total = *a.retry_count;
     for (int i = blockIdx.x; i < total; i += gridDim.x) {
         const int s = a.retry_list[i];
         int cnt = 0;
-        const int st = knn_search<kBigF, kBigH>(a, s, smem, cnt);
+        const int st = knn_search<kBigH, kBigF, kBigS>(a, s, smem, cnt);
         if (st) {
             if ((threadIdx.x & 31) == 0) atomicOr(a.err, st == kRetry ? kErrFrontier : st);
             continue;
         }
-        knn_fit_write(a, s, cnt, reinterpret_cast<const int*>(smem + Lay::fixed),
-                      reinterpret_cast<const long long*>(smem + Lay::o_sdist(a.k)));
+        knn_fit_write(a, s, cnt, reinterpret_cast<const unsigned long long*>(smem + Lay::o_sort));
     }
 }
 
@@ -636,7 +745,7 @@ __global__ void __launch_bounds__(kThreads) epic_dense_kernel(const unsigned lon
 
 // Workspace layout (256-byte aligned sections).
 struct EpicLayout {
-    size_t key, cost, seed_pix, cnt, off, cur, adj_t, adj_w, adj_i, models, retry, counters, total;
+    size_t key, cost, seed_pix, cnt, off, cur, minin, adj_t, adj_w, adj_i, models, retry, counters, total;
 };
 
 EpicLayout epic_layout(int W, int H, int n)
@@ -655,6 +764,7 @@ EpicLayout epic_layout(int W, int H, int n)
     L.cnt = take((size_t)n * 4);
     L.off = take(((size_t)n + 1) * 4);
     L.cur = take((size_t)n * 4);
+    L.minin = take((size_t)n * 4);
     L.adj_t = take(nl * 4);
     L.adj_w = take(nl * 8);
     L.adj_i = take(nl * 16);
@@ -721,6 +831,7 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
     auto* adj_t = reinterpret_cast<int*>(ws + L.adj_t);
     auto* adj_w = reinterpret_cast<long long*>(ws + L.adj_w);
     auto* adj_i = reinterpret_cast<int4*>(ws + L.adj_i);
+    auto* minin = reinterpret_cast<unsigned*>(ws + L.minin);
     auto* retry_list = reinterpret_cast<int*>(ws + L.retry);
     auto* models = reinterpret_cast<double*>(ws + L.models);
     auto* changed = reinterpret_cast<int*>(ws + L.counters);
@@ -763,14 +874,15 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
         epic_links_kernel<true><<<pix_grid, pix_block, 0, stream>>>(key, cost, W, H, nullptr, off, cur, adj_t, adj_w,
                                                                     err);
         epic_dedupe_kernel<<<(unsigned)((n + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, stream>>>(
-            off, cur, adj_t, adj_w, n);
-        epic_link_meta_kernel<<<pt_grid, kThreads, 0, stream>>>(off, cur, adj_t, adj_i, n);
+            off, cur, adj_t, adj_w, minin, n);
+        epic_link_meta_kernel<<<pt_grid, kThreads, 0, stream>>>(off, cur, adj_t, minin, adj_i, n);
         KnnArgs a;
         a.pts = p2;
         a.flow = f2;
         a.seed_pix = seed_pix;
         a.off = off;
         a.end = cur;
+        a.minin = minin;
         a.adj_i = adj_i;
         a.adj_w = adj_w;
         a.models = models;
@@ -785,17 +897,18 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
         a.n = n;
         a.k = p->k;
         a.model = p->model;
-        a.cost_base = p->cost_base;
-        a.a = p->a;
+        a.a_per_unit = p->a / (2.0 * p->cost_base);
         a.min_spread2 = p->min_spread * p->min_spread;
-        const size_t smem_fast = KnnLayout<kFastF, kFastH>::warp_bytes(p->k) * kFastWarps;
-        const size_t smem_big = KnnLayout<kBigF, kBigH>::warp_bytes(p->k);
-        if (cudaFuncSetAttribute(epic_knn_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fast) !=
-                cudaSuccess ||
+        const bool small = p->k <= kSmallK;
+        auto fast = small ? epic_knn_fit_kernel<512, 256, 256> : epic_knn_fit_kernel<1024, 512, 512>;
+        const size_t smem_fast =
+            (small ? KnnLayout<512, 256, 256>::bytes : KnnLayout<1024, 512, 512>::bytes) * kFastWarps;
+        const size_t smem_big = KnnLayout<kBigH, kBigF, kBigS>::bytes;
+        if (cudaFuncSetAttribute(fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fast) != cudaSuccess ||
             cudaFuncSetAttribute(epic_knn_retry_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_big) !=
                 cudaSuccess)
             return DGF_ERR_CUDA;
-        epic_knn_fit_kernel<<<(unsigned)((n + kFastWarps - 1) / kFastWarps), kFastWarps * 32, smem_fast, stream>>>(a);
+        fast<<<(unsigned)((n + kFastWarps - 1) / kFastWarps), kFastWarps * 32, smem_fast, stream>>>(a);
         epic_knn_retry_kernel<<<kRetryBlocks, 32, smem_big, stream>>>(a);
     }
     epic_dense_kernel<<<pix_grid, pix_block, 0, stream>>>(key, models, p2, W, H, reinterpret_cast<float2*>(dense),

@@ -138,20 +138,29 @@ def test_edge_cases(dgf):
 
 
 def test_hub_seed_takes_the_retry_path(dgf):
-    """A seed in the middle of a flat frame inside a ring of 500 seeds: its cell
-    borders 200 ring cells, so its search discovers 200 seeds at once, more than the
-    fast frontier holds; the search is redone with the large one and must still
-    match the oracle exactly (on a flat frame, with many equal distances, which also
-    exercises the index tie-break)."""
-    W = H = 301
+    """A seed in the middle of a flat frame inside a ring of 1,600 seeds: its cell
+    borders 604 ring cells, so its search discovers more seeds at once than the fast
+    hash holds; the search is redone with the large layout and must still match the
+    oracle exactly (on a flat frame, with many equal distances and ring seeds that
+    share pixels, which also exercises the index tie-break and the pixel rule)."""
+    W = H = 601
     img = np.full((H, W), 100, np.uint8)
-    ang = np.linspace(0, 2 * np.pi, 500, endpoint=False)
-    ring = np.stack([150 + 140 * np.cos(ang), 150 + 140 * np.sin(ang)], 1)
-    pts = np.vstack([[[150.2, 149.9]], ring])
+    ang = np.linspace(0, 2 * np.pi, 1600, endpoint=False)
+    ring = np.stack([300 + 285 * np.cos(ang), 300 + 285 * np.sin(ang)], 1)
+    pts = np.vstack([[[300.2, 299.9]], ring])
     rng = np.random.default_rng(12)
     flow = rng.normal(0, 1, pts.shape)
     status = np.zeros(len(pts), np.uint8)
     g, o = run_both(dgf, img, pts, flow, status)
-    print(f"searches redone with the large frontier: {int(g['retried'][0])}")
+    print(f"searches redone with the large layout: {int(g['retried'][0])}")
     assert g["retried"][0] >= 1
+    assert_parity(g, o)
+
+
+def test_large_k_layout(dgf):
+    """k = 256 takes the larger fast layout."""
+    W, H = 160, 120
+    img = textured(W, H, 13)
+    pts, flow, status = random_matches(W, H, 700, 13)
+    g, o = run_both(dgf, img, pts, flow, status, k=256)
     assert_parity(g, o)
