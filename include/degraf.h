@@ -346,7 +346,7 @@ size_t dgf_epic_workspace(int W, int H, int n);
  * Returns DGF_ERR_ARG for bad arguments or parameters, DGF_ERR_WORKSPACE for a
  * short workspace, DGF_ERR_TIMEOUT if the labelling has not converged after 4096
  * passes, DGF_ERR_DEVICE if a neighbourhood search outgrew its largest
- * shared-memory frontier (more than 4096 discovered, unsettled seeds), else DGF_OK.
+ * shared-memory layout (more than 8192 discovered or settled seeds), else DGF_OK.
  */
 int epic_interpolate(const uint8_t* img, int W, int H, int pitch, const float* pts, const float* flow,
                      const uint8_t* status, int n, const dgf_epic_params* p, float* dense, const dgf_epic_debug* dbg,

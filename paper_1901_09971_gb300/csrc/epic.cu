@@ -16,8 +16,8 @@
 //      counter every four passes). Relaxation converges to the unique fixed
 //      point, the lexicographic (distance, seed) minimum, whatever the order;
 //   4-6. seed graph: links of 4-adjacent pixels in different cells are counted,
-//      scanned into offsets and filled into per-seed lists (duplicates kept: the
-//      search below takes their minimum);
+//      scanned into offsets (three launches: block scans, a scan of the block
+//      totals, the block offsets added) and filled into per-seed lists;
 //   7-8. each list keeps one link per neighbour (its smallest weight), and every
 //      link records where its neighbour's list lies, so a search reads a popped
 //      seed's links without first loading its list bounds;
@@ -242,6 +242,48 @@ __global__ void __launch_bounds__(1024) epic_scan_kernel(const int* cnt, int n, 
         __syncthreads();
     }
     if (t == 0) off[n] = carry;
+}
+
+// Multi-block exclusive scan of the link counts: each block scans 1024 counts and
+// publishes its total; the one-block scan above turns the totals into block
+// offsets; a last pass adds them (and fills the cursors).
+__global__ void __launch_bounds__(1024) epic_scan_blocks_kernel(const int* cnt, int n, int* off, int* bsum)
+{
+    __shared__ int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int i = blockIdx.x * 1024 + t;
+    const int v = i < n ? cnt[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int z = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        wsum[lane] = z;
+    }
+    __syncthreads();
+    if (i < n) off[i] = (w ? wsum[w - 1] : 0) + x - v;
+    if (t == 0) bsum[blockIdx.x] = wsum[31];
+}
+
+__global__ void __launch_bounds__(1024) epic_scan_add_kernel(const int* boff, int n, int nb, int* off, int* cur)
+{
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) {
+        const int o = off[i] + boff[blockIdx.x];
+        off[i] = o;
+        cur[i] = o;
+    }
+    if (i == 0) off[n] = boff[nb];
 }
 
 // Per seed: keeps one link per neighbour (the smallest weight), compacting the list
@@ -745,7 +787,7 @@ __global__ void __launch_bounds__(kThreads) epic_dense_kernel(const unsigned lon
 
 // Workspace layout (256-byte aligned sections).
 struct EpicLayout {
-    size_t key, cost, seed_pix, cnt, off, cur, minin, adj_t, adj_w, adj_i, models, retry, counters, total;
+    size_t key, cost, seed_pix, cnt, off, cur, minin, bsum, adj_t, adj_w, adj_i, models, retry, counters, total;
 };
 
 EpicLayout epic_layout(int W, int H, int n)
@@ -765,6 +807,7 @@ EpicLayout epic_layout(int W, int H, int n)
     L.off = take(((size_t)n + 1) * 4);
     L.cur = take((size_t)n * 4);
     L.minin = take((size_t)n * 4);
+    L.bsum = take(((size_t)n / 1024 + 2) * 12);  // block totals, block offsets (+1), scan cursors
     L.adj_t = take(nl * 4);
     L.adj_w = take(nl * 8);
     L.adj_i = take(nl * 16);
@@ -832,6 +875,7 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
     auto* adj_w = reinterpret_cast<long long*>(ws + L.adj_w);
     auto* adj_i = reinterpret_cast<int4*>(ws + L.adj_i);
     auto* minin = reinterpret_cast<unsigned*>(ws + L.minin);
+    auto* bsum = reinterpret_cast<int*>(ws + L.bsum);
     auto* retry_list = reinterpret_cast<int*>(ws + L.retry);
     auto* models = reinterpret_cast<double*>(ws + L.models);
     auto* changed = reinterpret_cast<int*>(ws + L.counters);
@@ -870,7 +914,10 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
     if (n > 0) {
         epic_links_kernel<false><<<pix_grid, pix_block, 0, stream>>>(key, cost, W, H, cnt, nullptr, nullptr, nullptr,
                                                                      nullptr, err);
-        epic_scan_kernel<<<1, 1024, 0, stream>>>(cnt, n, off, cur);
+        const int nb = (n + 1023) / 1024;
+        epic_scan_blocks_kernel<<<nb, 1024, 0, stream>>>(cnt, n, off, bsum);
+        epic_scan_kernel<<<1, 1024, 0, stream>>>(bsum, nb, bsum + nb, bsum + 2 * nb + 1);
+        epic_scan_add_kernel<<<nb, 1024, 0, stream>>>(bsum + nb, n, nb, off, cur);
         epic_links_kernel<true><<<pix_grid, pix_block, 0, stream>>>(key, cost, W, H, nullptr, off, cur, adj_t, adj_w,
                                                                     err);
         epic_dedupe_kernel<<<(unsigned)((n + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, stream>>>(
