@@ -367,6 +367,54 @@ def cpu_baseline(pair, reps: int = 2):
                       f"{dt:.1f} s wall"}
 
 
+def oracle_epe(dgf, torch, dev, pair):
+    """End-point error of the GPU path against the FP64 oracle (part of the CPU
+    baseline leg: the oracle runs on this host), per workload, on the GPU's own
+    key-points: the 1242x375 pair in full, the 256x128 pair, two pairs of the mixed
+    batch, and two 1242x375 translation pairs with FP32 and FP16 pyramid storage.
+    EPE over the points both sides tracked to convergence (TRACKED), with the
+    status agreement over all points."""
+    import oracle
+
+    def compare(I1, I2, win, step, levels, radius, storages=(("f32", None),)):
+        H, W = I1.shape
+        f1 = torch.from_numpy(I1).to(dev)
+        pts = dgf.detect(f1, win, step)
+        P = pts.cpu().numpy().astype(np.float64)
+        fo, so, _, _ = oracle.rlof_track(I1, I2, P, oracle.RlofParams(levels=levels, radius=radius, max_iter=30,
+                                                                      model=4))
+        out = {}
+        for name, storage in storages:
+            storage = dgf.F32 if storage is None else storage
+            prm = dgf.RlofParams(levels=levels, radius=radius, max_iter=30, model=4, storage=storage)
+            p1 = dgf.build_pyramid(f1, levels, storage, True)
+            p2 = dgf.build_pyramid(torch.from_numpy(I2).to(dev), levels, storage, False)
+            fg, sg = dgf.track(p1, p2, W, H, pts, prm)
+            fg, sg = fg.cpu().numpy().astype(np.float64), sg.cpu().numpy()
+            both = (sg == dgf.TRACKED) & (so == dgf.TRACKED)
+            e = np.hypot(*(fg - fo)[both].T)
+            out[name] = {"points": int(len(sg)), "both_tracked": int(both.sum()), "epe_mean_px": float(e.mean()),
+                         "epe_p99_px": float(np.percentile(e, 99)), "epe_max_px": float(e.max()),
+                         "within_1e-2_px": float(np.mean(e <= 1e-2)), "status_agreement": float(np.mean(sg == so))}
+        return out if len(storages) > 1 else out["f32"]
+
+    res = {"definition": "unsquared end-point difference GPU vs FP64 oracle on points TRACKED by both; "
+                         "status agreement over all points"}
+    res["driving_scene_1242x375"] = compare(pair.I1, pair.I2, WORKLOAD["win"], WORKLOAD["step"], WORKLOAD["levels"],
+                                            WORKLOAD["radius"])
+    p1 = synth.make_pair(1)
+    res["translation_256x128"] = compare(p1.I1, p1.I2, p1.win, p1.step, p1.levels, p1.radius)
+    specs = synth.make_batch_specs(64, 3000)
+    for i in range(2):
+        W, H, st = specs[i]
+        fr = synth.make_translation_pair(W, H, seed=3000 + i)
+        res[f"batch_pair_{i}_{W}x{H}_step{st}"] = compare(fr.I1, fr.I2, 8, st, 3, 4)
+    for i in range(2):
+        q = synth.make_pair(4, index=i)
+        res[f"storage_pair_{i}_1242x375"] = compare(q.I1, q.I2, 8, 4, 3, 4, (("f32", dgf.F32), ("f16", dgf.F16)))
+    return res
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
@@ -526,6 +574,7 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
             line["epic"] = run_epic(dgf, torch, dev, pair)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pair)
+            line["epe_vs_oracle"] = oracle_epe(dgf, torch, dev, pair)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
