@@ -19,6 +19,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -129,6 +130,8 @@ def run_batched(dgf, torch, dev, reps: int = 10):
     prm = dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)
     bt = dgf.BatchTracker(specs, prm, dev)
     bt.bind(d1, d2)
+    with tempfile.TemporaryDirectory() as tmp:  # the launch shape, tuned on this batch
+        tuned = bt.autotune(reps=3, path=os.path.join(tmp, "tune.json"))
     stream = torch.cuda.current_stream(dev)
 
     def timed(stages, reps):
@@ -161,6 +164,7 @@ def run_batched(dgf, torch, dev, reps: int = 10):
                       "(working set > L2, no flush)",
             "pairs": 64, "points": npts, "ms_per_batch": t_all, "points_per_s": npts / (t_all / 1e3),
             "pairs_per_s": 64 / (t_all / 1e3),
+            "autotune": {"lanes_per_point": tuned["lanes"], "ms_per_batch_by_lanes": tuned["ms"]},
             "detect_pyramid": {"ms": t_dp, "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
                                "frac_of_measured_hbm": gbs / HBM_PEAK_GBS}}
 

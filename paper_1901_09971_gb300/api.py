@@ -11,7 +11,7 @@ import dataclasses
 
 import torch
 
-from . import _abi
+from . import _abi, tune
 from ._abi import F16, F32, check, load
 
 
@@ -405,11 +405,14 @@ class BatchTracker:
     ``bind`` + ``run()`` reuse validated descriptors of fixed frame buffers.
     """
 
-    def __init__(self, specs, params: RlofParams, device: torch.device | str = "cuda"):
+    def __init__(self, specs, params: RlofParams, device: torch.device | str = "cuda", lanes=0):
         self.specs = [tuple(int(v) for v in sp) for sp in specs]
         self.params = params
         self.device = torch.device(device)
         self.n = [degraf_count(W, H, win, step) for (W, H, win, step) in self.specs]
+        # lanes per tracked point: 0 = the library's choice, 8 / 16 / 32, or "auto" =
+        # the autotuner's cached choice for this GPU, parameters and batch size
+        self.lanes = (tune.lookup(self.tune_key()) or 0) if lanes == "auto" else int(lanes)
         dev = self.device
         self.pts = [torch.empty((n, 2), dtype=torch.float32, device=dev) for n in self.n]
         self.flow = [torch.empty((n, 2), dtype=torch.float32, device=dev) for n in self.n]
@@ -452,10 +455,43 @@ class BatchTracker:
             self.bind(frames1, frames2)
         elif getattr(self, "_arr", None) is None:
             raise ValueError("run() without frames needs frames bound first")
-        check("rlof_track_many", load().rlof_track_many(self._arr, len(self.specs), ctypes.byref(self._prm),
-                                                        _ptr(self.workspace), self.workspace.numel(), int(stages),
-                                                        int(use_graph), _stream()))
+        prev = set_lanes(self.lanes) if self.lanes else None
+        try:
+            check("rlof_track_many", load().rlof_track_many(self._arr, len(self.specs), ctypes.byref(self._prm),
+                                                            _ptr(self.workspace), self.workspace.numel(), int(stages),
+                                                            int(use_graph), _stream()))
+        finally:
+            if prev is not None:
+                set_lanes(prev)
         return self.pts, self.flow, self.status, self.iters
+
+    def tune_key(self) -> str:
+        return tune.key(torch.cuda.get_device_name(self.device), self.params, sum(self.n))
+
+    def autotune(self, frames1=None, frames2=None, reps: int = 5, path: str | None = None) -> dict:
+        """Times the whole batch (detection, pyramids, tracking; graph replay) for
+        every lane count the library honours at this radius, keeps the fastest for
+        this tracker and records it in the autotuner's cache. Returns the record."""
+        if frames1 is not None or frames2 is not None:
+            self.bind(frames1, frames2)
+        stream = torch.cuda.current_stream(self.device)
+
+        def measure(lanes: int) -> float:
+            self.lanes = lanes
+            for _ in range(2):
+                self.run()
+            torch.cuda.synchronize(self.device)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                self.run()
+            b.record(stream)
+            b.synchronize()
+            return a.elapsed_time(b) / reps
+
+        rec = tune.tune(measure, self.params.radius, self.tune_key(), path)
+        self.lanes = rec["lanes"]
+        return rec
 
 
 def track_pair(frame1, frame2, win: int, step: int, params: RlofParams, device="cuda"):

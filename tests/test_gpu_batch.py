@@ -155,3 +155,28 @@ def test_mixed_size_batch_of_64_pairs(dgf):
         e = np.hypot(*(fg.astype(np.float64) - fo).T)
         assert np.mean(sg == so) >= 0.98
         assert np.mean(e[both] <= TOL_FLOW) >= 0.99
+
+
+def test_autotune_picks_a_shape_and_every_shape_tracks_alike(dgf, tmp_path, monkeypatch):
+    """The autotuner times every lane count the library honours at radius 4, keeps
+    the fastest for the tracker and in its cache (which lanes="auto" then reads);
+    every shape tracks the batch like the library's default within the tracking
+    bars (the shapes sum the normal equations in different orders, so FP32
+    trajectories may part at a threshold)."""
+    monkeypatch.setenv("DGF_TUNE_CACHE", str(tmp_path / "tune.json"))
+    prm = dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)
+    frames = frames_for(SMALL_SPECS, 500)
+    bt, d1, d2 = run_batch(dgf, SMALL_SPECS, frames, prm, True)
+    ref = [(f.cpu().numpy().copy(), s.cpu().numpy().copy()) for f, s in zip(bt.flow, bt.status)]
+    rec = bt.autotune(reps=2)
+    assert rec["lanes"] in (8, 16, 32) and set(rec["ms"]) == {"8", "16", "32"} and bt.lanes == rec["lanes"]
+    assert dgf.BatchTracker(SMALL_SPECS, prm, lanes="auto").lanes == rec["lanes"]
+    for lanes in (8, 16, 32):
+        bt.lanes = lanes
+        bt.run()
+        torch.cuda.synchronize()
+        for i, (fr, sr) in enumerate(ref):
+            f, s = bt.flow[i].cpu().numpy(), bt.status[i].cpu().numpy()
+            assert np.mean(s == sr) >= 0.995, (lanes, i)
+            both = (s == 0) & (sr == 0)
+            assert np.mean(np.abs(f[both] - fr[both]).max(axis=1) <= 1e-2) >= 0.999, (lanes, i)
