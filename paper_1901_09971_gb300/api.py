@@ -247,7 +247,8 @@ def epic_workspace_bytes(W: int, H: int, n: int) -> int:
 
 
 def epic_interpolate(frame: torch.Tensor, pts: torch.Tensor, flow: torch.Tensor, status: torch.Tensor,
-                     params: EpicParams = EpicParams(), debug: bool = False, workspace: torch.Tensor | None = None):
+                     params: EpicParams = EpicParams(), debug: bool = False, workspace: torch.Tensor | None = None,
+                     out: torch.Tensor | None = None):
     """Dense flow (float32 [H, W, 2]) from sparse matches by EPIC interpolation
     (epic_interpolate). With debug=True also returns a dict of the labels, geodesic
     distances, neighbourhoods, per-seed models and fit kinds."""
@@ -259,7 +260,9 @@ def epic_interpolate(frame: torch.Tensor, pts: torch.Tensor, flow: torch.Tensor,
         raise ValueError("status must be a contiguous uint8 tensor [n]")
     n = pts.shape[0]
     dev = frame.device
-    dense = torch.empty((H, W, 2), dtype=torch.float32, device=dev)
+    dense = out if out is not None else torch.empty((H, W, 2), dtype=torch.float32, device=dev)
+    if dense.shape != (H, W, 2) or dense.dtype != torch.float32 or not dense.is_contiguous():
+        raise ValueError("out must be a contiguous float32 tensor [H, W, 2]")
     if workspace is None:
         workspace = torch.empty(max(epic_workspace_bytes(W, H, n), 256), dtype=torch.uint8, device=dev)
     out = None
@@ -492,6 +495,55 @@ class BatchTracker:
         rec = tune.tune(measure, self.params.radius, self.tune_key(), path)
         self.lanes = rec["lanes"]
         return rec
+
+
+class DenseFlow:
+    """The DeGraF-Flow pipeline for one frame size (Section 2): DeGraF key-points on
+    frame 1, RLOF tracking into frame 2 (with the global-motion prior, the paper's
+    RLOF(IM-GM), unless gm is None), optionally the forward-backward filter
+    (fb_max > 0; both pyramids then carry gradients), and EPIC interpolation of the
+    tracked points into a dense flow field. Pyramids, key-points, workspaces and the
+    dense field are allocated once; ``run`` returns the dense field [H, W, 2] and the
+    sparse (points, flow, status). EPIC reads a convergence counter on the host, so a
+    run synchronises the stream."""
+
+    def __init__(self, W: int, H: int, win: int, step: int, params: RlofParams, gm: GmParams | None = None,
+                 epic: EpicParams | None = None, fb_max: float = 0.0, device: torch.device | str = "cuda"):
+        self.W, self.H, self.win, self.step = W, H, win, step
+        self.params, self.gm, self.fb_max = params, gm, float(fb_max)
+        self.epic = epic or EpicParams()
+        self.device = dev = torch.device(device)
+        self.levels = params.levels + (gm.extra_levels if gm is not None else 0)
+        grad2 = self.fb_max > 0
+        self.pyr1 = torch.empty(pyramid_bytes(W, H, self.levels, params.storage, True), dtype=torch.uint8, device=dev)
+        self.pyr2 = torch.empty(pyramid_bytes(W, H, self.levels, params.storage, grad2), dtype=torch.uint8,
+                                device=dev)
+        self.n = degraf_count(W, H, win, step)
+        self.pts = torch.empty((self.n, 2), dtype=torch.float32, device=dev)
+        self.dense = torch.empty((H, W, 2), dtype=torch.float32, device=dev)
+        self.ws_epic = torch.empty(max(epic_workspace_bytes(W, H, self.n), 256), dtype=torch.uint8, device=dev)
+        self.ws_gm = (torch.zeros(max(gm_workspace_bytes(self.n, gm), 256), dtype=torch.uint8, device=dev)
+                      if gm is not None else None)
+        self.ws_fb = (torch.empty(max(int(load().dgf_fb_workspace(self.n)), 256), dtype=torch.uint8, device=dev)
+                      if grad2 else None)
+        if gm is not None and grad2:
+            raise ValueError("choose the global-motion prior or the forward-backward filter")
+
+    def run(self, frame1: torch.Tensor, frame2: torch.Tensor):
+        prm = self.params
+        detect(frame1, self.win, self.step, out=self.pts)
+        build_pyramid(frame1, self.levels, prm.storage, True, out=self.pyr1)
+        build_pyramid(frame2, self.levels, prm.storage, self.fb_max > 0, out=self.pyr2)
+        if self.gm is not None:
+            flow, status = track_gm(self.pyr1, self.pyr2, self.W, self.H, self.levels, self.pts, prm, self.gm,
+                                    workspace=self.ws_gm)[:2]
+        elif self.fb_max > 0:
+            flow, status, _ = track_fb(self.pyr1, self.pyr2, self.W, self.H, self.pts, prm, self.fb_max,
+                                       workspace=self.ws_fb)
+        else:
+            flow, status = track(self.pyr1, self.pyr2, self.W, self.H, self.pts, prm)
+        epic_interpolate(frame1, self.pts, flow, status, self.epic, workspace=self.ws_epic, out=self.dense)
+        return self.dense, (self.pts, flow, status)
 
 
 def track_pair(frame1, frame2, win: int, step: int, params: RlofParams, device="cuda"):
