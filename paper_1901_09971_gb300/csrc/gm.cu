@@ -3,18 +3,19 @@
 // model used is a global affine motion fitted robustly to a sparse first pass and
 // used as every point's initial flow in the main pass.
 //
-// The fit runs in one CTA: per IRLS iteration every thread accumulates the weighted
-// normal-equation sums of its points in FP64, the CTA reduces them in a fixed tree
-// order (deterministic), and one thread solves the two 3 x 3 systems. It is tiny
-// next to tracking (a few sums per first-pass point), so one CTA is enough and no
-// host round trip separates the three stages: the main pass reads the fitted
-// parameters from device memory.
+// The fit is an IRLS loop of a few iterations, each two launches: 64 CTAs sum the
+// weighted normal equations of their points in FP64 (GB300's FP64 pipe is narrow,
+// so the sums are spread over the SMs) into per-CTA partials, then one warp adds the
+// partials in CTA order (deterministic) and solves the two 3 x 3 systems. The
+// state (affine, fitted flag, go-on flag) lives in the workspace, so no host round
+// trip separates the stages: the main pass reads the fitted parameters from device
+// memory.
 #include "common.cuh"
 #include "batch.cuh"
 
 namespace {
 
-constexpr int kFitThreads = 1024;
+constexpr int kPartThreads = 256, kPartBlocks = 64;
 constexpr int kSums = 12;  // xx xy x yy y w | x qx, y qx, qx | x qy, y qy, qy
 
 // Cholesky solve of the 3 x 3 normal equations (row-major m[9]); a pivot below
@@ -46,92 +47,97 @@ __device__ bool solve3(const double* m, const double* b, double* x)
     return true;
 }
 
-// Robust affine fit over the n first-pass points (point k at pts[k * stride]).
-// out: a[6] then an int flag at byte 48 (1 = fitted).
-__global__ void __launch_bounds__(kFitThreads) gm_fit_kernel(const float* pts, int stride, const float* flow,
-                                                             const uint8_t* status, int n, int iters, double c0,
-                                                             double c_min, double* out)
+// State at the start of the workspace: a[6] (doubles), then int flags at byte 48
+// (1 = fitted) and byte 52 (1 = iterating).
+__global__ void gm_init_kernel(double* state)
 {
-    __shared__ double part[kFitThreads / 32][kSums];
-    __shared__ int used_part[kFitThreads / 32];
-    __shared__ double a[6];
-    __shared__ int go, made;
+    state[0] = 1; state[1] = 0; state[2] = 0;
+    state[3] = 0; state[4] = 1; state[5] = 0;
+    reinterpret_cast<int*>(state + 6)[0] = 0;
+    reinterpret_cast<int*>(state + 6)[1] = 1;
+}
+
+// IRLS iteration k, part 1: per-CTA sums over the points of the CTA's grid stride
+// (point i at pts[i * stride]); partial[blockIdx.x][0..11] = the 12 sums,
+// [12] = the number of weighted points.
+__global__ void __launch_bounds__(kPartThreads) gm_partial_kernel(const float* pts, int stride, const float* flow,
+                                                                  const uint8_t* status, int n, int k, double c0,
+                                                                  double c_min, const double* state,
+                                                                  double* partial)
+{
+    __shared__ double part[kPartThreads / 32][kSums + 1];
+    if (!reinterpret_cast<const int*>(state + 6)[1]) return;  // uniform: the fit has stopped
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        a[0] = 1; a[1] = 0; a[2] = 0;
-        a[3] = 0; a[4] = 1; a[5] = 0;
-        go = 1;
-        made = 0;
+    double a[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) a[j] = state[j];
+    const double ck = fmax(c_min, ldexp(c0, -(k - 1)));
+    double s[kSums + 1];
+#pragma unroll
+    for (int j = 0; j <= kSums; ++j) s[j] = 0.0;
+    for (int i = blockIdx.x * kPartThreads + threadIdx.x; i < n; i += kPartBlocks * kPartThreads) {
+        if (status[i] != DGF_TRACKED) continue;
+        const float2 p = reinterpret_cast<const float2*>(pts)[(long long)i * stride];
+        const float2 f = reinterpret_cast<const float2*>(flow)[i];
+        const double x = p.x, y = p.y, qx = x + (double)f.x, qy = y + (double)f.y;
+        double w = 1.0;
+        if (k > 0) {
+            const double ex = a[0] * x + a[1] * y + a[2] - qx, ey = a[3] * x + a[4] * y + a[5] - qy;
+            const double e = sqrt(ex * ex + ey * ey);
+            if (e >= ck) continue;
+            const double u = 1.0 - (e / ck) * (e / ck);
+            w = u * u;
+        }
+        s[0] += w * x * x;
+        s[1] += w * x * y;
+        s[2] += w * x;
+        s[3] += w * y * y;
+        s[4] += w * y;
+        s[5] += w;
+        s[6] += w * x * qx;
+        s[7] += w * y * qx;
+        s[8] += w * qx;
+        s[9] += w * x * qy;
+        s[10] += w * y * qy;
+        s[11] += w * qy;
+        s[12] += 1.0;
     }
+    // fixed-order reduction: xor butterfly in each warp, then thread 0 over the warps
+#pragma unroll
+    for (int j = 0; j <= kSums; ++j)
+        for (int o = 16; o > 0; o >>= 1) s[j] += __shfl_xor_sync(0xffffffffu, s[j], o);
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j <= kSums; ++j) part[warp][j] = s[j];
     __syncthreads();
-    for (int k = 0; k < iters; ++k) {
-        if (!go) break;  // uniform: every thread reads it after the same barrier
-        const double ck = fmax(c_min, ldexp(c0, -(k - 1)));
-        double s[kSums];
-#pragma unroll
-        for (int j = 0; j < kSums; ++j) s[j] = 0.0;
-        int used = 0;
-        for (int i = threadIdx.x; i < n; i += kFitThreads) {
-            if (status[i] != DGF_TRACKED) continue;
-            const float2 p = reinterpret_cast<const float2*>(pts)[(long long)i * stride];
-            const float2 f = reinterpret_cast<const float2*>(flow)[i];
-            const double x = p.x, y = p.y, qx = x + (double)f.x, qy = y + (double)f.y;
-            double w = 1.0;
-            if (k > 0) {
-                const double ex = a[0] * x + a[1] * y + a[2] - qx, ey = a[3] * x + a[4] * y + a[5] - qy;
-                const double e = sqrt(ex * ex + ey * ey);
-                if (e >= ck) continue;
-                const double u = 1.0 - (e / ck) * (e / ck);
-                w = u * u;
-            }
-            s[0] += w * x * x;
-            s[1] += w * x * y;
-            s[2] += w * x;
-            s[3] += w * y * y;
-            s[4] += w * y;
-            s[5] += w;
-            s[6] += w * x * qx;
-            s[7] += w * y * qx;
-            s[8] += w * qx;
-            s[9] += w * x * qy;
-            s[10] += w * y * qy;
-            s[11] += w * qy;
-            ++used;
-        }
-        // fixed-order reduction: xor butterfly in each warp, then one thread over the warps
-#pragma unroll
-        for (int j = 0; j < kSums; ++j)
-            for (int o = 16; o > 0; o >>= 1) s[j] += __shfl_xor_sync(0xffffffffu, s[j], o);
-        for (int o = 16; o > 0; o >>= 1) used += __shfl_xor_sync(0xffffffffu, used, o);
-        if (lane == 0) {
-#pragma unroll
-            for (int j = 0; j < kSums; ++j) part[warp][j] = s[j];
-            used_part[warp] = used;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t[kSums];
-            int u = 0;
-            for (int j = 0; j < kSums; ++j) t[j] = 0.0;
-            for (int w = 0; w < kFitThreads / 32; ++w) {
-                for (int j = 0; j < kSums; ++j) t[j] += part[w][j];
-                u += used_part[w];
-            }
-            const double m[9] = {t[0], t[1], t[2], t[1], t[3], t[4], t[2], t[4], t[5]};
-            const double bx[3] = {t[6], t[7], t[8]}, by[3] = {t[9], t[10], t[11]};
-            double sx[3], sy[3];
-            if (u < 3 || !solve3(m, bx, sx) || !solve3(m, by, sy)) {
-                go = 0;  // keep the previous estimate
-            } else {
-                a[0] = sx[0]; a[1] = sx[1]; a[2] = sx[2];
-                a[3] = sy[0]; a[4] = sy[1]; a[5] = sy[2];
-                made = 1;
-            }
-        }
-        __syncthreads();
+    if (threadIdx.x <= kSums) {
+        double t = 0.0;
+        for (int w = 0; w < kPartThreads / 32; ++w) t += part[w][threadIdx.x];
+        partial[blockIdx.x * (kSums + 1) + threadIdx.x] = t;
     }
-    if (threadIdx.x < 6) out[threadIdx.x] = a[threadIdx.x];
-    if (threadIdx.x == 0) reinterpret_cast<int*>(out + 6)[0] = made;
+}
+
+// IRLS iteration k, part 2: the partials added in CTA order and the two 3 x 3
+// systems solved; a step with fewer than 3 weighted points or a singular matrix
+// keeps the previous estimate and stops the loop.
+__global__ void gm_solve_kernel(const double* partial, double* state)
+{
+    int* flags = reinterpret_cast<int*>(state + 6);
+    if (!flags[1] || threadIdx.x != 0) return;
+    double t[kSums + 1];
+    for (int j = 0; j <= kSums; ++j) t[j] = 0.0;
+    for (int b = 0; b < kPartBlocks; ++b)
+        for (int j = 0; j <= kSums; ++j) t[j] += partial[b * (kSums + 1) + j];
+    const double m[9] = {t[0], t[1], t[2], t[1], t[3], t[4], t[2], t[4], t[5]};
+    const double bx[3] = {t[6], t[7], t[8]}, by[3] = {t[9], t[10], t[11]};
+    double sx[3], sy[3];
+    if (t[12] < 3.0 || !solve3(m, bx, sx) || !solve3(m, by, sy)) {
+        flags[1] = 0;  // keep the previous estimate
+        return;
+    }
+    state[0] = sx[0]; state[1] = sx[1]; state[2] = sx[2];
+    state[3] = sy[0]; state[4] = sy[1]; state[5] = sy[2];
+    flags[0] = 1;
 }
 
 bool gm_params_ok(const dgf_gm_params* g)
@@ -140,9 +146,12 @@ bool gm_params_ok(const dgf_gm_params* g)
            g->iters <= 64 && g->c0 > 0 && g->c_min > 0;
 }
 
-// Workspace layout: [a[6], flag; 256 B] [first-pass flow, n_sub x 8 B] [first-pass status, n_sub B]
+// Workspace layout: [a[6], flags; 256 B] [first-pass flow, n_sub x 8 B] [first-pass status, n_sub B]
+// [per-CTA partial sums, 64 x 13 doubles]
 size_t flow_offset() { return 256; }
 size_t status_offset(long long n_sub) { return dgf::round_up(flow_offset() + (size_t)n_sub * 8, 256); }
+size_t partial_offset(long long n_sub) { return dgf::round_up(status_offset(n_sub) + (size_t)n_sub, 256); }
+constexpr size_t kPartialBytes = (size_t)kPartBlocks * (kSums + 1) * 8;
 
 }  // namespace
 
@@ -161,7 +170,7 @@ extern "C" size_t dgf_gm_workspace(int n, const dgf_gm_params* g)
 {
     if (n < 0 || !gm_params_ok(g)) return 0;
     const long long n_sub = ((long long)n + g->stride - 1) / g->stride;
-    return dgf::round_up(status_offset(n_sub) + (size_t)n_sub, 256);
+    return dgf::round_up(partial_offset(n_sub) + kPartialBytes, 256);
 }
 
 extern "C" int rlof_track_gm(const void* pyr1, const void* pyr2, int W, int H, int pyr_levels, const float* pts, int n,
@@ -199,8 +208,13 @@ extern "C" int rlof_track_gm(const void* pyr1, const void* pyr2, int W, int H, i
                                   sub_status, nullptr, nullptr, 0, g->stride, nullptr};
     if ((rc = dgf::launch_track(first, &deep, stream)) != DGF_OK) return rc;
     // 2. robust affine fit
-    gm_fit_kernel<<<1, kFitThreads, 0, stream>>>(pts, g->stride, sub_flow, sub_status, (int)n_sub, g->iters, g->c0,
-                                                 g->c_min, affine);
+    double* partial = reinterpret_cast<double*>(ws + partial_offset(n_sub));
+    gm_init_kernel<<<1, 1, 0, stream>>>(affine);
+    for (int k = 0; k < g->iters; ++k) {
+        gm_partial_kernel<<<kPartBlocks, kPartThreads, 0, stream>>>(pts, g->stride, sub_flow, sub_status, (int)n_sub,
+                                                                     k, g->c0, g->c_min, affine, partial);
+        gm_solve_kernel<<<1, 32, 0, stream>>>(partial, affine);
+    }
     if ((rc = dgf::launch_status()) != DGF_OK) return rc;
     // 3. main pass from the prior
     main.pyr_levels = pyr_levels;
