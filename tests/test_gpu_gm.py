@@ -128,3 +128,25 @@ def test_gm_without_a_fit_is_plain_tracking(dgf):
     f0, s0 = dgf.track(p1, p2, p.W, p.H, to_dev(pts32), prm)
     np.testing.assert_array_equal(fg, f0.cpu().numpy())
     np.testing.assert_array_equal(sg, s0.cpu().numpy())
+
+
+def test_gm_with_cross_support_driving_scene(dgf):
+    """The paper's tracking configuration (Section 3: RLOF(IM-GM) with the adaptive
+    cross-based support) on the driving scene: the fit on the GPU's own first pass
+    equals the oracle's fit on the same tracks, and the main pass meets the cross
+    support's bars for this scene (tau 20) against the oracle run from the same prior."""
+    p = synth.make_pair(2)
+    pts, _, _ = oracle.degraf_detect(p.I1, p.win, p.win, p.step)
+    pts32 = pts.astype(np.float32)
+    pts64 = pts32.astype(np.float64)
+    tau = 20.0
+    prm = dgf.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4, cross_tau=tau)
+    gm = dgf.GmParams(extra_levels=0)
+    fg, sg, a, made, sub_flow, sub_status, _ = run_gm(dgf, p, pts32, prm, gm)
+    assert made == 1
+    a_o, made_o = oracle.gm_fit_affine(pts64[::gm.stride], sub_flow, sub_status, gm.iters, gm.c0, gm.c_min)
+    assert made_o
+    assert np.abs(oracle.gm_prior_flow(a, pts64) - oracle.gm_prior_flow(a_o, pts64)).max() < 1e-6
+    oprm = oracle.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4, cross_tau=tau)
+    fo, so, _, _ = oracle.rlof_track(p.I1, p.I2, pts64, oprm, init_flow=oracle.gm_prior_flow(a, pts64))
+    print("gm + cross", bars(fg, sg, fo, so, agree_min=0.98, within_min=0.995))
