@@ -392,6 +392,37 @@ def cpu_baseline(pair, reps: int = 2):
                       f"{dt:.1f} s wall"}
 
 
+def oracle_next_rows(dgf, torch, dev, pair):
+    """The FP64 oracle of each extension timed on this host beside its GPU section
+    (part of the CPU baseline leg), on the same 1242x375 pair: the global-motion
+    prior, the cross-based support (tau 20), the forward-backward filter (1 px), and
+    EPIC (k 128) on the GPU's plain tracks. One run each, wall time on all cores."""
+    import oracle
+    prm = oracle.RlofParams(levels=WORKLOAD["levels"], radius=WORKLOAD["radius"], max_iter=WORKLOAD["max_iter"],
+                            model=WORKLOAD["model"])
+    f1 = torch.from_numpy(pair.I1).to(dev)
+    pts_d = dgf.detect(f1, WORKLOAD["win"], WORKLOAD["step"])
+    pts = pts_d.cpu().numpy().astype(np.float64)
+    out = {}
+
+    def timed(name, fn):
+        t0 = time.perf_counter()
+        fn()
+        out[name] = {"oracle_ms": 1e3 * (time.perf_counter() - t0), "cores": oracle.max_threads(), "kind": "oracle"}
+
+    timed("gm_prior", lambda: oracle.rlof_track_gm(pair.I1, pair.I2, pts, prm, extra_levels=0))
+    timed("cross_support", lambda: oracle.rlof_track(pair.I1, pair.I2, pts,
+                                                     oracle.RlofParams(**{**prm.__dict__, "cross_tau": 20.0})))
+    timed("fb_filter", lambda: oracle.rlof_track_fb(pair.I1, pair.I2, pts, prm, 1.0))
+    gp = dgf.RlofParams(levels=prm.levels, radius=prm.radius, max_iter=prm.max_iter, model=prm.model)
+    p1 = dgf.build_pyramid(f1, gp.levels, dgf.F32, True)
+    p2 = dgf.build_pyramid(torch.from_numpy(pair.I2).to(dev), gp.levels, dgf.F32, False)
+    flow, status = dgf.track(p1, p2, pair.W, pair.H, pts_d, gp)
+    fl, st = flow.cpu().numpy().astype(np.float64), status.cpu().numpy()
+    timed("epic", lambda: oracle.epic_interpolate(pair.I1, pts, fl, st, oracle.EpicParams()))
+    return out
+
+
 def oracle_epe(dgf, torch, dev, pair):
     """End-point error of the GPU path against the FP64 oracle (part of the CPU
     baseline leg: the oracle runs on this host), per workload, on the GPU's own
@@ -601,6 +632,9 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pair)
             line["epe_vs_oracle"] = oracle_epe(dgf, torch, dev, pair)
+            if not args.no_batched:
+                for name, rec in oracle_next_rows(dgf, torch, dev, pair).items():
+                    line[name]["oracle"] = rec
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
