@@ -582,14 +582,47 @@ __device__ int knn_search(const KnnArgs& a, int s, unsigned char* base, int& cnt
         }
         if (lane == 0) *fcount = kept;
         __syncwarp();
-        // relax the batch's links, one lane per batch seed
+        // relax the batch's links, one lane per link: the batch seeds' link counts
+        // are prefix-summed over the warp (32 seeds at a time) and each lane finds
+        // the seed owning its link by a binary search over the sums, so all the
+        // links' loads are in flight together
         int st = 0;
-        for (int i = nset0 + lane; i < nset; i += 32) {
-            const int u = (int)(skey[i] & kIdxMask);
-            const long long du = (long long)(skey[i] >> kIdxBits);
-            for (int e = a.off[u], e1 = a.end[u]; e < e1; ++e) {
-                const int4 li = a.adj_i[e];
-                const long long nd = du + a.adj_w[e];
+        for (int b0 = nset0; b0 < nset; b0 += 32) {
+            const int nb = min(32, nset - b0);
+            int u = 0, first = 0, deg = 0;
+            long long du = 0;
+            if (lane < nb) {
+                const unsigned long long kb = skey[b0 + lane];
+                u = (int)(kb & kIdxMask);
+                du = (long long)(kb >> kIdxBits);
+                first = a.off[u];
+                deg = a.end[u] - first;
+            }
+            int incl = deg;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int c0 = 0; c0 < total; c0 += 32) {
+                const int e = c0 + lane;
+                // owner: the first batch lane whose inclusive sum exceeds e
+                int lo = 0, hi = nb - 1;
+#pragma unroll
+                for (int it = 0; it < 5; ++it) {
+                    const int mid = (lo + hi) >> 1;
+                    const int v = __shfl_sync(0xffffffffu, incl, mid);
+                    if (v > e) hi = mid; else lo = min(mid + 1, hi);
+                }
+                const int ow = lo;
+                const int ofirst = __shfl_sync(0xffffffffu, first, ow);
+                const int oexcl = __shfl_sync(0xffffffffu, incl - deg, ow);
+                const long long odu = __shfl_sync(0xffffffffu, du, ow);
+                if (e >= total || st) continue;
+                const int le = ofirst + (e - oexcl);
+                const int4 li = a.adj_i[le];
+                const long long nd = odu + a.adj_w[le];
                 if (nd >= kDistLimit) st |= kErrRange;
                 const int t = li.x;
                 int h = slot_of(t), hs = -1;
@@ -620,7 +653,7 @@ __device__ int knn_search(const KnnArgs& a, int s, unsigned char* base, int& cnt
                 }
                 if (hs < 0) {
                     st |= kRetry;
-                    break;
+                    continue;
                 }
                 // a settled seed keeps its final distance: the minimum is a no-op there
                 if (hst[hs] == kFrontier)
