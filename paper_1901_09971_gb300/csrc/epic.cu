@@ -439,6 +439,53 @@ __device__ __forceinline__ double exp_neg(double y)
     return e * __ldg(&kExp2Frac[k & 31]) * s1 * s2;
 }
 
+// Double-float arithmetic (an unevaluated pair hi + lo of FP32 values, about 48
+// significant bits; Dekker 1971, Knuth's TwoSum): the fit's per-neighbour products
+// and sums run on GB300's wide FP32 pipe instead of its narrow FP64 pipe, at an
+// accuracy far inside what the fit needs. Written with the _rn intrinsics so that
+// no addition is contracted or reordered.
+struct dfl {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfl two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ dfl fast_two_sum(float a, float b)  // |a| >= |b| or a == 0
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)));
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfl df_mul(dfl a, float b)
+{
+    const float p = __fmul_rn(a.hi, b);
+    const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfl df_add(dfl a, dfl b)
+{
+    const dfl s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ dfl to_dfl(double v)
+{
+    const float hi = __double2float_rn(v);
+    return {hi, __double2float_rn(v - (double)hi)};
+}
+
 // Sums of 12 values over the warp; the totals land in lane 0. Halving exchanges:
 // lanes 16 apart swap half of their values and keep the sum of the other half, then
 // lanes 8 apart the same with 3 of 6, then xor butterflies finish the 3 sums in each
@@ -679,9 +726,11 @@ __device__ int knn_search(const KnnArgs& a, int s, unsigned char* base, int& cnt
     return status & kErrRange ? kErrRange : status;
 }
 
-// The weighted affine fit of seed s over its neighbourhood (sorted keys; FP64, as
-// the 3 x 3 normal equations lose too many digits in FP32 when a neighbourhood is
-// narrow) and the outputs. M = sum w v v^T, v = (x_t - x_s, y_t - y_s, 1).
+// The weighted affine fit of seed s over its neighbourhood (sorted keys) and the
+// outputs. The 3 x 3 normal equations lose too many digits in FP32 when a
+// neighbourhood is narrow: the weights come from an FP64 exponential, the
+// per-neighbour terms are summed in double-float, the lanes' sums are reduced and
+// the systems solved in FP64. M = sum w v v^T, v = (x_t - x_s, y_t - y_s, 1).
 __device__ void knn_fit_write(const KnnArgs& a, int s, int cnt, const unsigned long long* key)
 {
     const int lane = threadIdx.x & 31, k = a.k;
@@ -692,20 +741,33 @@ __device__ void knn_fit_write(const KnnArgs& a, int s, int cnt, const unsigned l
             a.knn_dist[(size_t)s * k + j] = (int64_t)(key[j] >> kIdxBits);
         }
     const float2 ps = a.pts[s];
-    double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    dfl acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = {0.f, 0.f};
     for (int j = lane; j < cnt; j += 32) {
         const int t = (int)(key[j] & kIdxMask);
-        const double w = exp_neg(a.a_per_unit * (double)(long long)(key[j] >> kIdxBits));
+        const dfl w = to_dfl(exp_neg(a.a_per_unit * (double)(long long)(key[j] >> kIdxBits)));
         const float2 pt = a.pts[t], ft = a.flow[t];
-        const double vx = (double)pt.x - (double)ps.x, vy = (double)pt.y - (double)ps.y;
-        const double fu = ft.x, fv = ft.y, wx = w * vx, wy = w * vy;
-        acc[0] = fma(wx, vx, acc[0]); acc[1] = fma(wx, vy, acc[1]); acc[2] += wx;
-        acc[3] = fma(wy, vy, acc[3]); acc[4] += wy; acc[5] += w;
-        acc[6] = fma(wx, fu, acc[6]); acc[7] = fma(wy, fu, acc[7]); acc[8] = fma(w, fu, acc[8]);
-        acc[9] = fma(wx, fv, acc[9]); acc[10] = fma(wy, fv, acc[10]); acc[11] = fma(w, fv, acc[11]);
+        const dfl vx = two_sum(pt.x, -ps.x), vy = two_sum(pt.y, -ps.y);  // exact differences
+        const dfl wx = df_mul(w, vx), wy = df_mul(w, vy);
+        acc[0] = df_add(acc[0], df_mul(wx, vx));
+        acc[1] = df_add(acc[1], df_mul(wx, vy));
+        acc[2] = df_add(acc[2], wx);
+        acc[3] = df_add(acc[3], df_mul(wy, vy));
+        acc[4] = df_add(acc[4], wy);
+        acc[5] = df_add(acc[5], w);
+        acc[6] = df_add(acc[6], df_mul(wx, ft.x));
+        acc[7] = df_add(acc[7], df_mul(wy, ft.x));
+        acc[8] = df_add(acc[8], df_mul(w, ft.x));
+        acc[9] = df_add(acc[9], df_mul(wx, ft.y));
+        acc[10] = df_add(acc[10], df_mul(wy, ft.y));
+        acc[11] = df_add(acc[11], df_mul(w, ft.y));
     }
+    double accd[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) accd[i] = (double)acc[i].hi + (double)acc[i].lo;
     double tot[12];
-    warp_sum12(acc, tot);
+    warp_sum12(accd, tot);
     if (lane != 0) return;
     const double m00 = tot[0], m01 = tot[1], m02 = tot[2], m11 = tot[3], m12 = tot[4], m22 = tot[5];
     const double u0 = tot[6], u1 = tot[7], u2 = tot[8], v0 = tot[9], v1 = tot[10], v2 = tot[11];
