@@ -5,7 +5,8 @@
 // detection launch over every frame 1 (per distinct window size), one pyramid
 // launch over all 2 x pairs frames, and one tracking launch over every point of
 // the chunk (one lane group per point, blocks of eight points, so uneven pairs
-// and iteration counts balance through the block scheduler). Descriptors travel
+// and iteration counts balance through the block scheduler). In a captured graph
+// detection runs on a forked branch beside the pyramids. Descriptors travel
 // as kernel parameters, so the sequence needs no host-to-device copy and can be
 // captured into a CUDA graph; with use_graph = 1 the library captures it once per
 // distinct argument set and replays the instantiated graph afterwards.
@@ -51,12 +52,27 @@ size_t plan(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p, PairPl
     return off;
 }
 
+// Optional fork of detection onto a second stream (used while capturing a graph):
+// detection and the pyramids read the frames only, so they become parallel graph
+// branches that join before tracking.
+struct Fork {
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
 int enqueue(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p, const PairPlan* plans, char* ws,
-            int stages, cudaStream_t stream)
+            int stages, cudaStream_t stream, const Fork& fk = Fork())
 {
     for (int c0 = 0; c0 < n_pairs; c0 += dgf::kMaxBatchPairs) {
         const int cn = n_pairs - c0 < dgf::kMaxBatchPairs ? n_pairs - c0 : dgf::kMaxBatchPairs;
-        // detection, one launch per distinct window size
+        // detection, one launch per distinct window size (on the side stream when forked)
+        const bool forked = fk.side && (stages & DGF_STAGE_DETECT) && (stages & DGF_STAGE_PYRAMID);
+        cudaStream_t ds = stream;
+        if (forked) {
+            if (cudaEventRecord(fk.fork, stream) != cudaSuccess || cudaStreamWaitEvent(fk.side, fk.fork, 0) != cudaSuccess)
+                return DGF_ERR_CUDA;
+            ds = fk.side;
+        }
         bool done[dgf::kMaxBatchPairs] = {};
         for (int i = 0; i < cn && (stages & DGF_STAGE_DETECT); ++i) {
             if (done[i]) continue;
@@ -79,10 +95,11 @@ int enqueue(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p, const 
                 J.sums = nullptr;
             }
             if (d.n_jobs) {
-                const int rc = dgf::launch_detect(d, stream);
+                const int rc = dgf::launch_detect(d, ds);
                 if (rc != DGF_OK) return rc;
             }
         }
+        if (forked && cudaEventRecord(fk.join, fk.side) != cudaSuccess) return DGF_ERR_CUDA;
         // pyramids of both frames of every pair
         dgf::PyrBatch y = {};
         y.levels = p->levels;
@@ -94,6 +111,7 @@ int enqueue(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p, const 
         }
         int rc = (stages & DGF_STAGE_PYRAMID) ? dgf::launch_pyramids(y, p->storage, stream) : DGF_OK;
         if (rc != DGF_OK) return rc;
+        if (forked && cudaStreamWaitEvent(stream, fk.join, 0) != cudaSuccess) return DGF_ERR_CUDA;
         if (!(stages & DGF_STAGE_TRACK)) continue;
         // tracking of every point of the chunk
         dgf::TrackBatch t = {};
@@ -121,6 +139,25 @@ struct GraphCache {
 
 // Capture happens on a private non-blocking stream per device (the legacy default
 // stream cannot be captured); the instantiated graph then runs on the caller's.
+// The side stream and events of the fork, created once per device.
+Fork capture_fork(int dev)
+{
+    static Fork forks[64] = {};
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64) return Fork();
+    Fork& f = forks[dev];
+    if (!f.side) {
+        Fork t;
+        if (cudaStreamCreateWithFlags(&t.side, cudaStreamNonBlocking) != cudaSuccess) return Fork();
+        if (cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming) != cudaSuccess)
+            return Fork();
+        f = t;
+    }
+    return f;
+}
+
 cudaStream_t capture_stream(int dev)
 {
     static cudaStream_t streams[64] = {};
@@ -197,7 +234,7 @@ extern "C" int rlof_track_many(const dgf_pair* pairs, int n_pairs, const dgf_rlo
             delete[] plans;
             return DGF_ERR_CUDA;
         }
-        rc = enqueue(pairs, n_pairs, p, plans, ws, stages, cs);
+        rc = enqueue(pairs, n_pairs, p, plans, ws, stages, cs, capture_fork(dev));
         const cudaError_t e = cudaStreamEndCapture(cs, &g);
         delete[] plans;
         if (rc != DGF_OK || e != cudaSuccess) {
