@@ -509,6 +509,8 @@ class DenseFlow:
 
     def __init__(self, W: int, H: int, win: int, step: int, params: RlofParams, gm: GmParams | None = None,
                  epic: EpicParams | None = None, fb_max: float = 0.0, device: torch.device | str = "cuda"):
+        if gm is not None and fb_max > 0:
+            raise ValueError("choose the global-motion prior or the forward-backward filter")
         self.W, self.H, self.win, self.step = W, H, win, step
         self.params, self.gm, self.fb_max = params, gm, float(fb_max)
         self.epic = epic or EpicParams()
@@ -526,8 +528,6 @@ class DenseFlow:
                       if gm is not None else None)
         self.ws_fb = (torch.empty(max(int(load().dgf_fb_workspace(self.n)), 256), dtype=torch.uint8, device=dev)
                       if grad2 else None)
-        if gm is not None and grad2:
-            raise ValueError("choose the global-motion prior or the forward-backward filter")
 
     def run(self, frame1: torch.Tensor, frame2: torch.Tensor):
         prm = self.params

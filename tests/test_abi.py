@@ -216,6 +216,13 @@ def test_epic_host_checks_return_before_launch():
     assert call(dbg=half) == -1
 
 
+def test_dense_flow_rejects_prior_with_filter():
+    """DenseFlow runs the global-motion prior or the forward-backward filter, not both;
+    the check comes before any device allocation."""
+    with pytest.raises(ValueError):
+        dgf.DenseFlow(64, 48, 8, 4, dgf.RlofParams(), gm=dgf.GmParams(), fb_max=1.0, device="cpu")
+
+
 def test_adjoint_rejects_the_cross_support():
     """The tracking adjoint is defined for the square support only."""
     lib = dgf.load()
