@@ -54,6 +54,8 @@ struct TrackJob {
     int pt_begin;         // prefix count of points over the jobs of the launch
     int pt_stride;        // point k of the job is pts[k * pt_stride] (1: all points)
     const double* prior;  // global affine motion (6 doubles, device) or null
+    const uint8_t* gate;  // nullable: point k is tracked only if gate[k] is TRACKED or MAXITER;
+                          // otherwise its status is gate[k] and its flow 0
 };
 
 // Parameters and jobs of one tracking launch (a single pair or a batch).

@@ -4,8 +4,9 @@
 // round trip lands from the start.
 //
 // Four launches on the caller's stream: forward tracking, the end points p + f, the
-// backward tracking (frame 2's pyramid as the template), and the round-trip error
-// with the status update. The two element-wise kernels move 17 and 25 bytes per point.
+// backward tracking (frame 2's pyramid as the template; points the forward pass
+// lost are gated out), and the round-trip error with the status update. The two
+// element-wise kernels move 17 and 25 bytes per point.
 #include "common.cuh"
 #include "batch.cuh"
 
@@ -84,9 +85,11 @@ extern "C" int rlof_track_fb(const void* pyr1, const void* pyr2, size_t pyr_byte
     fb_endpoints_kernel<<<grid, kThreads, 0, stream>>>(reinterpret_cast<const float2*>(pts),
                                                        reinterpret_cast<const float2*>(flow), q, n);
     if ((rc = dgf::launch_status()) != DGF_OK) return rc;
+    // backward pass only for forward-tracked points (a point the forward pass lost
+    // has an infinite round-trip error whatever the backward pass finds)
     a.jobs[0] = dgf::TrackJob{static_cast<const char*>(pyr2), static_cast<const char*>(pyr1), W, H,
                               reinterpret_cast<const float*>(q), reinterpret_cast<float*>(bflow), bstatus, nullptr,
-                              nullptr, 0, 1, nullptr};
+                              nullptr, 0, 1, nullptr, status};
     if ((rc = dgf::launch_track(a, p, stream)) != DGF_OK) return rc;
     fb_finish_kernel<<<grid, kThreads, 0, stream>>>(reinterpret_cast<const float2*>(flow), status, bflow, bstatus,
                                                     fb_err, fb_max, n);

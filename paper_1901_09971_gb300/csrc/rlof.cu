@@ -694,6 +694,13 @@ __global__ void __launch_bounds__(block_threads<G>(), MINB) rlof_kernel(const __
     const float icb = a.inv_cb, hc_icb = a.hc * a.inv_cb;
     const dgf::TrackJob& J = a.jobs[find_job(a, gp)];
     const int pt = gp - J.pt_begin;
+    if (J.gate) {  // gated out: the whole group leaves (the kernel has no block barrier)
+        const uint8_t gs = J.gate[pt];
+        if (gs != DGF_TRACKED && gs != DGF_MAXITER) {
+            if (lane == 0) write_point(J, pt, gs, 0.f, 0.f, 0, 0.f, 0.f, MODEL == 4);
+            return;
+        }
+    }
     constexpr int NW = block_threads<G>() / 32;  // warps per block
     __shared__ WarpScratch s_ws[NW];
     WarpScratch& ws = s_ws[threadIdx.x >> 5];
