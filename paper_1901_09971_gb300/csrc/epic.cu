@@ -25,10 +25,10 @@
 //      (every frontier seed within its smallest incoming link of the frontier
 //      minimum is final, so about 14 steps settle the 128 nearest instead of 128
 //      pops), a hash of discovered seeds in shared memory, then sorts the settled
-//      (distance, index) keys and fits the weighted affine model to the first k in
-//      FP64. A search that outgrows the hash (512 seeds; 1024 for k > 160) or the
-//      sort buffer (256; 512) is queued and redone by a retry kernel with room for
-//      8192;
+//      (distance, index) keys and fits the weighted affine model to the first k
+//      (double-float sums, FP64 solve). A search that outgrows the hash (384 seeds;
+//      1024 for k > 160) or the sort buffer (256; 512) is queued and redone by a
+//      retry kernel with room for 8192;
 //   10. dense flow: every pixel evaluates its seed's model.
 #include <math.h>
 
@@ -382,8 +382,7 @@ struct KnnArgs {
 // as a list of FCAP hash slots, and the settled keys (SCAP, later sorted in place).
 template <int HCAP, int FCAP, int SCAP>
 struct KnnLayout {
-    static_assert((HCAP & (HCAP - 1)) == 0 && (SCAP & (SCAP - 1)) == 0 && HCAP <= 32768, "sizes");
-    static constexpr int hash_bits = __builtin_ctz(HCAP);
+    static_assert(HCAP % 32 == 0 && (SCAP & (SCAP - 1)) == 0 && HCAP <= 32768, "sizes");
     static constexpr size_t o_hdist = (size_t)HCAP * 4;
     static constexpr size_t o_sort = o_hdist + (size_t)HCAP * 8;
     static constexpr size_t o_minin = o_sort + (size_t)SCAP * 8;
@@ -394,8 +393,9 @@ struct KnnLayout {
 };
 
 // The fast layouts hold every search of the benchmark scenes (at k = 128 at most
-// about 250 discovered and 171 settled seeds; larger k takes the larger one); a
-// search that outgrows them is redone by the retry kernel with room for 8192.
+// about 250 discovered and 171 settled seeds, in a 384-slot hash; larger k takes
+// the larger one); a search that outgrows them is redone by the retry kernel with
+// room for 8192.
 constexpr int kFastWarps = 4, kSmallK = 160;
 constexpr int kBigH = 8192, kBigF = 8192, kBigS = 8192, kRetryBlocks = 152;
 constexpr int kRetry = 16;  // search status: capacity exceeded, redo with the large layout
@@ -568,7 +568,10 @@ __device__ int knn_search(const KnnArgs& a, int s, unsigned char* base, int& cnt
     unsigned char* hst = base + Lay::o_state;
     int* fcount = reinterpret_cast<int*>(base + Lay::o_count);  // frontier list length
     const int lane = threadIdx.x & 31;
-    auto slot_of = [](int t) { return (int)(((unsigned)t * 0x9E3779B1u) >> (32 - Lay::hash_bits)); };
+    // multiplicative hash scaled onto [0, HCAP) (HCAP need not be a power of two)
+    auto slot_of = [](int t) {
+        return (int)(((unsigned long long)((unsigned)t * 0x9E3779B1u) * (unsigned)HCAP) >> 32);
+    };
 
     for (int j = lane; j < HCAP; j += 32) {
         hkey[j] = -1;
@@ -696,7 +699,7 @@ __device__ int knn_search(const KnnArgs& a, int s, unsigned char* base, int& cnt
                             break;
                         }
                     }
-                    h = (h + 1) & (HCAP - 1);
+                    h = h + 1 == HCAP ? 0 : h + 1;
                 }
                 if (hs < 0) {
                     st |= kRetry;
@@ -1042,9 +1045,9 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
         a.a_per_unit = p->a / (2.0 * p->cost_base);
         a.min_spread2 = p->min_spread * p->min_spread;
         const bool small = p->k <= kSmallK;
-        auto fast = small ? epic_knn_fit_kernel<512, 256, 256> : epic_knn_fit_kernel<1024, 512, 512>;
+        auto fast = small ? epic_knn_fit_kernel<384, 256, 256> : epic_knn_fit_kernel<1024, 512, 512>;
         const size_t smem_fast =
-            (small ? KnnLayout<512, 256, 256>::bytes : KnnLayout<1024, 512, 512>::bytes) * kFastWarps;
+            (small ? KnnLayout<384, 256, 256>::bytes : KnnLayout<1024, 512, 512>::bytes) * kFastWarps;
         const size_t smem_big = KnnLayout<kBigH, kBigF, kBigS>::bytes;
         if (cudaFuncSetAttribute(fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fast) != cudaSuccess ||
             cudaFuncSetAttribute(epic_knn_retry_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_big) !=
