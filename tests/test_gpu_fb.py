@@ -29,13 +29,13 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def run_fb(dgf, I1, I2, pts, levels, radius, fb_max, model=4):
+def run_fb(dgf, I1, I2, pts, levels, radius, fb_max, model=4, storage=0):
     """GPU filter; also returns the backward pass's statuses from the workspace."""
     H, W = I1.shape
     n = len(pts)
-    prm = dgf.RlofParams(levels=levels, radius=radius, model=model)
-    p1 = dgf.build_pyramid(to_dev(I1), levels, 0, True)
-    p2 = dgf.build_pyramid(to_dev(I2), levels, 0, True)
+    prm = dgf.RlofParams(levels=levels, radius=radius, model=model, storage=storage)
+    p1 = dgf.build_pyramid(to_dev(I1), levels, storage, True)
+    p2 = dgf.build_pyramid(to_dev(I2), levels, storage, True)
     ws = torch.empty(int(dgf.load().dgf_fb_workspace(n)), dtype=torch.uint8, device="cuda")
     f, s, e = dgf.track_fb(p1, p2, W, H, to_dev(pts.astype(np.float32)), prm, fb_max, workspace=ws)
     torch.cuda.synchronize()
@@ -97,3 +97,21 @@ def test_fb_identical_frames_zero_error(dgf):
     fg, sg, eg, _ = run_fb(dgf, I1, I1, pts, 3, 4, 1.0)
     tr = (sg == oracle.TRACKED) | (sg == oracle.MAXITER)
     assert tr.mean() > 0.9 and np.all(eg[tr] == 0.0) and np.all(fg[tr] == 0.0)
+
+
+def test_fb_fp16_storage(dgf):
+    """FP16 pyramid storage: the filter's statuses stay close to the FP64 oracle's and
+    the occluding patch is still rejected."""
+    I1, I2 = occlusion_pair()
+    pts, _, _ = oracle.degraf_detect(I1, 8, 8, 4)
+    pts = pts.astype(np.float32).astype(np.float64)
+    fg, sg, eg, _ = run_fb(dgf, I1, I2, pts, 3, 4, 1.0, storage=dgf.F16)
+    _, so, _ = oracle.rlof_track_fb(I1, I2, pts, PRM, 1.0)
+    q = pts + np.array(T)
+    x0, y0, x1, y1 = PATCH
+    on_patch = (q[:, 0] >= x0 - 1) & (q[:, 0] < x1 + 1) & (q[:, 1] >= y0 - 1) & (q[:, 1] < y1 + 1)
+    fwd = np.isin(sg, [oracle.TRACKED, oracle.MAXITER, oracle.FB_REJECTED])
+    agree = np.mean(sg == so)
+    print(f"fp16 storage: status agree {agree:.4f}, patch rejected {np.mean(sg[fwd & on_patch] == oracle.FB_REJECTED):.3f}")
+    assert agree >= 0.97
+    assert np.mean(sg[fwd & on_patch] == oracle.FB_REJECTED) >= 0.95

@@ -40,8 +40,8 @@ def bars(fg, sg, fo, so, agree_min=0.99, within_min=0.999):
 
 def run_gm(dgf, p, pts32, prm, gm):
     pyr_levels = prm.levels + gm.extra_levels
-    p1 = dgf.build_pyramid(to_dev(p.I1), pyr_levels, 0, True)
-    p2 = dgf.build_pyramid(to_dev(p.I2), pyr_levels, 0, False)
+    p1 = dgf.build_pyramid(to_dev(p.I1), pyr_levels, prm.storage, True)
+    p2 = dgf.build_pyramid(to_dev(p.I2), pyr_levels, prm.storage, False)
     n = pts32.shape[0]
     ws = torch.zeros(dgf.gm_workspace_bytes(n, gm), dtype=torch.uint8, device="cuda")
     flow, status, a, made = dgf.track_gm(p1, p2, p.W, p.H, pyr_levels, to_dev(pts32), prm, gm, workspace=ws)
@@ -150,3 +150,29 @@ def test_gm_with_cross_support_driving_scene(dgf):
     oprm = oracle.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4, cross_tau=tau)
     fo, so, _, _ = oracle.rlof_track(p.I1, p.I2, pts64, oprm, init_flow=oracle.gm_prior_flow(a, pts64))
     print("gm + cross", bars(fg, sg, fo, so, agree_min=0.98, within_min=0.995))
+
+
+def test_gm_fp16_storage(dgf):
+    """FP16 pyramid storage with the prior on the 256x128 pair: the fitted motion is
+    within 0.01 px of the FP32-storage fit and the main pass stays close to the
+    oracle run from the same prior."""
+    p = synth.make_pair(1)
+    pts, _, _ = oracle.degraf_detect(p.I1, p.win, p.win, p.step)
+    pts32 = pts.astype(np.float32)
+    pts64 = pts32.astype(np.float64)
+    gm = dgf.GmParams(extra_levels=1)
+    res = {}
+    for storage in (dgf.F32, dgf.F16):
+        prm = dgf.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4, storage=storage)
+        res[storage] = run_gm(dgf, p, pts32, prm, gm)
+    a32, a16 = res[dgf.F32][2], res[dgf.F16][2]
+    d = np.abs(oracle.gm_prior_flow(a16, pts64) - oracle.gm_prior_flow(a32, pts64)).max()
+    print(f"prior difference FP16 vs FP32 storage: {d:.2e} px")
+    assert res[dgf.F16][3] == 1 and d < 0.01
+    fg, sg = res[dgf.F16][0], res[dgf.F16][1]
+    oprm = oracle.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4)
+    fo, so, _, _ = oracle.rlof_track(p.I1, p.I2, pts64, oprm, init_flow=oracle.gm_prior_flow(a16, pts64))
+    both = (sg == oracle.TRACKED) & (so == oracle.TRACKED)
+    e = np.hypot(*(fg.astype(np.float64) - fo).T)[both]
+    print(f"fp16 main pass: status agree {np.mean(sg == so):.4f}, median EPE vs oracle {np.median(e):.2e} px")
+    assert np.mean(sg == so) >= 0.97 and np.median(e) < 0.05
