@@ -34,10 +34,22 @@ METRIC = "tracked points/s and frame pairs/s at 1242x375; % HBM roofline; EPE vs
 WORKLOAD = dict(workload="driving-scene pair 1242x375: DeGraF w=7 step=3 (50676 pts) + RLOF "
                 "5 levels 11x11 max 30 iters gain/offset model, FP32",
                 W=1242, H=375, win=7, step=3, levels=5, radius=5, max_iter=30, model=4)
-# FP32 lanes x 2 flop x SMs at the maximum SM clock (GB300: 152 SMs, 128 FP32 lanes each)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
-HBM_PEAK_GBS = 6786.9  # measured STREAM-style copy on the GB300s
+
+
+def _measured_peaks():
+    """HBM bandwidth and maximum SM clock measured on the GB300s
+    (MEASURED_PEAKS.json), else the stated fallback (6.8 TB/s, 2070 MHz)."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(rec["hbm_gbs"]), float(rec.get("sm_max_mhz", 2070.0)), "measured (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError, TypeError):
+        return 6800.0, 2070.0, "fallback (no MEASURED_PEAKS.json)"
+
+
+HBM_PEAK_GBS, SM_MAX_MHZ, PEAK_SOURCE = _measured_peaks()
+# FP32 lanes x 2 flop x SMs at the maximum SM clock (GB300: 152 SMs, 128 FP32 lanes each)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
 def flops_model(radius: int, model: int):
@@ -166,7 +178,8 @@ def run_batched(dgf, torch, dev, reps: int = 10):
             "pairs_per_s": 64 / (t_all / 1e3),
             "autotune": {"lanes_per_point": tuned["lanes"], "ms_per_batch_by_lanes": tuned["ms"]},
             "detect_pyramid": {"ms": t_dp, "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
-                               "frac_of_measured_hbm": gbs / HBM_PEAK_GBS}}
+                               "frac_of_measured_hbm": gbs / HBM_PEAK_GBS, "peak_gbs": HBM_PEAK_GBS,
+                               "peak_source": PEAK_SOURCE}}
 
 
 def _timed(torch, dev, fn, reps, flush):
@@ -614,7 +627,8 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
                 "tracked_fraction": float(np.mean((status == 0) | (status == 4))),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": achieved / FP32_PEAK_TFLOPS, "traffic": kernel_traffic(),
-                             "peak_basis": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max clock)",
+                             "peak_basis": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz (max clock, "
+                                           f"{PEAK_SOURCE})",
                              "kernel": "rlof_kernel", "flops_per_launch": flops},
                 "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": 2 * W * H,
                         "d2h_bytes_per_step": n_pts * (8 + 8 + 1)},
