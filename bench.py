@@ -238,6 +238,34 @@ def run_adjoint(dgf, torch, dev, reps: int = 5):
             "ms_per_8_pairs": t, "pairs_per_s": 8 / (t / 1e3)}
 
 
+def hbm_context(W: int, H: int, n: int, ms_per_step: float):
+    """The whole step's HBM fraction under two byte models, reported beside the FP32
+    fraction of tracking (the step is ALU-bound, so both are small): I/O only (both
+    frames in; points, flow and status out) and with the pyramid materialised (4
+    FP32 planes over the levels written once and read once, the points re-read)."""
+    px = sum((W >> l) * (H >> l) for l in range(WORKLOAD["levels"]))
+    io = 2 * W * H + n * (8 + 8 + 1)
+    mat = io + 2 * 4 * 4 * px + 8 * n
+    gbs = lambda b: b / (ms_per_step / 1e3) / 1e9
+    return {"io_only_bytes": io, "materialised_bytes": mat, "io_only_frac": gbs(io) / HBM_PEAK_GBS,
+            "materialised_frac": gbs(mat) / HBM_PEAK_GBS, "peak_gbs": HBM_PEAK_GBS,
+            "note": "tracking is FP32-ALU bound (roofline above); the HBM traffic of a step is a few MB"}
+
+
+def run_small_pair(dgf, torch, dev, reps: int = 50):
+    """The 256x128 translation pair (window 8, step 4, 3 levels, 9x9): one
+    PairTracker step (detection, both pyramids, tracking), device frames."""
+    p = synth.make_pair(1)
+    prm = dgf.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4)
+    tr = dgf.PairTracker(p.W, p.H, p.win, p.step, prm, dev)
+    f1, f2 = torch.from_numpy(p.I1).to(dev), torch.from_numpy(p.I2).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    t = _timed(torch, dev, lambda: tr.run(f1, f2), reps, flush)
+    n = int(tr.pts.shape[0])
+    return {"workload": f"256x128 translation pair, window 8, step 4 ({n} points), 3 levels, 9x9, model 4, FP32",
+            "ms_per_step": t, "points_per_s": n / (t / 1e3), "pairs_per_s": 1e3 / t}
+
+
 def run_gm_prior(dgf, torch, dev, pair, reps: int = 20):
     """The global-motion prior on the 1242x375 pair: plain tracking against
     rlof_track_gm (sparse first pass every 4th point, affine fit, main pass), both
@@ -634,7 +662,9 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
                         "d2h_bytes_per_step": n_pts * (8 + 8 + 1)},
                 "gpu_launches": 4 * args.steps,
                 "clocks": clocks.summary()}
+        line["hbm_context"] = hbm_context(W, H, n_pts, 1e3 * total_s / args.steps)
         if not args.no_batched:
+            line["small_pair"] = run_small_pair(dgf, torch, dev)
             line["batched"] = run_batched(dgf, torch, dev)
             line["fp16_storage"] = run_fp16(dgf, torch, dev)
             line["adjoint"] = run_adjoint(dgf, torch, dev)
