@@ -60,7 +60,7 @@ def assert_parity(g, o, dense_tol=1e-4, model_tol=1e-9):
     assert err.max() <= dense_tol
 
 
-@pytest.mark.parametrize("seed,k", [(0, 5), (1, 12), (2, 200)])
+@pytest.mark.parametrize("seed,k", [(0, 5), (1, 12), (2, 200), (3, 1)])
 def test_small_random_matches_exact(dgf, seed, k):
     W, H = 41, 29
     img = textured(W, H, seed)
