@@ -48,7 +48,7 @@ constexpr int kThreads = 256;
 constexpr long long kNoLink = 0xffffffffll;  // min link weight of a seed without links
 
 // Device status bits (any of them makes the call return DGF_ERR_DEVICE).
-enum : int { kErrFrontier = 1, kErrHash = 2, kErrFill = 4, kErrRange = 8 };
+enum : int { kErrFrontier = 1, kErrFill = 4, kErrRange = 8 };
 
 __device__ __forceinline__ bool is_tracked(uint8_t s) { return s == DGF_TRACKED || s == DGF_MAXITER; }
 
