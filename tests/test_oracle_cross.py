@@ -41,6 +41,21 @@ def test_cross_inside_a_region_is_its_intersection_with_the_window():
         np.testing.assert_array_equal(m, expect, err_msg=f"centre {(cx, cy)}")
 
 
+def test_row_arms_are_measured_from_their_own_arm_pixel():
+    """Centre column 100 + 20 (y - cy), the rest of each row 20 above its centre-column
+    pixel; tau 25. The vertical arm keeps rows cy - 1 .. cy + 1 (|20| <= 25, |40| > 25);
+    each of those rows differs from its own arm pixel by 20 and is kept whole, although
+    rows cy +- 1 lie 40 or 0 away from the centre pixel."""
+    W, H, cx, cy = 21, 21, 10, 10
+    y = np.arange(H)[:, None].repeat(W, 1).astype(np.float64)
+    img = 100.0 + 20.0 * (y - cy)
+    img[:, np.arange(W) != cx] += 20.0
+    m = oracle.cross_mask(img, cx, cy, R, 25.0)
+    expect = np.zeros((2 * R + 1, 2 * R + 1), np.uint8)
+    expect[R - 1:R + 2, :] = 1
+    np.testing.assert_array_equal(m, expect)
+
+
 def test_uniform_image_keeps_the_whole_window_and_the_border_clamps():
     img = np.full((40, 50), 77, np.uint8)
     for c in [(25, 20), (0, 0), (49, 39)]:

@@ -55,6 +55,29 @@ def test_fit_rejects_gross_outliers_where_least_squares_fails():
     assert err < 1e-6  # outliers end with weight exactly 0
 
 
+def test_one_reweighting_is_tukey_weighted_least_squares():
+    """Two IRLS iterations: a least-squares fit, then a weighted least-squares fit
+    with Tukey biweights (1 - (e / c)^2)^2 of its residuals e at c = c0 (zero beyond);
+    both steps recomputed here with numpy's least squares."""
+    pts = grid_points(step=24)
+    rng = np.random.default_rng(5)
+    flow = affine_flow(A_TRUE, pts) + rng.normal(0, 3.0, (len(pts), 2))
+    flow[rng.choice(len(pts), 40, replace=False)] += rng.uniform(-60, 60, (40, 2))
+    status = np.zeros(len(pts), np.uint8)
+    c0 = 16.0
+    a, made = oracle.gm_fit_affine(pts, flow, status, iters=2, c0=c0, c_min=1.0)
+    assert made
+    X = np.c_[pts, np.ones(len(pts))]
+    Q = pts + flow
+    a0 = np.linalg.lstsq(X, Q, rcond=None)[0]  # [3, 2]: columns are the x and y rows
+    e = np.hypot(*(X @ a0 - Q).T)
+    w = np.where(e < c0, (1 - (e / c0) ** 2) ** 2, 0.0)
+    a1 = np.linalg.lstsq(X * np.sqrt(w)[:, None], Q * np.sqrt(w)[:, None], rcond=None)[0]
+    expect = np.r_[a1[:, 0], a1[:, 1]]
+    assert 0 < np.mean(w > 0) < 1
+    np.testing.assert_allclose(a, expect, rtol=0, atol=1e-8)
+
+
 def test_fit_degenerate_cases_fall_back_to_identity():
     ident = np.array([1, 0, 0, 0, 1, 0], float)
     pts = grid_points()[:2]
