@@ -17,6 +17,7 @@ import test_oracle_cross
 import test_oracle_degraf
 import test_oracle_epic
 import test_oracle_gm
+import test_oracle_pyramid
 import test_oracle_rlof
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "degraf_oracle.c")
@@ -26,6 +27,15 @@ MUTANTS = {
     "detection swaps the negative centroid's coordinates": (
         "double cx = use_neg ? (double)Xn / (double)Sn : (double)X / (double)S;",
         "double cx = use_neg ? (double)Yn / (double)Sn : (double)X / (double)S;", [test_oracle_degraf]),
+    "pyramid mean weighs one pixel twice": (
+        "I[(long)y * Wl + x] = ((a + b) + (c + d)) * 0.25;", "I[(long)y * Wl + x] = ((a + a) + (c + d)) * 0.25;",
+        [test_oracle_pyramid]),
+    "pyramid y-gradient uses the x kernel": (
+        "gy += sobel_x[dx + 1][dy + 1] * v; /* transposed kernel */",
+        "gy += sobel_x[dy + 1][dx + 1] * v; /* transposed kernel */", [test_oracle_pyramid]),
+    "tracking keeps points with too little gradient": (
+        "if (lam_min / n_keep < prm->min_eig) { status = OR_SMALL_EIG; break; }",
+        "if (lam_min / n_keep < -prm->min_eig) { status = OR_SMALL_EIG; break; }", [test_oracle_rlof]),
     "tracking residual adds the offset": (
         "res = J - (1 + m) * T[s] - c;", "res = J - (1 + m) * T[s] + c;", [test_oracle_rlof]),
     "Hampel drops the clipping between its first two knots": (
