@@ -554,6 +554,10 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
         if rank == 0:
             print(json.dumps({"batched": run_batched(dgf, torch, dev)}), flush=True)
         return
+    if args.adjoint_only:  # profiling aid: the adjoint section alone, no bench line
+        if rank == 0:
+            print(json.dumps({"adjoint": run_adjoint(dgf, torch, dev, reps=args.steps)}), flush=True)
+        return
     if args.epic_only:  # profiling aid: the EPIC section alone, no bench line
         if rank == 0:
             print(json.dumps({"epic": run_epic(dgf, torch, dev, synth.make_pair(2), reps=args.steps)}), flush=True)
@@ -696,6 +700,8 @@ def main():
     ap.add_argument("--lanes", type=int, default=0, help="lanes per tracked point (0 = automatic)")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the 64-pair batch section and print its JSON (for profiling)")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint section (--steps timed runs) and print its JSON (for profiling)")
     ap.add_argument("--epic-only", action="store_true",
                     help="run only the EPIC section (--steps timed calls) and print its JSON (for profiling)")
     args = ap.parse_args()
