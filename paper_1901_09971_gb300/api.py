@@ -32,6 +32,55 @@ def _frame(frame: torch.Tensor):
     return W, H, frame.stride(0)
 
 
+def _nbytes(t: torch.Tensor) -> int:
+    return t.numel() * t.element_size()
+
+
+def _points(pts: torch.Tensor, name: str = "pts") -> int:
+    """Number of points of a contiguous float32 CUDA tensor [n, 2]."""
+    if pts.dtype != torch.float32 or pts.dim() != 2 or pts.shape[1] != 2 or not pts.is_contiguous() or not pts.is_cuda:
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor [n, 2]")
+    return pts.shape[0]
+
+
+def _buffer(t, name: str, dtype, shape, device):
+    """Checks a caller's buffer (the kernels write or read every element of it); None passes."""
+    if t is not None and (t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous()
+                          or t.device != device):
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor {list(shape)} on {device}")
+    return t
+
+
+def _bytes_buffer(t: torch.Tensor, name: str, device) -> torch.Tensor:
+    """A byte buffer (pyramid or workspace): contiguous uint8 on the device."""
+    if t.dtype != torch.uint8 or not t.is_contiguous() or t.device != device:
+        raise ValueError(f"{name} must be a contiguous uint8 tensor on {device}")
+    return t
+
+
+def _grad_plane(g: torch.Tensor, name: str, W: int, H: int, device) -> None:
+    """A float32 [H, W] gradient image with unit column stride (rows may be padded)."""
+    if (g.dtype != torch.float32 or tuple(g.shape) != (H, W) or g.stride(1) != 1 or g.stride(0) < W
+            or g.device != device):
+        raise ValueError(f"{name} must be a float32 tensor [{H}, {W}] with contiguous rows on {device}")
+
+
+def _pyramids(pyr1, pyr2, W: int, H: int, levels: int, storage: int, device, grad2: bool = False):
+    """The tracker reads frame 1's pyramid at the offsets of a `levels`-level pyramid with
+    gradients, and frame 2's intensity planes (a prefix of any pyramid with at least
+    `levels` levels; with grad2, frame 2's gradients too, at the offsets of exactly
+    `levels` levels): check both buffers against those layouts."""
+    _bytes_buffer(pyr1, "pyr1", device)
+    _bytes_buffer(pyr2, "pyr2", device)
+    need1 = pyramid_bytes(W, H, levels, storage, True)
+    need2 = pyramid_bytes(W, H, levels, storage, grad2)
+    if need1 and pyr1.numel() != need1:  # 0: invalid sizes, which the library reports itself
+        raise ValueError(f"pyr1 must be a {levels}-level pyramid with gradients ({need1} bytes)")
+    if need2 and (pyr2.numel() != need2 if grad2 else pyr2.numel() < need2):
+        raise ValueError(f"pyr2 must hold a {levels}-level pyramid{' with gradients' if grad2 else ''} "
+                         f"({need2} bytes)")
+
+
 @dataclasses.dataclass
 class RlofParams:
     """Tracking parameters (mirror of dgf_rlof_params)."""
@@ -102,7 +151,8 @@ def detect(frame: torch.Tensor, win: int, step: int, win_h: int | None = None,
     W, H, pitch = _frame(frame)
     wh = win if win_h is None else win_h
     n = degraf_count(W, H, win, step, wh)
-    pts = out if out is not None else torch.empty((n, 2), dtype=torch.float32, device=frame.device)
+    pts = (_buffer(out, "out", torch.float32, (n, 2), frame.device) if out is not None
+           else torch.empty((n, 2), dtype=torch.float32, device=frame.device))
     sums = torch.empty((n, 4), dtype=torch.int32, device=frame.device) if with_sums else None
     check("degraf_detect", load().degraf_detect(_ptr(frame), W, H, pitch, win, wh, step, _ptr(pts),
                                                 _ptr(sums), _stream()))
@@ -128,7 +178,8 @@ def build_pyramid(frame: torch.Tensor, levels: int, storage: int = F32, with_gra
     """Pyramid buffer (uint8 tensor laid out as pyramid_layout describes)."""
     W, H, pitch = _frame(frame)
     nbytes = pyramid_bytes(W, H, levels, storage, with_grad)
-    buf = out if out is not None else torch.empty(nbytes, dtype=torch.uint8, device=frame.device)
+    buf = _bytes_buffer(out, "out", frame.device) if out is not None else torch.empty(
+        nbytes, dtype=torch.uint8, device=frame.device)
     check("pyramid_build", load().pyramid_build(_ptr(frame), W, H, pitch, levels, storage,
                                                 int(with_grad), _ptr(buf), buf.numel(), _stream()))
     return buf
@@ -159,11 +210,12 @@ def set_lanes(lanes: int) -> int:
 
 def track(pyr1: torch.Tensor, pyr2: torch.Tensor, W: int, H: int, pts: torch.Tensor, params: RlofParams,
           with_iters: bool = False, with_illum: bool = False, out=None):
-    """RLOF tracking of pts [n, 2] (float32, CUDA): returns flow, status[, iters][, illum]."""
-    if pts.dtype != torch.float32 or not pts.is_contiguous():
-        raise ValueError("pts must be a contiguous float32 tensor [n, 2]")
-    n = pts.shape[0]
+    """RLOF tracking of pts [n, 2] (float32, CUDA): returns flow, status[, iters][, illum].
+    pyr1 is frame 1's pyramid with gradients and params.levels levels; out = (flow,
+    status, iters or None, illum or None) are caller buffers."""
+    n = _points(pts)
     dev = pts.device
+    _pyramids(pyr1, pyr2, W, H, params.levels, params.storage, dev)
     if out is None:
         flow = torch.empty((n, 2), dtype=torch.float32, device=dev)
         status = torch.empty(n, dtype=torch.uint8, device=dev)
@@ -171,6 +223,10 @@ def track(pyr1: torch.Tensor, pyr2: torch.Tensor, W: int, H: int, pts: torch.Ten
         illum = torch.empty((n, 2), dtype=torch.float32, device=dev) if with_illum else None
     else:
         flow, status, iters, illum = out
+        _buffer(flow, "flow", torch.float32, (n, 2), dev)
+        _buffer(status, "status", torch.uint8, (n,), dev)
+        _buffer(iters, "iters", torch.uint8, (n,), dev)
+        _buffer(illum, "illum", torch.float32, (n, 2), dev)
     prm = params.c()
     check("rlof_track", load().rlof_track(_ptr(pyr1), _ptr(pyr2), W, H, _ptr(pts), n, ctypes.byref(prm),
                                           _ptr(flow), _ptr(status), _ptr(iters), _ptr(illum), _stream()))
@@ -194,10 +250,9 @@ def track_gm(pyr1: torch.Tensor, pyr2: torch.Tensor, W: int, H: int, pyr_levels:
     [, iters][, illum], then the fitted affine (float64 [6], device) and its flag
     (int32 [1], device; 1 = fitted)."""
     gm = gm or GmParams()
-    if pts.dtype != torch.float32 or not pts.is_contiguous():
-        raise ValueError("pts must be a contiguous float32 tensor [n, 2]")
-    n = pts.shape[0]
+    n = _points(pts)
     dev = pts.device
+    _pyramids(pyr1, pyr2, W, H, pyr_levels, params.storage, dev)
     flow = torch.empty((n, 2), dtype=torch.float32, device=dev)
     status = torch.empty(n, dtype=torch.uint8, device=dev)
     iters = torch.empty(n, dtype=torch.uint8, device=dev) if with_iters else None
@@ -205,6 +260,7 @@ def track_gm(pyr1: torch.Tensor, pyr2: torch.Tensor, W: int, H: int, pyr_levels:
     need = gm_workspace_bytes(n, gm)
     if workspace is None:
         workspace = torch.zeros(max(need, 256), dtype=torch.uint8, device=dev)
+    _bytes_buffer(workspace, "workspace", dev)
     prm, g = params.c(), gm.c()
     check("rlof_track_gm", load().rlof_track_gm(_ptr(pyr1), _ptr(pyr2), W, H, pyr_levels, _ptr(pts), n,
                                                 ctypes.byref(prm), ctypes.byref(g), _ptr(flow), _ptr(status),
@@ -225,16 +281,16 @@ def track_fb(pyr1: torch.Tensor, pyr2: torch.Tensor, W: int, H: int, pts: torch.
     """Forward-backward consistency filter (rlof_track_fb): both pyramids built with
     gradients. Returns flow, status (FB_REJECTED where the round-trip error exceeds
     fb_max > 0) and the round-trip error (float32 [n], +inf where a pass lost the point)."""
-    if pts.dtype != torch.float32 or not pts.is_contiguous():
-        raise ValueError("pts must be a contiguous float32 tensor [n, 2]")
-    n = pts.shape[0]
+    n = _points(pts)
     dev = pts.device
+    _pyramids(pyr1, pyr2, W, H, params.levels, params.storage, dev, grad2=True)
     flow = torch.empty((n, 2), dtype=torch.float32, device=dev)
     status = torch.empty(n, dtype=torch.uint8, device=dev)
     err = torch.empty(n, dtype=torch.float32, device=dev)
     if workspace is None:
         workspace = torch.empty(max(int(load().dgf_fb_workspace(n)), 256), dtype=torch.uint8, device=dev)
-    nbytes = min(pyr1.numel() * pyr1.element_size(), pyr2.numel() * pyr2.element_size())
+    _bytes_buffer(workspace, "workspace", dev)
+    nbytes = min(pyr1.numel(), pyr2.numel())
     prm = params.c()
     check("rlof_track_fb", load().rlof_track_fb(_ptr(pyr1), _ptr(pyr2), nbytes, W, H, _ptr(pts), n, ctypes.byref(prm),
                                                 float(fb_max), _ptr(flow), _ptr(status), _ptr(err), _ptr(workspace),
@@ -253,18 +309,16 @@ def epic_interpolate(frame: torch.Tensor, pts: torch.Tensor, flow: torch.Tensor,
     (epic_interpolate). With debug=True also returns a dict of the labels, geodesic
     distances, neighbourhoods, per-seed models and fit kinds."""
     W, H, pitch = _frame(frame)
-    for name, t in (("pts", pts), ("flow", flow)):
-        if t.dtype != torch.float32 or not t.is_contiguous():
-            raise ValueError(f"{name} must be a contiguous float32 tensor [n, 2]")
-    if status.dtype != torch.uint8 or not status.is_contiguous():
-        raise ValueError("status must be a contiguous uint8 tensor [n]")
-    n = pts.shape[0]
     dev = frame.device
-    dense = out if out is not None else torch.empty((H, W, 2), dtype=torch.float32, device=dev)
-    if dense.shape != (H, W, 2) or dense.dtype != torch.float32 or not dense.is_contiguous():
-        raise ValueError("out must be a contiguous float32 tensor [H, W, 2]")
+    n = _points(pts)
+    _buffer(pts, "pts", torch.float32, (n, 2), dev)
+    _buffer(flow, "flow", torch.float32, (n, 2), dev)
+    _buffer(status, "status", torch.uint8, (n,), dev)
+    dense = (_buffer(out, "out", torch.float32, (H, W, 2), dev) if out is not None
+             else torch.empty((H, W, 2), dtype=torch.float32, device=dev))
     if workspace is None:
         workspace = torch.empty(max(epic_workspace_bytes(W, H, n), 256), dtype=torch.uint8, device=dev)
+    _bytes_buffer(workspace, "workspace", dev)
     out = None
     dbg = None
     if debug:
@@ -290,9 +344,12 @@ def detect_backward(frame: torch.Tensor, win: int, step: int, grad_pts: torch.Te
     """Adds sum_k grad_pts[k] . d(point_k)/d(frame) into grad_img (float32 [H, W])."""
     W, H, pitch = _frame(frame)
     wh = win if win_h is None else win_h
+    n = degraf_count(W, H, win, step, wh)
     if grad_img is None:
         grad_img = torch.zeros((H, W), dtype=torch.float32, device=frame.device)
+    _grad_plane(grad_img, "grad_img", W, H, frame.device)
     grad_pts = grad_pts.contiguous().float()
+    _buffer(grad_pts, "grad_pts", torch.float32, (n, 2), frame.device)
     ws = torch.empty(int(load().dgf_degraf_backward_workspace(W, H, win, wh, step)), dtype=torch.uint8,
                      device=frame.device)
     check("degraf_detect_backward", load().degraf_detect_backward(
@@ -303,15 +360,26 @@ def detect_backward(frame: torch.Tensor, win: int, step: int, grad_pts: torch.Te
 
 def track_backward(pyr1, pyr2, W: int, H: int, pts, params: RlofParams, flow, illum, status, grad_flow,
                    grad_illum=None, grad_I1=None, grad_I2=None):
-    """Adds the implicit-function VJP of tracking into (grad_I1, grad_I2) float32 [H, W]."""
+    """Adds the implicit-function VJP of tracking into (grad_I1, grad_I2) float32 [H, W]
+    (rows of both planes equally far apart)."""
+    n = _points(pts)
     dev = pts.device
+    _pyramids(pyr1, pyr2, W, H, params.levels, params.storage, dev)
     if grad_I1 is None:
         grad_I1 = torch.zeros((H, W), dtype=torch.float32, device=dev)
     if grad_I2 is None:
         grad_I2 = torch.zeros((H, W), dtype=torch.float32, device=dev)
+    _grad_plane(grad_I1, "grad_I1", W, H, dev)
+    _grad_plane(grad_I2, "grad_I2", W, H, dev)
+    if grad_I1.stride(0) != grad_I2.stride(0):
+        raise ValueError("grad_I1 and grad_I2 rows must be equally far apart")
+    _buffer(flow, "flow", torch.float32, (n, 2), dev)
+    _buffer(illum, "illum", torch.float32, (n, 2), dev)
+    _buffer(status, "status", torch.uint8, (n,), dev)
     ws = torch.empty(int(load().dgf_rlof_backward_workspace(W, H)), dtype=torch.uint8, device=dev)
-    grad_flow = grad_flow.contiguous().float()
-    gi = grad_illum.contiguous().float() if grad_illum is not None else None
+    grad_flow = _buffer(grad_flow.contiguous().float(), "grad_flow", torch.float32, (n, 2), dev)
+    gi = (_buffer(grad_illum.contiguous().float(), "grad_illum", torch.float32, (n, 2), dev)
+          if grad_illum is not None else None)
     prm = params.c()
     check("rlof_track_backward", load().rlof_track_backward(
         _ptr(pyr1), _ptr(pyr2), W, H, _ptr(pts), pts.shape[0], ctypes.byref(prm), _ptr(flow), _ptr(illum),

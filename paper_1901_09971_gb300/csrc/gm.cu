@@ -5,7 +5,7 @@
 //
 // The fit is an IRLS loop of a few iterations, each two launches: 64 CTAs sum the
 // weighted normal equations of their points in FP64 (GB300's FP64 pipe is narrow,
-// so the sums are spread over the SMs) into per-CTA partials, then one warp adds the
+// so the sums are spread over the SMs) into per-CTA partials, then one thread adds the
 // partials in CTA order (deterministic) and solves the two 3 x 3 systems. The
 // state (affine, fitted flag, go-on flag) lives in the workspace, so no host round
 // trip separates the stages: the main pass reads the fitted parameters from device

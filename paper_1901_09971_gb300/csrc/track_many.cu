@@ -12,6 +12,7 @@
 // distinct argument set and replays the instantiated graph afterwards.
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <unordered_map>
 
 #include "batch.cuh"
@@ -131,10 +132,10 @@ int enqueue(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p, const 
     return DGF_OK;
 }
 
-// Instantiated graphs keyed by a hash of everything the launches bake in.
+// Instantiated graphs keyed by everything the launches bake in (graph_key).
 struct GraphCache {
     std::mutex mu;
-    std::unordered_map<uint64_t, cudaGraphExec_t> map;
+    std::unordered_map<std::string, cudaGraphExec_t> map;
 };
 
 // Capture happens on a private non-blocking stream per device (the legacy default
@@ -151,8 +152,11 @@ Fork capture_fork(int dev)
         Fork t;
         if (cudaStreamCreateWithFlags(&t.side, cudaStreamNonBlocking) != cudaSuccess) return Fork();
         if (cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming) != cudaSuccess)
-            return Fork();
+            cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming) != cudaSuccess) {
+            if (t.fork) cudaEventDestroy(t.fork);
+            cudaStreamDestroy(t.side);
+            return Fork();  // no fork: detection stays on the capture stream
+        }
         f = t;
     }
     return f;
@@ -173,11 +177,27 @@ GraphCache& cache()
     return *c;
 }
 
-uint64_t fnv1a(uint64_t h, const void* data, size_t n)
+// The exact argument set a captured graph bakes in, written out field by field (so
+// struct padding never enters it): a cache hit replays launches whose arguments all
+// equal the caller's.
+std::string graph_key(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p, const char* ws, int dev,
+                      int stages, int lanes)
 {
-    const unsigned char* b = static_cast<const unsigned char*>(data);
-    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ULL;
-    return h;
+    std::string k;
+    k.reserve((size_t)n_pairs * 68 + sizeof(*p) + 24);
+    const auto put = [&k](const void* v, size_t n) { k.append(static_cast<const char*>(v), n); };
+    for (int i = 0; i < n_pairs; ++i) {
+        const dgf_pair& P = pairs[i];
+        const void* ptrs[6] = {P.frame1, P.frame2, P.pts, P.flow, P.status, P.iters};
+        const int dims[5] = {P.W, P.H, P.pitch, P.win, P.step};
+        put(ptrs, sizeof(ptrs));
+        put(dims, sizeof(dims));
+    }
+    put(p, sizeof(*p));  // ints and floats only: no padding
+    put(&ws, sizeof(ws));
+    const int rest[3] = {dev, stages, lanes};
+    put(rest, sizeof(rest));
+    return k;
 }
 
 }  // namespace
@@ -215,14 +235,8 @@ extern "C" int rlof_track_many(const dgf_pair* pairs, int n_pairs, const dgf_rlo
     }
     int dev = 0;
     cudaGetDevice(&dev);
-    uint64_t key = 1469598103934665603ULL;
-    key = fnv1a(key, pairs, sizeof(dgf_pair) * (size_t)n_pairs);
-    key = fnv1a(key, p, sizeof(*p));
-    key = fnv1a(key, &ws, sizeof(ws));
-    key = fnv1a(key, &dev, sizeof(dev));
-    key = fnv1a(key, &stages, sizeof(stages));
-    const int lanes = dgf::lanes_setting();  // the lanes setting is baked in too
-    key = fnv1a(key, &lanes, sizeof(lanes));
+    const std::string key =
+        graph_key(pairs, n_pairs, p, ws, dev, stages, dgf::lanes_setting());  // the lanes setting is baked in too
     GraphCache& C = cache();
     std::lock_guard<std::mutex> lock(C.mu);
     auto it = C.map.find(key);
