@@ -13,4 +13,5 @@ from .pairs import (  # noqa: F401
     make_batch_specs,
     CONFIG_SIZES,
     render,
+    render_affine,
 )

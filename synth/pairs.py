@@ -80,6 +80,20 @@ class Texture:
             out += amp * (wy.T @ vals @ wx)
         return out
 
+    def raw_at(self, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+        """Texture value at the points (x[i], y[i]) (float64, unmapped); equal to
+        ``raw`` on grid points up to rounding."""
+        x = np.asarray(x, dtype=np.float64).ravel()
+        y = np.asarray(y, dtype=np.float64).ravel()
+        two_s2 = 2.0 * self.sigma[:, None] ** 2
+        out = self.amp @ np.exp(-(((x[None, :] - self.cx[:, None]) ** 2) + (y[None, :] - self.cy[:, None]) ** 2)
+                                / two_s2)
+        for spacing, amp, pad, vals in self.octaves:
+            wx = _lattice_weights(x, spacing, pad, vals.shape[1])
+            wy = _lattice_weights(y, spacing, pad, vals.shape[0])
+            out += amp * np.einsum("ip,ij,jp->p", wy, vals, wx)
+        return out
+
 
 def _quantise(v: np.ndarray) -> np.ndarray:
     """Round half to even and clip to uint8."""
@@ -263,3 +277,19 @@ def render(W: int, H: int, seed: int, shift=(0.0, 0.0)) -> np.ndarray:
     xs, ys = np.arange(W, dtype=np.float64), np.arange(H, dtype=np.float64)
     m = _Mapper(tex.raw(xs, ys))
     return m(tex.raw(xs - shift[0], ys - shift[1]))
+
+
+def render_affine(W: int, H: int, seed: int, A, c) -> np.ndarray:
+    """Frame 2 of an analytic affine motion of ``render(W, H, seed)``: the frame-1
+    point x moves to c + A (x - c), so the true flow at x is (A - I)(x - c). The
+    texture is evaluated at each pixel's exact source point A^-1 (x - c) + c (no
+    interpolation or rounding), with frame 1's intensity mapping."""
+    rng = _rng(seed)
+    tex = Texture(rng, W, H)
+    xs, ys = np.arange(W, dtype=np.float64), np.arange(H, dtype=np.float64)
+    m = _Mapper(tex.raw(xs, ys))
+    Ai = np.linalg.inv(np.asarray(A, dtype=np.float64))
+    Y, X = np.mgrid[0:H, 0:W].astype(np.float64)
+    sx = c[0] + Ai[0, 0] * (X - c[0]) + Ai[0, 1] * (Y - c[1])
+    sy = c[1] + Ai[1, 0] * (X - c[0]) + Ai[1, 1] * (Y - c[1])
+    return m(tex.raw_at(sx, sy).reshape(H, W))

@@ -40,6 +40,12 @@ MUTANTS = {
         "res = J - (1 + m) * T[s] - c;", "res = J - (1 + m) * T[s] + c;", [test_oracle_rlof]),
     "Hampel drops the clipping between its first two knots": (
         "if (ar <= b) return a * s;", "if (ar <= b) return r;", [test_oracle_rlof]),
+    "Hampel's descending part spans the wrong interval": (
+        "if (ar <= c) return a * s * (c - ar) / (c - b);", "if (ar <= c) return a * s * (c - ar) / (c - a);",
+        [test_oracle_rlof]),
+    "tracking template sampled half a pixel off in y": (
+        "T[s] = bilinear(A->I, A->W, A->H, plx + kx, ply + ky);",
+        "T[s] = bilinear(A->I, A->W, A->H, plx + kx, ply + ky + 0.5);", [test_oracle_rlof]),
     "cross rows measured from the centre pixel": (
         "while (lf < r && fabs(PIX(cx - lf - 1, cy + ky) - va) <= tau) ++lf;",
         "while (lf < r && fabs(PIX(cx - lf - 1, cy + ky) - vc) <= tau) ++lf;", [test_oracle_cross]),

@@ -192,3 +192,75 @@ def test_identical_frames_give_zero_flow(frame1):
     pts = interior_points()
     flow, st, it, illum = oracle.rlof_track(frame1, frame1, pts, oracle.RlofParams(levels=3, radius=5))
     assert np.all(st == oracle.TRACKED) and np.abs(flow).max() < 1e-12 and np.abs(illum).max() < 1e-12
+
+
+def test_affine_warp_recovered(frame1):
+    """Analytic affine motion about the frame centre (2% zoom, 1.2 degree rotation):
+    every point's flow is its centre's motion (A - I)(p - c) up to the bias of a
+    translation model over a deforming support, which is first order in A - I.
+    Bounds measured once: median 0.10 / 0.14 px, max 0.38 / 0.43 px (models 2 / 4)
+    at flows up to 1.32 px; halving A - I halves each point's error (median ratio
+    2.00). A swapped axis or a flipped sign leaves errors of the flow's own size."""
+    pts = interior_points()
+    c = np.array([W / 2, H / 2])
+
+    def errors(s, model):
+        th = np.deg2rad(1.2 * s)
+        A = (1 + 0.02 * s) * np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+        I2 = synth.render_affine(W, H, 5, A, c)
+        prm = oracle.RlofParams(levels=3, radius=4, model=model, eps=1e-8, max_iter=200)
+        flow, st, _, _ = oracle.rlof_track(frame1, I2, pts, prm)
+        assert np.all(st == oracle.TRACKED)
+        return np.hypot(*(flow - (pts - c) @ (A - np.eye(2)).T).T)
+
+    for model, med, top in ((2, 0.12, 0.45), (4, 0.16, 0.5)):
+        e1, e2 = errors(1.0, model), errors(0.5, model)
+        assert np.median(e1) < med and e1.max() < top
+        assert 1.9 < np.median(e1 / np.maximum(e2, 1e-9)) < 2.1
+
+
+def test_converged_state_is_a_fixed_point(frame1):
+    """At convergence the robust normal equations vanish: sum_k psi(r_k) a_k = 0 with
+    r_k = J(p + f + k) - (1 + m) T(p + k) - c and a_k = (Tx, Ty, -T, -1) at level 0.
+    Recomputed here from the oracle's flow and gain/offset with SciPy's bilinear
+    sampling and Sobel filter and a Hampel psi written from its definition, the
+    Newton step H^-1 sum psi a (H = sum w a a^T) must be below 1e-8 (d, m) and
+    1e-6 (c, in intensity levels). Noise and a corrupted block put residuals in
+    every zone of the Hampel norm."""
+    a_, b_, c_ = 8.0, 16.0, 32.0
+    r = 4
+    I2 = 1.1 * synth.render(W, H, 5, shift=(1.7, -0.9)) + 5 + np.random.default_rng(11).normal(0, 10, (H, W))
+    I2[40:47, 60:67] += 120.0
+    gx0, gy0 = np.meshgrid(np.arange(50.0, 76.0, 1.5), np.arange(34.0, 54.0, 1.5))  # supports over the block
+    pts = np.concatenate([interior_points(), np.stack([gx0.ravel(), gy0.ravel()], 1)])
+    prm = oracle.RlofParams(levels=3, radius=r, model=4, eps=1e-10, max_iter=200, hampel_a=a_, hampel_b=b_,
+                            hampel_c=c_)
+    flow, st, _, illum = oracle.rlof_track(frame1, I2, pts, prm)
+    done = np.flatnonzero(st == oracle.TRACKED)
+    assert done.size >= 30
+
+    def psi(x):
+        ax = np.abs(x)
+        return np.where(ax <= a_, x, np.where(ax <= b_, a_ * np.sign(x),
+                                              np.where(ax <= c_, a_ * np.sign(x) * (c_ - ax) / (c_ - b_), 0.0)))
+
+    def sample(img, yy, xx):
+        return ndimage.map_coordinates(img, [yy, xx], order=1, mode="nearest")
+
+    gx = ndimage.sobel(frame1, axis=1, mode="nearest") / 8.0
+    gy = ndimage.sobel(frame1, axis=0, mode="nearest") / 8.0
+    k = np.arange(-r, r + 1, dtype=np.float64)
+    ky, kx = (v.ravel() for v in np.meshgrid(k, k, indexing="ij"))
+    zones = np.zeros(4)
+    for i in done:
+        cy, cx = pts[i, 1] + ky, pts[i, 0] + kx
+        T, Tx, Ty = sample(frame1, cy, cx), sample(gx, cy, cx), sample(gy, cy, cx)
+        m, c = illum[i]
+        res = sample(I2, cy + flow[i, 1], cx + flow[i, 0]) - (1 + m) * T - c
+        w = np.where(res == 0, 1.0, psi(res) / np.where(res == 0, 1.0, res))
+        a = np.stack([Tx, Ty, -T, -np.ones_like(T)], 1)
+        step = np.linalg.solve((a * w[:, None]).T @ a, a.T @ psi(res))
+        assert np.abs(step[:3]).max() < 1e-8 and abs(step[3]) < 1e-6, (i, step)
+        ar = np.abs(res)
+        zones += [(ar <= a_).sum(), ((ar > a_) & (ar <= b_)).sum(), ((ar > b_) & (ar <= c_)).sum(), (ar > c_).sum()]
+    assert np.all(zones > 0), zones
