@@ -696,7 +696,8 @@ def main():
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
-                    help="skip the batch, FP16-storage and adjoint sections")
+                    help="skip every section after the main step (small pair, batch, FP16 storage, adjoint, "
+                         "global-motion prior, cross support, forward-backward filter, EPIC, dense pipeline)")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per tracked point (0 = automatic)")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the 64-pair batch section and print its JSON (for profiling)")
