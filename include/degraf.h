@@ -369,6 +369,7 @@ size_t dgf_degraf_backward_workspace(int W, int H, int win_w, int win_h, int ste
  *   workspace  device, 256-byte aligned, ws_bytes >= dgf_degraf_backward_workspace().
  *   grad_img   device, float, row y at grad_img + y * grad_pitch (elements,
  *              >= W); accumulated into. Deterministic (gathered, no atomics).
+ * DGF_ERR_ARG also for a float array that is not 4-byte aligned.
  */
 int degraf_detect_backward(const uint8_t* img, int W, int H, int pitch, int win_w, int win_h, int step,
                            const float* grad_pts, void* workspace, size_t ws_bytes, float* grad_img,
@@ -394,6 +395,7 @@ size_t dgf_rlof_backward_workspace(int W, int H);
  *   grad_I1, grad_I2  device, float, row pitch grad_pitch elements; accumulated
  *               into with atomics (the summation order, and so the last bits, may
  *               vary between runs).
+ * DGF_ERR_ARG also for a float array that is not 4-byte aligned.
  */
 int rlof_track_backward(const void* pyr1, const void* pyr2, int W, int H, const float* pts, int n,
                         const dgf_rlof_params* p, const float* flow, const float* illum, const uint8_t* status,

@@ -17,6 +17,8 @@
 //    and of the two Sobel planes (workspace); a per-pixel pass then adds the
 //    template adjoint and the transposed Sobel / 8 stencil into grad I1. Atomic
 //    order makes the last bits of the result vary between runs.
+#include <initializer_list>
+
 #include "common.cuh"
 
 namespace {
@@ -324,7 +326,9 @@ extern "C" int degraf_detect_backward(const uint8_t* img, int W, int H, int pitc
     const long long n = dgf_degraf_count(W, H, win_w, win_h, step);
     if (n < 0 || !img || pitch < W || !grad_img || grad_pitch < W) return DGF_ERR_ARG;
     if (n == 0) return DGF_OK;
-    if (!grad_pts || !workspace || !dgf::aligned(workspace, 256) || n > (1LL << 30)) return DGF_ERR_ARG;
+    if (!grad_pts || !workspace || !dgf::aligned(workspace, 256) || n > (1LL << 30) || !dgf::aligned(grad_pts, 4) ||
+        !dgf::aligned(grad_img, 4))
+        return DGF_ERR_ARG;
     if (ws_bytes < dgf_degraf_backward_workspace(W, H, win_w, win_h, step)) return DGF_ERR_WORKSPACE;
     float4* coef = static_cast<float4*>(workspace);
     int* argmax = reinterpret_cast<int*>(static_cast<char*>(workspace) + dgf::round_up((size_t)n * sizeof(float4), 256));
@@ -359,6 +363,9 @@ extern "C" int rlof_track_backward(const void* pyr1, const void* pyr2, int W, in
     if (!pyr1 || !pyr2 || !pts || !flow || !status || !grad_flow || (p->model == 4 && !illum) || !workspace ||
         !dgf::aligned(workspace, 256) || !dgf::aligned(pyr1, 256) || !dgf::aligned(pyr2, 256))
         return DGF_ERR_ARG;
+    for (const void* f : {(const void*)pts, (const void*)flow, (const void*)illum, (const void*)grad_flow,
+                          (const void*)grad_illum, (const void*)grad_I1, (const void*)grad_I2})
+        if (f && !dgf::aligned(f, 4)) return DGF_ERR_ARG;  // float arrays (null where optional)
     const size_t plane = dgf::round_up((size_t)W * H * sizeof(float), 256);
     if (ws_bytes < dgf_rlof_backward_workspace(W, H)) return DGF_ERR_WORKSPACE;
     dgf::LevelGeom g;

@@ -234,6 +234,25 @@ def test_adjoint_rejects_the_cross_support():
     assert rc == -1
 
 
+@pytest.mark.parametrize("which", ["pts", "flow", "illum", "grad_flow", "grad_illum", "grad_I1", "grad_I2"])
+def test_adjoint_rejects_misaligned_float_arrays(which):
+    """A float array off its 4-byte alignment is refused before any launch."""
+    lib = dgf.load()
+    good, bad = ctypes.c_void_p(1 << 20), ctypes.c_void_p((1 << 20) + 2)
+    prm = dgf.RlofParams().c()
+    ws = lib.dgf_rlof_backward_workspace(64, 64)
+    a = {k: good for k in ("pts", "flow", "illum", "grad_flow", "grad_illum", "grad_I1", "grad_I2")}
+    a[which] = bad
+    rc = lib.rlof_track_backward(good, good, 64, 64, a["pts"], 10, ctypes.byref(prm), a["flow"], a["illum"], good,
+                                 a["grad_flow"], a["grad_illum"], good, ws, a["grad_I1"], a["grad_I2"], 64, None)
+    assert rc == -1
+    if which in ("pts", "grad_I1"):  # the detection adjoint's float arrays: grad_pts and grad_img
+        rc = lib.degraf_detect_backward(good, 64, 64, 64, 8, 8, 4, bad if which == "pts" else good, good,
+                                        lib.dgf_degraf_backward_workspace(64, 64, 8, 8, 4),
+                                        bad if which == "grad_I1" else good, 64, None)
+        assert rc == -1
+
+
 def test_product_package_never_loads_the_oracle():
     code = ("import sys; sys.path.insert(0, %r); import paper_1901_09971_gb300 as d; d.load(); "
             "import bench; assert 'oracle' not in sys.modules, 'oracle imported'" % ROOT)
