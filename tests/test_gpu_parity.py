@@ -67,8 +67,14 @@ def test_detect_parity(dgf, size, ww, wh, step):
     err = np.abs(pts_g.cpu().numpy().astype(np.float64) - pts_o).max()
     assert err <= TOL_PTS
     # two correctly rounded FP32 steps (quotient, then origin): within one FP32 ulp
-    ulp = np.spacing(np.abs(pts_o).astype(np.float32)).astype(np.float64)
-    assert np.all(np.abs(pts_g.cpu().numpy().astype(np.float64) - pts_o) <= ulp)
+    g = pts_g.cpu().numpy()
+    ulp = np.maximum(np.spacing(np.abs(pts_o).astype(np.float32)), np.spacing(np.abs(g))).astype(np.float64)
+    diff = np.abs(g.astype(np.float64) - pts_o)
+    assert np.all(diff <= ulp)
+    # and the rounding budget itself: half an ulp of the result (the origin added) plus
+    # half an ulp of the local centroid (its quotient, from exact FP32 operands or, for
+    # sums from 2^24 on, from FP64), below one ulp of the window size
+    assert np.all(diff <= 0.5 * ulp + float(np.spacing(np.float32(max(ww, wh)))))
 
 
 def test_detect_pitched_frame(dgf):
