@@ -253,6 +253,21 @@ def test_adjoint_rejects_misaligned_float_arrays(which):
         assert rc == -1
 
 
+def test_missing_library_raises_instead_of_falling_back(monkeypatch, tmp_path):
+    """Without libdegraf.so every entry point raises: there is no CPU path to fall back to."""
+    from paper_1901_09971_gb300 import _abi, build
+    missing = str(tmp_path / "libdegraf.so")
+    monkeypatch.setattr(_abi, "_lib", None)
+    monkeypatch.setattr(build, "LIB", missing)
+    monkeypatch.setattr(build, "build", lambda *a, **k: missing)  # a build that produced nothing
+    with pytest.raises(RuntimeError, match="libdegraf.so not found"):
+        _abi.load()
+    with pytest.raises(RuntimeError):
+        dgf.degraf_count(64, 64, 8, 4)
+    with pytest.raises(RuntimeError):
+        dgf.pyramid_bytes(64, 64, 3)
+
+
 def test_product_package_never_loads_the_oracle():
     code = ("import sys; sys.path.insert(0, %r); import paper_1901_09971_gb300 as d; d.load(); "
             "import bench; assert 'oracle' not in sys.modules, 'oracle imported'" % ROOT)
