@@ -1,8 +1,8 @@
 """Sensitivity of the oracle's pins: copies of the oracle, each with one plausible
-mistake planted in its C source (a wrong cost, sign, index, weight or tie-break),
-are built on the CPU, and for every copy at least one pin of the stage it touches
-must fail. The copies live in a temporary directory and are loaded in place of the
-oracle only for the duration of one check."""
+mistake planted in its C source (a wrong cost, sign, index, weight or tie-break)
+or in one of its Python functions, are built on the CPU, and for every copy at
+least one pin of the stage it touches must fail. The C copies live in a temporary
+directory; each copy is loaded in place of the oracle only for one check."""
 import ctypes  # noqa: F401  (the oracle wrapper loads the copies through ctypes)
 import inspect
 import itertools
@@ -16,6 +16,7 @@ import oracle
 import test_oracle_cross
 import test_oracle_degraf
 import test_oracle_epic
+import test_oracle_fb
 import test_oracle_gm
 import test_oracle_pyramid
 import test_oracle_rlof
@@ -46,6 +47,12 @@ MUTANTS = {
     "tracking template sampled half a pixel off in y": (
         "T[s] = bilinear(A->I, A->W, A->H, plx + kx, ply + ky);",
         "T[s] = bilinear(A->I, A->W, A->H, plx + kx, ply + ky + 0.5);", [test_oracle_rlof]),
+    "DeGraF tie picks the negative centroid": (
+        "int use_neg = Sn > S;\n            double cx = use_neg ? (double)Xn",
+        "int use_neg = Sn >= S;\n            double cx = use_neg ? (double)Xn", [test_oracle_degraf]),
+    "pyramid level sizes rounded up": (
+        "for (int k = 0; k < l; ++k) { w /= 2; h /= 2; }", "for (int k = 0; k < l; ++k) { w = (w + 1) / 2; h = (h + 1) / 2; }",
+        [test_oracle_pyramid]),
     "cross rows measured from the centre pixel": (
         "while (lf < r && fabs(PIX(cx - lf - 1, cy + ky) - va) <= tau) ++lf;",
         "while (lf < r && fabs(PIX(cx - lf - 1, cy + ky) - vc) <= tau) ++lf;", [test_oracle_cross]),
@@ -69,6 +76,21 @@ MUTANTS = {
         "const double v[3] = {xs - pts[2 * t], pts[2 * t + 1] - ys, 1.0};", [test_oracle_epic]),
     "EPIC edges from a Prewitt instead of a Sobel operator": (
         "const int wc = dy == 0 ? 2 : 1, wr = dx == 0 ? 2 : 1;", "const int wc = 1, wr = 1;", [test_oracle_epic]),
+}
+
+
+# Mistakes in the oracle's Python functions: name: (function, text, replacement, pin modules)
+PY_MUTANTS = {
+    "round-trip error subtracts the backward flow": (
+        "rlof_track_fb", "np.hypot(*(f + b).T)", "np.hypot(*(f - b).T)", [test_oracle_fb]),
+    "backward pass starts from the start points": (
+        "rlof_track_fb", "rlof_track(I2, I1, pts + f, params, nthreads)", "rlof_track(I2, I1, pts, params, nthreads)",
+        [test_oracle_fb]),
+    "the filter also rejects points the forward pass lost": (
+        "rlof_track_fb", "status[fwd & (err > fb_max)] = FB_REJECTED", "status[err > fb_max] = FB_REJECTED",
+        [test_oracle_fb]),
+    "global-motion prior forgets to subtract the point": (
+        "gm_prior_flow", "a[0] * x + a[1] * y + a[2] - x", "a[0] * x + a[1] * y + a[2]", [test_oracle_gm]),
 }
 
 
@@ -140,5 +162,24 @@ def test_every_planted_mistake_fails_a_pin(name, monkeypatch):
                 except Exception:  # a failed assertion, or an error the mistake provokes
                     failed.append(pin)
         monkeypatch.setattr(oracle, "_lib", None)  # the real oracle is loaded again on next use
+    print(f"{name}: caught by {failed[:3]}{' ...' if len(failed) > 3 else ''}")
+    assert failed, f"no pin catches: {name}"
+
+
+@pytest.mark.parametrize("name", list(PY_MUTANTS))
+def test_every_planted_python_mistake_fails_a_pin(name, monkeypatch):
+    fn_name, old, new, modules = PY_MUTANTS[name]
+    source = inspect.getsource(getattr(oracle, fn_name))
+    assert source.count(old) == 1, f"mutation site not unique: {old}"
+    namespace = dict(vars(oracle))
+    exec(compile(source.replace(old, new), f"<mutant of oracle.{fn_name}>", "exec"), namespace)
+    monkeypatch.setattr(oracle, fn_name, namespace[fn_name])
+    failed = []
+    for module in modules:
+        for pin, call in pin_calls(module):
+            try:
+                call()
+            except Exception:  # a failed assertion, or an error the mistake provokes
+                failed.append(pin)
     print(f"{name}: caught by {failed[:3]}{' ...' if len(failed) > 3 else ''}")
     assert failed, f"no pin catches: {name}"
