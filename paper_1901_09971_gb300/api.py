@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import threading
 
 import torch
 
@@ -199,6 +200,12 @@ def pyramid_planes(buf: torch.Tensor, layout: dict):
         grads = (plane(layout["off_Ix"][l]), plane(layout["off_Iy"][l])) if layout["with_grad"] else (None, None)
         out.append((plane(layout["off_I"][l]), *grads))
     return out
+
+
+# The lanes setting is process-wide; a BatchTracker holds this lock from setting its
+# own value to restoring the previous one, so concurrent trackers never see each
+# other's value.
+_lanes_lock = threading.Lock()
 
 
 def set_lanes(lanes: int) -> int:
@@ -526,13 +533,16 @@ class BatchTracker:
             self.bind(frames1, frames2)
         elif getattr(self, "_arr", None) is None:
             raise ValueError("run() without frames needs frames bound first")
-        prev = set_lanes(self.lanes) if self.lanes else None
-        try:
+        def call():
             check("rlof_track_many", load().rlof_track_many(self._arr, len(self.specs), ctypes.byref(self._prm),
                                                             _ptr(self.workspace), self.workspace.numel(), int(stages),
                                                             int(use_graph), _stream()))
-        finally:
-            if prev is not None:
+
+        with _lanes_lock:  # this tracker's setting (0 = the library's choice) for exactly this call
+            prev = set_lanes(self.lanes)
+            try:
+                call()
+            finally:
                 set_lanes(prev)
         return self.pts, self.flow, self.status, self.iters
 

@@ -23,6 +23,8 @@
 // Time per iteration splits roughly 70% per-sample accumulation, 18% group
 // reduction, 5% solve: the kernel is bound by instruction issue and dependency
 // latency on the FP32 and integer pipes, not by memory (the pyramids stay in L1/L2).
+#include <atomic>
+
 #include "common.cuh"
 #include "batch.cuh"
 
@@ -769,7 +771,8 @@ __global__ void __launch_bounds__(block_threads<G>(), MINB) rlof_kernel(const __
     if (lane == 0) write_point(J, pt, status, gx + dx, gy + dy, iters, m, c, MODEL == 4);
 }
 
-int g_lanes_override = 0;
+// Set by dgf_rlof_set_lanes from any thread, read when a launch is configured.
+std::atomic<int> g_lanes_override{0};
 
 template <typename TS, int MODEL, int G, int SLP, int RC>
 int launch_one(const TrackBatch& a, cudaStream_t stream)
@@ -814,7 +817,8 @@ int choose_lanes(int radius)
     // 8 and 16 lanes are built for radius 4 and 5 only; other radii use 32 lanes.
     // Measured on GB300: radius 5 fastest at 16 lanes, radius 4 at 8.
     if (radius != 4 && radius != 5) return 32;
-    if (g_lanes_override) return g_lanes_override;
+    const int set = g_lanes_override.load(std::memory_order_relaxed);
+    if (set) return set;
     return radius == 5 ? 16 : 8;
 }
 
@@ -844,9 +848,7 @@ extern "C" void dgf_rlof_params_default(dgf_rlof_params* p)
 extern "C" int dgf_rlof_set_lanes(int lanes)
 {
     if (lanes != 0 && lanes != 8 && lanes != 16 && lanes != 32) return DGF_ERR_ARG;
-    const int prev = g_lanes_override;
-    g_lanes_override = lanes;
-    return prev;
+    return g_lanes_override.exchange(lanes, std::memory_order_relaxed);
 }
 
 namespace dgf {
@@ -884,7 +886,7 @@ int check_levels(int W, int H, const dgf_rlof_params* p)
     return g.W < need || g.H < need ? DGF_ERR_LEVELS : DGF_OK;
 }
 
-int lanes_setting() { return ::rlof_detail::g_lanes_override; }
+int lanes_setting() { return ::rlof_detail::g_lanes_override.load(std::memory_order_relaxed); }
 
 int launch_track(const TrackBatch& a, const dgf_rlof_params* p, cudaStream_t stream)
 {
