@@ -37,6 +37,25 @@ def test_header_declarations_are_exported():
     assert set(names) <= exported
 
 
+def declared_arity():
+    """Parameter count of every prototype in the header (comments removed)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for name, args in re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(([^()]*)\)\s*;", text):
+        args = args.strip()
+        out[name] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_argtypes_match_the_header():
+    """The ctypes declarations pass exactly as many arguments as each prototype takes."""
+    lib = dgf.load()
+    arity = declared_arity()
+    assert set(arity) == set(_abi.EXPORTS)
+    for name in _abi.EXPORTS:
+        assert len(getattr(lib, name).argtypes) == arity[name], name
+
+
 def test_count_matches_oracle():
     for (W, H, w, h, s) in [(1242, 375, 7, 7, 3), (256, 128, 8, 8, 4), (1240, 376, 3, 3, 9), (5, 5, 7, 7, 1),
                             (64, 64, 64, 64, 1), (100, 37, 9, 2, 5)]:
