@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+import golden
 import oracle
 import synth
 
@@ -75,6 +76,22 @@ def test_detect_parity(dgf, size, ww, wh, step):
     # half an ulp of the local centroid (its quotient, from exact FP32 operands or, for
     # sums from 2^24 on, from FP64), below one ulp of the window size
     assert np.all(diff <= 0.5 * ulp + float(np.spacing(np.float32(max(ww, wh)))))
+
+
+@pytest.mark.parametrize("case", golden.degraf_cases(), ids=lambda c: c[0])
+def test_detect_hand_worked_examples(dgf, case):
+    """The kernel on the hand-worked key-points of tests/golden (Eq. 1-2: inverted and
+    positive centroids, a tie, a grid of two windows): within the FP32 rounding budget
+    of the exact fractions (half an ulp of the result plus one ulp of the window size)."""
+    _, img, ww, wh, step, expect = case
+    pts = dgf.detect(to_dev(img), ww, step, win_h=wh)
+    torch.cuda.synchronize()
+    g = pts.cpu().numpy()
+    exact = np.array([[float(x), float(y)] for x, y in expect])
+    assert g.shape == exact.shape
+    ulp = np.maximum(np.spacing(np.abs(exact).astype(np.float32)), np.spacing(np.abs(g))).astype(np.float64)
+    budget = 0.5 * ulp + float(np.spacing(np.float32(max(ww, wh))))
+    assert np.all(np.abs(g.astype(np.float64) - exact) <= budget)
 
 
 def test_detect_pitched_frame(dgf):

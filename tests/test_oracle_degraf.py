@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+import golden
 
 
 def brute_force(img, w, h, step):
@@ -135,3 +136,15 @@ def test_ramp_closed_forms():
 def test_all_zero_window_uses_negative_centroid():
     p, s, neg = oracle.degraf_detect(np.zeros((5, 5), np.uint8), 5, 5, 1)
     assert neg[0] and s[0, 0] == 0 and np.allclose(p[0], [2, 2])
+
+
+@pytest.mark.parametrize("case", golden.degraf_cases(), ids=lambda c: c[0])
+def test_hand_worked_examples(case):
+    """Key-points worked by hand from Eq. 1-2 (tests/golden/degraf_hand_worked.txt):
+    an inverted-intensity centroid, a positive one, a tie (kept positive) and a grid of
+    two windows; the oracle equals the exact fractions to FP64 rounding."""
+    _, img, ww, wh, step, expect = case
+    pts, _, _ = oracle.degraf_detect(img, ww, wh, step)
+    assert pts.shape == (len(expect), 2)
+    for (x, y), (ex, ey) in zip(pts, expect):
+        assert abs(x - float(ex)) <= 1e-12 and abs(y - float(ey)) <= 1e-12
