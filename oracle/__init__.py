@@ -2,7 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the benchmark's
 CPU-baseline leg may use this module; the CUDA product path never imports it.
-The arithmetic lives in ``degraf_oracle.c``; this wrapper only marshals arrays.
+The arithmetic lives in ``degraf_oracle.c``; this wrapper marshals arrays, except for
+three compositions written here in a few numpy lines each: the forward-backward round
+trip (``rlof_track_fb``), the global-motion prior's initial flow (``gm_prior_flow``)
+and the two-pass sequence of ``rlof_track_gm``.
 """
 from __future__ import annotations
 
