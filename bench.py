@@ -48,8 +48,65 @@ def _measured_peaks():
 
 
 HBM_PEAK_GBS, SM_MAX_MHZ, PEAK_SOURCE = _measured_peaks()
-# FP32 lanes x 2 flop x SMs at the maximum SM clock (GB300: 152 SMs, 128 FP32 lanes each)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def _median_loaded_mhz():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["clocks_under_load"]["sm_mhz_median"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return None
+
+
+def measure_fp32_peak(dgf, torch, dev, seconds: float = 1.0):
+    """FP32 FMA throughput of this GPU, measured with the library's probe (scalar FFMA
+    and packed FP32x2 FMA over 8 resident blocks of 256 threads per SM), timed with
+    CUDA events while nvidia-smi samples the SM clock; the tracking kernel's roofline
+    denominator. Also scaled to the maximum and to the median loaded SM clock."""
+    import ctypes
+    lib = dgf.load()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads, iters = sms * 8, 256, 20000
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    s_ptr = ctypes.c_void_p(stream.cuda_stream)
+    rec = {"sms": sms, "blocks": blocks, "threads": threads}
+    for packed in (0, 1):
+        def launch():
+            rc = lib.dgf_fp32_probe(ctypes.c_void_p(out.data_ptr()), blocks, threads, iters, packed, s_ptr)
+            if rc:
+                raise RuntimeError(f"dgf_fp32_probe failed ({rc})")
+        for _ in range(3):
+            launch()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        launch()
+        b.record(stream)
+        b.synchronize()
+        reps = max(3, int(seconds / max(a.elapsed_time(b) * 1e-3, 1e-4)))
+        with ClockSampler(dev.index or 0) as clocks:
+            a.record(stream)
+            for _ in range(reps):
+                launch()
+            b.record(stream)
+            b.synchronize()
+        tflops = lib.dgf_fp32_probe_flops(blocks, threads, iters, packed) * reps / (a.elapsed_time(b) * 1e-3) / 1e12
+        c = clocks.summary()
+        key = "packed" if packed else "scalar"
+        rec[key] = {"tflops": tflops, "clocks": c}
+    best = max(rec["scalar"]["tflops"], rec["packed"]["tflops"])
+    mhz = rec["packed"]["clocks"].get("sm_mhz") if rec["packed"]["tflops"] >= rec["scalar"]["tflops"] else \
+        rec["scalar"]["clocks"].get("sm_mhz")
+    rec["tflops"] = best
+    rec["sm_mhz"] = mhz
+    if mhz:
+        rec["tflops_at_max_clock"] = best * SM_MAX_MHZ / mhz
+        med = _median_loaded_mhz()
+        if med:
+            rec["tflops_at_median_loaded_clock"] = best * med / mhz
+            rec["median_loaded_mhz"] = med
+    return rec
 
 
 def flops_model(radius: int, model: int):
@@ -632,6 +689,7 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
     status = tr.status.cpu().numpy()
     flops = algorithmic_flops(iters, status, prm.levels, prm.radius, prm.model)
     achieved = flops / (rlof_ms.mean() / 1e3) / 1e12
+    fp32 = measure_fp32_peak(dgf, torch, dev)
 
     # end to end through the public API: pinned host frames in, host results out
     h1 = torch.from_numpy(pair.I1).pin_memory()
@@ -675,11 +733,13 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
                 "pairs_per_s": world * args.steps / total_s,
                 "rlof_ms": float(rlof_ms.mean()), "detect_pyramid_ms": float((step_ms - rlof_ms).mean()),
                 "tracked_fraction": float(np.mean((status == 0) | (status == 4))),
-                "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": kernel_traffic(),
-                             "peak_basis": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz (max clock, "
-                                           f"{PEAK_SOURCE})",
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32["tflops"], "unit": "TFLOP/s",
+                             "frac": achieved / fp32["tflops"], "traffic": kernel_traffic(),
+                             "peak_basis": f"measured: FP32 FMA probe (dgf_fp32_probe, the faster of scalar and "
+                                           f"packed FMA) on {fp32['sms']} SMs at a median {fp32['sm_mhz']} MHz, "
+                                           f"CUDA events",
                              "kernel": "rlof_kernel", "flops_per_launch": flops},
+                "fp32_peak": fp32,
                 "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": 2 * W * H,
                         "d2h_bytes_per_step": n_pts * (8 + 8 + 1)},
                 "gpu_launches": 4 * args.steps,

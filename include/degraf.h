@@ -478,6 +478,30 @@ int rlof_track_many(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p
  */
 int rlof_track_pair_noalloc(const dgf_pair* pair, const dgf_rlof_params* p, cudaStream_t stream);
 
+/* ---- measurement and accuracy probes (no counterpart in the paper) -------- */
+
+/*
+ * FP32 throughput probe, the measured ceiling of the tracking kernel's roofline
+ * (tracking is bound by FP32 issue, not memory). Launches `blocks` x `threads`
+ * threads (threads a multiple of 32, at most 256), each running 64 steps of eight
+ * independent fused multiply-add chains per trip for `iters` trips; packed = 1 uses
+ * the packed FP32x2 FMA (two FMAs per lane and instruction, the form the tracking
+ * kernel issues), packed = 0 scalar FFMA. out: device float [blocks * threads],
+ * written once per thread (a value of no interest that keeps the work alive).
+ * The caller times the launch on `stream`; dgf_fp32_probe_flops() gives its FLOPs
+ * (2 per FMA). Returns DGF_ERR_ARG for bad sizes.
+ */
+int dgf_fp32_probe(float* out, int blocks, int threads, int iters, int packed, cudaStream_t stream);
+double dgf_fp32_probe_flops(int blocks, int threads, int iters, int packed);
+
+/*
+ * exp(-y) as the EPIC fit weights compute it (Tang's table-driven method, ACM TOMS
+ * 15(2), 1989; FP64), for y >= 0, so that its error can be measured against a
+ * reference exponential. y, out: device double [n]. Returns DGF_ERR_ARG for n < 0
+ * or null pointers with n > 0.
+ */
+int dgf_epic_exp_neg(const double* y, double* out, int n, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

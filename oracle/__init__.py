@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes
 import dataclasses
 import os
+import platform
 import subprocess
 
 import numpy as np
@@ -20,20 +21,36 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "degraf_oracle.c")
 _LIBDIR = os.path.join(_HERE, "lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
+# The same source with the tracking iteration in FP32 (-DORACLE_REAL=float): a
+# measuring device for the GPU parity bars, never a reference value; "f32fma" also
+# lets the compiler fuse multiply-adds (another FP32 rounding pattern).
+_VARIANTS = {"f64": ("liboracle.so", []),
+             "f32": ("liboracle_f32.so", ["-DORACLE_REAL=float"]),
+             "f32fma": ("liboracle_f32fma.so", ["-DORACLE_REAL=float", "-ffp-contract=fast"])}
 
 TRACKED, OOB, SMALL_EIG, SINGULAR, MAXITER = 0, 1, 2, 3, 4
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP64, no fast-math, no FMA contraction)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
+def build(force: bool = False, precision: str = "f64") -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction, so x86 and Arm
+    hosts give the same bits). precision "f64" is the oracle; "f32" compiles the
+    same source with the tracking iteration in FP32 and "f32fma" does so with fused
+    multiply-adds (test infrastructure that measures what FP32 rounding alone does
+    to the iteration)."""
+    if precision not in _VARIANTS:
+        raise ValueError(precision)
+    name, extra = _VARIANTS[precision]
+    out = os.path.join(_LIBDIR, name)
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
     os.makedirs(_LIBDIR, exist_ok=True)
-    tmp = _LIB + f".tmp{os.getpid()}"
+    tmp = out + f".tmp{os.getpid()}"
+    if precision == "f32fma" and platform.machine() in ("x86_64", "AMD64"):
+        extra = extra + ["-mfma"]  # FMA is part of the base instruction set on Arm
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-                    "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"], check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+                    "-ffp-contract=off", "-fno-fast-math", *extra, "-o", tmp, _SRC, "-lm"], check=True)
+    os.replace(tmp, out)
+    return out
 
 
 class _RlofParams(ctypes.Structure):
@@ -61,13 +78,14 @@ class RlofParams:
                            self.hampel_a, self.hampel_b, self.hampel_c, self.min_eig, self.cross_tau)
 
 
-_lib = None
+_libs: dict = {}
 
 
-def lib():
-    global _lib
+def lib(precision: str = "f64"):
+    _lib = _libs.get(precision)
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        _lib = ctypes.CDLL(build(precision=precision))
+        _libs[precision] = _lib
         P, I, L, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double
         _lib.oracle_degraf_count.argtypes = [I, I, I, I, I]
         _lib.oracle_degraf_count.restype = L
@@ -91,6 +109,8 @@ def lib():
         _lib.oracle_rlof_track_init.argtypes = [P, P, I, I, P, I, ctypes.POINTER(_RlofParams), P, P, P, P,
                                                 P, I]
         _lib.oracle_rlof_track_init.restype = I
+        _lib.oracle_rlof_track_pyr.argtypes = [P, P, I, I, P, I, ctypes.POINTER(_RlofParams), P, P, P, P, I]
+        _lib.oracle_rlof_track_pyr.restype = I
         _lib.oracle_cross_mask.argtypes = [P, I, I, D, D, I, D, P]
         _lib.oracle_cross_mask.restype = I
         _lib.oracle_gm_fit_affine.argtypes = [P, P, P, I, I, D, D, P]
@@ -160,11 +180,12 @@ def hampel_psi(r: float, a: float, b: float, c: float) -> float:
 
 
 def rlof_track(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofParams,
-               nthreads: int = 0, init_flow: np.ndarray | None = None):
+               nthreads: int = 0, init_flow: np.ndarray | None = None, precision: str = "f64"):
     """Track pts [n,2] from I1 to I2: (flow [n,2], status [n] u8, iters [n] i32, illum [n,2]).
 
     init_flow [n,2] (optional): initial level-0 flow per point (the global-motion
-    prior); tracking then starts the coarsest level at init_flow / 2^(levels-1)."""
+    prior); tracking then starts the coarsest level at init_flow / 2^(levels-1).
+    precision "f32" runs the FP32 build of the same iteration (see build())."""
     I1 = np.ascontiguousarray(I1, dtype=np.float64)
     I2 = np.ascontiguousarray(I2, dtype=np.float64)
     pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
@@ -176,11 +197,45 @@ def rlof_track(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofPara
     illum = np.zeros((n, 2), np.float64)
     prm = params._c()
     init = None if init_flow is None else np.ascontiguousarray(init_flow, dtype=np.float64).reshape(n, 2)
-    rc = lib().oracle_rlof_track_init(_ptr(I1), _ptr(I2), W, H, _ptr(pts), n, ctypes.byref(prm),
+    rc = lib(precision).oracle_rlof_track_init(_ptr(I1), _ptr(I2), W, H, _ptr(pts), n, ctypes.byref(prm),
                                       _ptr(init) if init is not None else None, _ptr(flow), _ptr(status),
                                       _ptr(iters), _ptr(illum), int(nthreads))
     if rc:
         raise ValueError("oracle_rlof_track: bad arguments")
+    return flow, status, iters, illum
+
+
+def pyramid_buffer(img: np.ndarray, levels: int) -> np.ndarray:
+    """The pyramid of a frame as one flat float64 buffer (per level I, Ix, Iy), the
+    layout rlof_track_on_pyramids reads."""
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    H, W = img.shape
+    buf = np.zeros(int(lib().oracle_pyramid_size(W, H, levels)), np.float64)
+    if lib().oracle_pyramid(_ptr(img), W, H, levels, _ptr(buf)):
+        raise ValueError("oracle_pyramid: bad arguments")
+    return buf
+
+
+def rlof_track_on_pyramids(pyr1: np.ndarray, pyr2: np.ndarray, W: int, H: int, pts: np.ndarray,
+                           params: RlofParams, nthreads: int = 0, precision: str = "f64"):
+    """rlof_track on given pyramid buffers (pyramid_buffer's layout), e.g. with their
+    values rounded to a storage format first: (flow, status, iters, illum)."""
+    pyr1 = np.ascontiguousarray(pyr1, dtype=np.float64)
+    pyr2 = np.ascontiguousarray(pyr2, dtype=np.float64)
+    size = int(lib().oracle_pyramid_size(W, H, params.levels))
+    if pyr1.size != size or pyr2.size != size:
+        raise ValueError("pyramid buffers do not match W, H and the level count")
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
+    n = pts.shape[0]
+    flow = np.zeros((n, 2), np.float64)
+    status = np.zeros(n, np.uint8)
+    iters = np.zeros(n, np.int32)
+    illum = np.zeros((n, 2), np.float64)
+    prm = params._c()
+    rc = lib(precision).oracle_rlof_track_pyr(_ptr(pyr1), _ptr(pyr2), W, H, _ptr(pts), n, ctypes.byref(prm),
+                                              _ptr(flow), _ptr(status), _ptr(iters), _ptr(illum), int(nthreads))
+    if rc:
+        raise ValueError("oracle_rlof_track_pyr: bad arguments")
     return flow, status, iters, illum
 
 
@@ -203,7 +258,8 @@ def gm_fit_affine(pts: np.ndarray, flow: np.ndarray, status: np.ndarray, iters: 
 
 
 def rlof_track_gm(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofParams, stride: int = 4,
-                  extra_levels: int = 2, iters: int = 8, c0: float = 32.0, c_min: float = 2.0, nthreads: int = 0):
+                  extra_levels: int = 2, iters: int = 8, c0: float = 32.0, c_min: float = 2.0, nthreads: int = 0,
+                  precision: str = "f64"):
     """Tracking with the global-motion prior (Section 3, RLOF(IM-GM); the paper
     gives no formula, so this is the reading): (1) a sparse first pass tracks
     every stride-th point with extra_levels more pyramid levels, which reaches
@@ -213,9 +269,10 @@ def rlof_track_gm(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofP
     pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
     sub = pts[::stride]
     deep = dataclasses.replace(params, levels=params.levels + extra_levels)
-    fs, ss, _, _ = rlof_track(I1, I2, sub, deep, nthreads)
+    fs, ss, _, _ = rlof_track(I1, I2, sub, deep, nthreads, precision=precision)
     a, made = gm_fit_affine(sub, fs, ss, iters, c0, c_min)
-    flow, status, its, illum = rlof_track(I1, I2, pts, params, nthreads, init_flow=gm_prior_flow(a, pts))
+    flow, status, its, illum = rlof_track(I1, I2, pts, params, nthreads, init_flow=gm_prior_flow(a, pts),
+                                          precision=precision)
     return flow, status, its, illum, a, made
 
 
@@ -235,7 +292,7 @@ FB_REJECTED = 5
 
 
 def rlof_track_fb(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofParams, fb_max: float = 0.0,
-                  nthreads: int = 0):
+                  nthreads: int = 0, precision: str = "f64"):
     """Forward-backward consistency (not in the paper's text; a common filter on
     sparse tracks): points are tracked from I1 to I2 (flow f), their end points
     p + f back from I2 to I1 (flow b) with the same parameters; the round-trip error
@@ -243,8 +300,8 @@ def rlof_track_fb(I1: np.ndarray, I2: np.ndarray, pts: np.ndarray, params: RlofP
     With fb_max > 0, forward-tracked points whose error exceeds fb_max get status
     FB_REJECTED (5); their flow is kept. Returns (flow, status, fb_err)."""
     pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
-    f, s, _, _ = rlof_track(I1, I2, pts, params, nthreads)
-    b, sb, _, _ = rlof_track(I2, I1, pts + f, params, nthreads)
+    f, s, _, _ = rlof_track(I1, I2, pts, params, nthreads, precision=precision)
+    b, sb, _, _ = rlof_track(I2, I1, pts + f, params, nthreads, precision=precision)
     fwd = (s == TRACKED) | (s == MAXITER)
     bwd = (sb == TRACKED) | (sb == MAXITER)
     err = np.where(fwd & bwd, np.hypot(*(f + b).T), np.inf)

@@ -180,6 +180,22 @@ int oracle_pyramid(const double* img, int W, int H, int levels, double* out)
 
 /* -------------------------------------------------------------------- RLOF */
 
+/*
+ * Arithmetic type of the tracking iteration (template sampling, residuals, robust
+ * weights, normal equations, solve and update). It is double: this is the FP64
+ * oracle. The test suite also compiles this file a second time with
+ * -DORACLE_REAL=float, which rounds every tracking quantity to FP32 while taking
+ * exactly the same steps; comparing that build with the FP64 one measures how far
+ * FP32 rounding alone moves the iteration, the basis of the GPU parity bars. Pyramid
+ * values are exact dyadic fractions in both types. Every literal below is cast to
+ * `real` so that the FP32 build never computes in double.
+ */
+#ifndef ORACLE_REAL
+#define ORACLE_REAL double
+#endif
+typedef ORACLE_REAL real;
+#define R(x) ((real)(x))
+
 typedef struct {
     int levels;     /* pyramid levels, level 0 included */
     int radius;     /* support is (2 radius + 1)^2 pixels */
@@ -199,59 +215,65 @@ typedef struct {
  *          = a sgn(r) (c - |r|) / (c - b)       b < |r| <= c
  *          = 0                                  |r| > c
  */
-double oracle_hampel_psi(double r, double a, double b, double c)
+static real hampel_psi(real r, real a, real b, real c)
 {
-    double ar = fabs(r), s = r < 0 ? -1.0 : 1.0;
+    real ar = fabs(r), s = r < 0 ? R(-1) : R(1);
     if (ar <= a) return r;
     if (ar <= b) return a * s;
     if (ar <= c) return a * s * (c - ar) / (c - b);
-    return 0.0;
+    return R(0);
+}
+
+double oracle_hampel_psi(double r, double a, double b, double c)
+{
+    return (double)hampel_psi(R(r), R(a), R(b), R(c));
 }
 
 /* IRLS weight psi(r) / r, equal to 1 at r = 0. */
-static double hampel_weight(double r, double a, double b, double c)
+static real hampel_weight(real r, real a, real b, real c)
 {
-    if (fabs(r) <= a) return 1.0;
-    return oracle_hampel_psi(r, a, b, c) / r;
+    if (fabs(r) <= a) return R(1);
+    return hampel_psi(r, a, b, c) / r;
 }
 
 /* Bilinear interpolation of a W x H plane at (x, y); each of the four taps is
  * clamped to the border. */
-static double bilinear(const double* P, int W, int H, double x, double y)
+static real bilinear(const double* P, int W, int H, real x, real y)
 {
-    double fx0 = floor(x), fy0 = floor(y);
+    real fx0 = floor(x), fy0 = floor(y);
     int x0 = (int)fx0, y0 = (int)fy0;
-    double ax = x - fx0, ay = y - fy0;
+    real ax = x - fx0, ay = y - fy0;
     int xa = clampi(x0, 0, W - 1), xb = clampi(x0 + 1, 0, W - 1);
     int ya = clampi(y0, 0, H - 1), yb = clampi(y0 + 1, 0, H - 1);
-    return (1 - ax) * (1 - ay) * P[(long)ya * W + xa] + ax * (1 - ay) * P[(long)ya * W + xb]
-         + (1 - ax) * ay * P[(long)yb * W + xa] + ax * ay * P[(long)yb * W + xb];
+    return (1 - ax) * (1 - ay) * R(P[(long)ya * W + xa]) + ax * (1 - ay) * R(P[(long)ya * W + xb])
+         + (1 - ax) * ay * R(P[(long)yb * W + xa]) + ax * ay * R(P[(long)yb * W + xb]);
 }
 
 /* Cholesky solve of the n x n symmetric system A x = rhs (n <= 4). Returns 0 on a
  * non-positive pivot. */
-static int cholesky_solve(int n, const double A[4][4], const double rhs[4], double x[4])
+static int cholesky_solve(int n, const real A[4][4], const real rhs[4], real x[4])
 {
-    double L[4][4] = {{0}};
+    real L[4][4] = {{0}};
     for (int i = 0; i < n; ++i)
         for (int j = 0; j <= i; ++j) {
-            double s = A[i][j];
+            real s = A[i][j];
             for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
             if (i == j) {
-                if (!(s > 0.0)) return 0;
-                L[i][i] = sqrt(s);
+                if (!(s > 0)) return 0;
+                L[i][i] = R(sqrt(s));  /* FP32 build: a double square root rounded once more is
+                                           still the correctly rounded FP32 root */
             } else {
                 L[i][j] = s / L[j][j];
             }
         }
-    double z[4];
+    real z[4];
     for (int i = 0; i < n; ++i) {
-        double s = rhs[i];
+        real s = rhs[i];
         for (int k = 0; k < i; ++k) s -= L[i][k] * z[k];
         z[i] = s / L[i][i];
     }
     for (int i = n - 1; i >= 0; --i) {
-        double s = z[i];
+        real s = z[i];
         for (int k = i + 1; k < n; ++k) s -= L[k][i] * x[k];
         x[i] = s / L[i][i];
     }
@@ -318,10 +340,10 @@ static void pyramid_views(const double* pyr, int W, int H, int levels, level_vie
  * Pixels outside the level are read clamped to the border. Returns the number of
  * kept samples (at least 1: the centre).
  */
-static int cross_mask(const level_view* A, double plx, double ply, int r, double tau, unsigned char* mask)
+static int cross_mask(const level_view* A, real plx, real ply, int r, double tau, unsigned char* mask)
 {
     const int side = 2 * r + 1;
-    const int cx = clampi((int)floor(plx + 0.5), 0, A->W - 1), cy = clampi((int)floor(ply + 0.5), 0, A->H - 1);
+    const int cx = clampi((int)floor(plx + R(0.5)), 0, A->W - 1), cy = clampi((int)floor(ply + R(0.5)), 0, A->H - 1);
 #define PIX(x, y) A->I[(long)clampi((y), 0, A->H - 1) * A->W + clampi((x), 0, A->W - 1)]
     const double vc = PIX(cx, cy);
     int up = 0, dn = 0, n = 0;
@@ -350,7 +372,7 @@ int oracle_cross_mask(const double* I1, int W, int H, double px, double py, int 
 {
     if (!I1 || W < 1 || H < 1 || r < 1 || r > 15 || !mask) return -1;
     level_view v = {W, H, I1, NULL, NULL};
-    return cross_mask(&v, px, py, r, tau, mask);
+    return cross_mask(&v, R(px), R(py), r, tau, mask);
 }
 
 static int track_point(const level_view* P1, const level_view* P2, const oracle_rlof_params* prm,
@@ -358,26 +380,27 @@ static int track_point(const level_view* P1, const level_view* P2, const oracle_
 {
     const int r = prm->radius, side = 2 * r + 1, npx = side * side;
     const int nm = prm->model == 4 ? 4 : 2;
-    double* T = malloc(sizeof(double) * 4 * npx);
-    double *Tx = T + npx, *Ty = T + 2 * npx, *Mk = T + 3 * npx;
+    const real ha = R(prm->hampel_a), hb = R(prm->hampel_b), hc = R(prm->hampel_c);
+    real* T = malloc(sizeof(real) * 4 * npx);
+    real *Tx = T + npx, *Ty = T + 2 * npx, *Mk = T + 3 * npx;
     unsigned char* keep = malloc((size_t)npx);
     /* an initial level-0 flow u starts the coarsest level at g = u / 2^(L-1) */
-    const double s0 = ldexp(1.0, -(prm->levels - 1));
-    double gx = init ? init[0] * s0 : 0, gy = init ? init[1] * s0 : 0, dx = 0, dy = 0, m = 0, c = 0;
+    const real s0 = R(ldexp(1.0, -(prm->levels - 1)));
+    real gx = init ? R(init[0]) * s0 : R(0), gy = init ? R(init[1]) * s0 : R(0), dx = 0, dy = 0, m = 0, c = 0;
     int status = OR_TRACKED;
     *iters = 0;
     for (int l = prm->levels - 1; l >= 0 && status == OR_TRACKED; --l) {
         const level_view* A = &P1[l];
         const level_view* B = &P2[l];
-        double scale = ldexp(1.0, -l);
-        double plx = (px + 0.5) * scale - 0.5, ply = (py + 0.5) * scale - 0.5;
+        real scale = R(ldexp(1.0, -l));
+        real plx = (R(px) + R(0.5)) * scale - R(0.5), ply = (R(py) + R(0.5)) * scale - R(0.5);
         /* support mask: the cross (tau > 0) or the whole square */
         int n_keep = npx;
         if (prm->cross_tau > 0)
             n_keep = cross_mask(A, plx, ply, r, prm->cross_tau, keep);
         else
             memset(keep, 1, (size_t)npx);
-        double G00 = 0, G01 = 0, G11 = 0;
+        real G00 = 0, G01 = 0, G11 = 0;
         for (int ky = -r; ky <= r; ++ky)
             for (int kx = -r; kx <= r; ++kx) {
                 int s = (ky + r) * side + (kx + r);
@@ -389,41 +412,41 @@ static int track_point(const level_view* P1, const level_view* P2, const oracle_
                 G01 += Mk[s] * Tx[s] * Ty[s];
                 G11 += Mk[s] * Ty[s] * Ty[s];
             }
-        double half_tr = 0.5 * (G00 + G11), half_df = 0.5 * (G00 - G11);
-        double lam_min = half_tr - sqrt(half_df * half_df + G01 * G01);
-        if (lam_min / n_keep < prm->min_eig) { status = OR_SMALL_EIG; break; }
+        real half_tr = R(0.5) * (G00 + G11), half_df = R(0.5) * (G00 - G11);
+        real lam_min = half_tr - R(sqrt(half_df * half_df + G01 * G01));
+        if (lam_min / n_keep < R(prm->min_eig)) { status = OR_SMALL_EIG; break; }
         dx = dy = 0;
         int converged = 0;
         for (int it = 0; it < prm->max_iter; ++it) {
-            double qx = plx + gx + dx, qy = ply + gy + dy;
+            real qx = plx + gx + dx, qy = ply + gy + dy;
             if (!(qx >= 0 && qx <= B->W - 1 && qy >= 0 && qy <= B->H - 1)) { status = OR_OOB; break; }
-            double Hm[4][4] = {{0}}, bv[4] = {0};
+            real Hm[4][4] = {{0}}, bv[4] = {0};
             for (int ky = -r; ky <= r; ++ky)
                 for (int kx = -r; kx <= r; ++kx) {
                     int s = (ky + r) * side + (kx + r);
-                    double J = bilinear(B->I, B->W, B->H, qx + kx, qy + ky);
-                    double res, a[4];
+                    real J = bilinear(B->I, B->W, B->H, qx + kx, qy + ky);
+                    real res, a[4];
                     if (nm == 4) {
                         res = J - (1 + m) * T[s] - c;
-                        a[0] = Tx[s]; a[1] = Ty[s]; a[2] = -T[s]; a[3] = -1.0;
+                        a[0] = Tx[s]; a[1] = Ty[s]; a[2] = -T[s]; a[3] = R(-1);
                     } else {
                         res = J - T[s];
                         a[0] = Tx[s]; a[1] = Ty[s];
                     }
-                    double w = Mk[s] * hampel_weight(res, prm->hampel_a, prm->hampel_b, prm->hampel_c);
+                    real w = Mk[s] * hampel_weight(res, ha, hb, hc);
                     for (int i = 0; i < nm; ++i) {
                         for (int j = 0; j < nm; ++j) Hm[i][j] += w * a[i] * a[j];
                         bv[i] += w * a[i] * res;
                     }
                 }
-            double rhs[4], delta[4];
+            real rhs[4], delta[4];
             for (int i = 0; i < nm; ++i) rhs[i] = -bv[i];
             if (!cholesky_solve(nm, Hm, rhs, delta)) { status = OR_SINGULAR; break; }
             dx += delta[0];
             dy += delta[1];
             if (nm == 4) { m += delta[2]; c += delta[3]; }
             ++*iters;
-            if (sqrt(delta[0] * delta[0] + delta[1] * delta[1]) < prm->eps) { converged = 1; break; }
+            if (R(sqrt(delta[0] * delta[0] + delta[1] * delta[1])) < R(prm->eps)) { converged = 1; break; }
         }
         if (status != OR_TRACKED) break;
         if (l > 0) {
@@ -436,9 +459,9 @@ static int track_point(const level_view* P1, const level_view* P2, const oracle_
     free(T);
     free(keep);
     if (status == OR_TRACKED || status == OR_MAXITER) {
-        flow[0] = gx + dx;
-        flow[1] = gy + dy;
-        if (illum) { illum[0] = m; illum[1] = c; }
+        flow[0] = (double)(gx + dx);
+        flow[1] = (double)(gy + dy);
+        if (illum) { illum[0] = (double)m; illum[1] = (double)c; }
     } else {
         flow[0] = flow[1] = 0;
         if (illum) illum[0] = illum[1] = 0;
@@ -494,6 +517,35 @@ done:
     free(pyr1);
     free(pyr2);
     return rc;
+}
+
+/*
+ * Tracking on given pyramids (both in the layout of oracle_pyramid, levels prm->levels,
+ * frame 1 with its gradient planes; frame 2's gradient planes are not read): the same
+ * iteration as oracle_rlof_track_init, for pyramids whose values were rounded to a
+ * storage format (FP16 storage) before tracking.
+ */
+int oracle_rlof_track_pyr(const double* pyr1, const double* pyr2, int W, int H, const double* pts, int n,
+                          const oracle_rlof_params* prm, double* flow, uint8_t* status, int32_t* iters,
+                          double* illum, int nthreads)
+{
+    if (!pyr1 || !pyr2 || W < 1 || H < 1 || n < 0 || (n > 0 && (!pts || !flow || !status)) ||
+        !rlof_params_ok(prm))
+        return -1;
+    level_view v1[12], v2[12];
+    pyramid_views(pyr1, W, H, prm->levels, v1);
+    pyramid_views(pyr2, W, H, prm->levels, v2);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int k = 0; k < n; ++k) {
+        int it = 0;
+        status[k] = (uint8_t)track_point(v1, v2, prm, pts[2 * k], pts[2 * k + 1], NULL, flow + 2 * k,
+                                         illum ? illum + 2 * k : NULL, &it);
+        if (iters) iters[k] = it;
+    }
+    return 0;
 }
 
 int oracle_rlof_track(const double* I1, const double* I2, int W, int H, const double* pts, int n,

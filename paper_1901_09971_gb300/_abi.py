@@ -26,6 +26,7 @@ RLOF_PARAMS_VERSION = 2
 GM_PARAMS_VERSION = 1
 EPIC_PARAMS_VERSION = 1
 EPIC_MAX_K = 256
+DGF_NOALLOC_SCRATCH_BYTES = 24 << 20  # scratch of rlof_track_pair_noalloc
 
 # Every entry point that include/degraf.h declares.
 EXPORTS = (
@@ -35,6 +36,7 @@ EXPORTS = (
     "dgf_degraf_backward_workspace", "degraf_detect_backward", "dgf_rlof_backward_workspace", "rlof_track_backward",
     "dgf_gm_params_default", "dgf_gm_workspace", "rlof_track_gm", "dgf_fb_workspace", "rlof_track_fb",
     "dgf_epic_params_default", "dgf_epic_workspace", "epic_interpolate",
+    "dgf_fp32_probe", "dgf_fp32_probe_flops", "dgf_epic_exp_neg",
 )
 
 
@@ -140,6 +142,9 @@ def load(build_if_missing: bool = True):
     L.epic_interpolate.argtypes = [P, I, I, I, P, P, P, I, ctypes.POINTER(EpicParamsC), P, ctypes.POINTER(EpicDebugC),
                                    P, Z, P]
     L.epic_interpolate.restype = I
+    L.dgf_fp32_probe.argtypes, L.dgf_fp32_probe.restype = [P, I, I, I, I, P], I
+    L.dgf_fp32_probe_flops.argtypes, L.dgf_fp32_probe_flops.restype = [I, I, I, I], ctypes.c_double
+    L.dgf_epic_exp_neg.argtypes, L.dgf_epic_exp_neg.restype = [P, P, I, P], I
     _lib = L
     return L
 

@@ -419,10 +419,18 @@ class DeGraFDetect(torch.autograd.Function):
 class RLOFTrack(torch.autograd.Function):
     """Flow of fixed key-points from frame 1 to frame 2 (float intensities, rounded
     to uint8 for the forward); backward is rlof_track_backward (gradients for both
-    frames, none for the key-points or the parameters). Returns flow and status."""
+    frames, none for the key-points or the parameters). Returns flow and status.
+
+    The key-points must not require grad: the flow's derivative with respect to
+    them is not computed, so a chain such as DeGraFDetect -> RLOFTrack would silently
+    lose the path flow -> key-points -> frame 1. forward raises instead; detach the
+    key-points to differentiate through the frames only."""
 
     @staticmethod
     def forward(ctx, frame1: torch.Tensor, frame2: torch.Tensor, pts: torch.Tensor, params: RlofParams):
+        if pts.requires_grad:
+            raise ValueError("RLOFTrack: the key-points require grad, but the flow's derivative with respect to "
+                             "them is not computed; pass pts.detach() to differentiate through the frames only")
         f1, f2 = _as_u8(frame1), _as_u8(frame2)
         H, W = f1.shape
         pyr1 = build_pyramid(f1, params.levels, params.storage, True)

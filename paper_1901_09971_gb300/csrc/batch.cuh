@@ -68,7 +68,9 @@ struct TrackBatch {
 
 int prepare_params(const dgf_rlof_params* p, TrackBatch& a);
 int check_levels(int W, int H, const dgf_rlof_params* p);
-int launch_track(const TrackBatch& a, const dgf_rlof_params* p, cudaStream_t stream);
+// lanes_set: the lanes-per-point setting to launch with (dgf_rlof_set_lanes; 0 is the
+// automatic choice); -1 reads the current setting.
+int launch_track(const TrackBatch& a, const dgf_rlof_params* p, cudaStream_t stream, int lanes_set = -1);
 int lanes_setting();
 
 }  // namespace dgf

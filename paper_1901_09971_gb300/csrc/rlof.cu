@@ -812,12 +812,11 @@ int launch(const TrackBatch& a, int lanes, cudaStream_t stream)
     return DGF_ERR_ARG;
 }
 
-int choose_lanes(int radius)
+int choose_lanes(int radius, int set)
 {
     // 8 and 16 lanes are built for radius 4 and 5 only; other radii use 32 lanes.
     // Measured on GB300: radius 5 fastest at 16 lanes, radius 4 at 8.
     if (radius != 4 && radius != 5) return 32;
-    const int set = g_lanes_override.load(std::memory_order_relaxed);
     if (set) return set;
     return radius == 5 ? 16 : 8;
 }
@@ -888,10 +887,10 @@ int check_levels(int W, int H, const dgf_rlof_params* p)
 
 int lanes_setting() { return ::rlof_detail::g_lanes_override.load(std::memory_order_relaxed); }
 
-int launch_track(const TrackBatch& a, const dgf_rlof_params* p, cudaStream_t stream)
+int launch_track(const TrackBatch& a, const dgf_rlof_params* p, cudaStream_t stream, int lanes_set)
 {
     using namespace ::rlof_detail;
-    const int lanes = choose_lanes(p->radius);
+    const int lanes = choose_lanes(p->radius, lanes_set >= 0 ? lanes_set : lanes_setting());
     if (p->storage == DGF_F32)
         return p->model == 4 ? launch<float, 4>(a, lanes, stream) : launch<float, 2>(a, lanes, stream);
     return p->model == 4 ? launch<__half, 4>(a, lanes, stream) : launch<__half, 2>(a, lanes, stream);

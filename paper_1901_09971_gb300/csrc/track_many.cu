@@ -62,7 +62,7 @@ struct Fork {
 };
 
 int enqueue(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p, const PairPlan* plans, char* ws,
-            int stages, cudaStream_t stream, const Fork& fk = Fork())
+            int stages, int lanes_set, cudaStream_t stream, const Fork& fk = Fork())
 {
     for (int c0 = 0; c0 < n_pairs; c0 += dgf::kMaxBatchPairs) {
         const int cn = n_pairs - c0 < dgf::kMaxBatchPairs ? n_pairs - c0 : dgf::kMaxBatchPairs;
@@ -127,7 +127,7 @@ int enqueue(const dgf_pair* pairs, int n_pairs, const dgf_rlof_params* p, const 
         }
         if (total > 0x7fffffffLL) return DGF_ERR_ARG;
         t.total = (int)total;
-        if (total > 0 && (rc = dgf::launch_track(t, p, stream)) != DGF_OK) return rc;
+        if (total > 0 && (rc = dgf::launch_track(t, p, stream, lanes_set)) != DGF_OK) return rc;
     }
     return DGF_OK;
 }
@@ -228,15 +228,17 @@ extern "C" int rlof_track_many(const dgf_pair* pairs, int n_pairs, const dgf_rlo
         delete[] plans;
         return DGF_ERR_CUDA;
     }
+    // the lanes setting is read once: the graph key and the launches use the same value
+    const int lanes_set = dgf::lanes_setting();
     if (!use_graph || cap != cudaStreamCaptureStatusNone) {  // plain launches (also inside a caller's capture)
-        rc = enqueue(pairs, n_pairs, p, plans, ws, stages, stream);
+        rc = enqueue(pairs, n_pairs, p, plans, ws, stages, lanes_set, stream);
         delete[] plans;
         return rc;
     }
     int dev = 0;
     cudaGetDevice(&dev);
     const std::string key =
-        graph_key(pairs, n_pairs, p, ws, dev, stages, dgf::lanes_setting());  // the lanes setting is baked in too
+        graph_key(pairs, n_pairs, p, ws, dev, stages, lanes_set);  // the lanes setting is baked in too
     GraphCache& C = cache();
     std::lock_guard<std::mutex> lock(C.mu);
     auto it = C.map.find(key);
@@ -248,7 +250,7 @@ extern "C" int rlof_track_many(const dgf_pair* pairs, int n_pairs, const dgf_rlo
             delete[] plans;
             return DGF_ERR_CUDA;
         }
-        rc = enqueue(pairs, n_pairs, p, plans, ws, stages, cs, capture_fork(dev));
+        rc = enqueue(pairs, n_pairs, p, plans, ws, stages, lanes_set, cs, capture_fork(dev));
         const cudaError_t e = cudaStreamEndCapture(cs, &g);
         delete[] plans;
         if (rc != DGF_OK || e != cudaSuccess) {
@@ -320,5 +322,5 @@ extern "C" int rlof_track_pair_noalloc(const dgf_pair* pair, const dgf_rlof_para
     if (cudaGetDevice(&dev) != cudaSuccess) return DGF_ERR_CUDA;
     char* ws = static_cast<char*>(scratch_address(dev));
     if (!ws) return DGF_ERR_CUDA;
-    return enqueue(pair, 1, p, &plan1, ws, DGF_STAGE_ALL, stream);
+    return enqueue(pair, 1, p, &plan1, ws, DGF_STAGE_ALL, dgf::lanes_setting(), stream);
 }

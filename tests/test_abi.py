@@ -296,3 +296,33 @@ def test_product_package_never_loads_the_oracle():
         for f in files:
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 assert "oracle" not in open(os.path.join(dirpath, f)).read().lower(), f
+
+
+def test_probe_host_checks_and_flop_count():
+    """The measurement probes reject bad sizes before any launch; the FP32 probe's FLOP
+    count is 2 per FMA: 8 chains x 8 steps per trip, two FMAs per packed lane."""
+    lib = dgf.load()
+    assert lib.dgf_fp32_probe(None, 1, 256, 1, 1, None) == _abi.DGF_ERR_ARG
+    assert lib.dgf_fp32_probe(ctypes.c_void_p(16), 1, 300, 1, 1, None) == _abi.DGF_ERR_ARG
+    assert lib.dgf_fp32_probe(ctypes.c_void_p(16), 1, 48, 1, 1, None) == _abi.DGF_ERR_ARG
+    assert lib.dgf_fp32_probe_flops(3, 256, 10, 0) == 2 * 64 * 10 * 256 * 3
+    assert lib.dgf_fp32_probe_flops(3, 256, 10, 1) == 4 * 64 * 10 * 256 * 3
+    assert lib.dgf_epic_exp_neg(None, None, -1, None) == _abi.DGF_ERR_ARG
+    assert lib.dgf_epic_exp_neg(None, None, 5, None) == _abi.DGF_ERR_ARG
+    assert lib.dgf_epic_exp_neg(None, None, 0, None) == _abi.DGF_OK
+
+
+def test_noalloc_scratch_size_matches_the_header():
+    text = open(HEADER).read()
+    m = re.search(r"#define DGF_NOALLOC_SCRATCH_BYTES \((\d+)u << (\d+)\)", text)
+    assert m and int(m.group(1)) << int(m.group(2)) == _abi.DGF_NOALLOC_SCRATCH_BYTES
+
+
+def test_rlof_track_function_rejects_keypoints_that_require_grad():
+    """The flow's derivative with respect to the key-points is not computed, so the
+    autograd Function refuses key-points that require grad (before any launch)."""
+    import torch
+    f = torch.zeros((64, 64))
+    pts = torch.zeros((3, 2), requires_grad=True)
+    with pytest.raises(ValueError, match="key-points require grad"):
+        dgf.RLOFTrack.apply(f, f, pts, dgf.RlofParams(levels=2, radius=3))

@@ -6,12 +6,11 @@ import numpy as np
 import pytest
 import torch
 
+import fp32_spread as fs
 import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
-
-TOL_FLOW = 1e-2
 
 
 @pytest.fixture(scope="module")
@@ -74,12 +73,8 @@ def test_batch_equals_single_pair_path_and_oracle(dgf, use_graph):
         pts_o, _, _ = oracle.degraf_detect(I1, win, win, step)
         pts = bt.pts[i].cpu().numpy()
         assert pts.shape == pts_o.shape and np.abs(pts - pts_o).max() <= 1e-4
-        fo, so, _, _ = oracle.rlof_track(I1, I2, pts.astype(np.float64), oprm)
         sg, fg = bt.status[i].cpu().numpy(), bt.flow[i].cpu().numpy()
-        both = (sg == 0) & (so == 0)
-        e = np.hypot(*(fg.astype(np.float64) - fo).T)
-        assert np.mean(sg == so) >= 0.99
-        assert np.mean(e[both] <= TOL_FLOW) >= 0.999
+        fs.check(fg, sg, fs.frames_spread(I1, I2, pts.astype(np.float64), oprm), f"pair {i}")
 
 
 def test_graph_replay_sees_new_frame_contents(dgf):
@@ -133,7 +128,7 @@ def test_more_pairs_than_one_chunk(dgf):
 def test_mixed_size_batch_of_64_pairs(dgf):
     """The mixed-size batch workload: 64 pairs of 640x480 .. 1280x720, steps 2..6,
     window 8, 3 levels, 9x9 support; every pair equals the single-pair path, and
-    sampled points of four pairs are checked against the oracle."""
+    4,000 sampled points of each of four pairs meet the oracle bars."""
     specs = [(W, H, 8, step) for (W, H, step) in synth.make_batch_specs(64, 3000)]
     frames = []
     for i, (W, H, win, step) in enumerate(specs):
@@ -147,36 +142,31 @@ def test_mixed_size_batch_of_64_pairs(dgf):
     rng = np.random.default_rng(0)
     for i in (0, 17, 42, 63):
         I1, I2 = frames[i]
-        idx = rng.choice(bt.n[i], size=min(400, bt.n[i]), replace=False)
+        idx = np.sort(rng.choice(bt.n[i], size=min(4000, bt.n[i]), replace=False))
         pts = bt.pts[i].cpu().numpy()[idx]
-        fo, so, _, _ = oracle.rlof_track(I1, I2, pts.astype(np.float64), oprm)
         sg, fg = bt.status[i].cpu().numpy()[idx], bt.flow[i].cpu().numpy()[idx]
-        both = (sg == 0) & (so == 0)
-        e = np.hypot(*(fg.astype(np.float64) - fo).T)
-        assert np.mean(sg == so) >= 0.98
-        assert np.mean(e[both] <= TOL_FLOW) >= 0.99
+        fs.check(fg, sg, fs.frames_spread(I1, I2, pts.astype(np.float64), oprm), f"batch pair {i}")
 
 
 def test_autotune_picks_a_shape_and_every_shape_tracks_alike(dgf, tmp_path, monkeypatch):
     """The autotuner times every lane count the library honours at radius 4, keeps
     the fastest for the tracker and in its cache (which lanes="auto" then reads);
-    every shape tracks the batch like the library's default within the tracking
-    bars (the shapes sum the normal equations in different orders, so FP32
-    trajectories may part at a threshold)."""
+    every shape meets the oracle bars on every pair of the batch (the shapes sum the
+    normal equations in different orders, so FP32 trajectories may part where an
+    FP32 restatement of the oracle's also does)."""
     monkeypatch.setenv("DGF_TUNE_CACHE", str(tmp_path / "tune.json"))
     prm = dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)
     frames = frames_for(SMALL_SPECS, 500)
     bt, d1, d2 = run_batch(dgf, SMALL_SPECS, frames, prm, True)
-    ref = [(f.cpu().numpy().copy(), s.cpu().numpy().copy()) for f, s in zip(bt.flow, bt.status)]
     rec = bt.autotune(reps=2)
     assert rec["lanes"] in (8, 16, 32) and set(rec["ms"]) == {"8", "16", "32"} and bt.lanes == rec["lanes"]
     assert dgf.BatchTracker(SMALL_SPECS, prm, lanes="auto").lanes == rec["lanes"]
+    oprm = oracle.RlofParams(levels=3, radius=4, max_iter=30, model=4)
+    spreads = [fs.frames_spread(I1, I2, bt.pts[i].cpu().numpy().astype(np.float64), oprm)
+               for i, (I1, I2) in enumerate(frames)]
     for lanes in (8, 16, 32):
         bt.lanes = lanes
         bt.run()
         torch.cuda.synchronize()
-        for i, (fr, sr) in enumerate(ref):
-            f, s = bt.flow[i].cpu().numpy(), bt.status[i].cpu().numpy()
-            assert np.mean(s == sr) >= 0.995, (lanes, i)
-            both = (s == 0) & (sr == 0)
-            assert np.mean(np.abs(f[both] - fr[both]).max(axis=1) <= 1e-2) >= 0.999, (lanes, i)
+        for i, sp in enumerate(spreads):
+            fs.check(bt.flow[i].cpu().numpy(), bt.status[i].cpu().numpy(), sp, f"lanes {lanes} pair {i}")

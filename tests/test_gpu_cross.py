@@ -1,12 +1,14 @@
 """GPU parity of the adaptive cross-based support (dgf_rlof_params.cross_tau > 0)
 against the oracle's reading (Section 3 "Parameters"): the masks are formed from
 exact pyramid values on both sides, so the tracking bars of the square support
-apply unchanged; a huge tau reproduces the square-support kernel; and at a motion
-boundary the GPU tracks the foreground as the oracle does."""
+(derived from FP32 restatements of the oracle) apply unchanged; a huge tau
+reproduces the square-support kernel; and at a motion boundary the GPU tracks the
+foreground as the oracle does."""
 import numpy as np
 import pytest
 import torch
 
+import fp32_spread as fs
 import oracle
 import synth
 from test_oracle_cross import RECT, two_region_frame
@@ -38,33 +40,22 @@ def track_gpu(dgf, I1, I2, pts, prm):
     return f.cpu().numpy(), st.cpu().numpy()
 
 
-def bars(fg, sg, fo, so, agree_min, within_min):
-    agree = np.mean(sg == so)
-    both = (sg == oracle.TRACKED) & (so == oracle.TRACKED)
-    e = np.hypot(*(fg.astype(np.float64) - fo).T)
-    within = np.mean(e[both] <= TOL_FLOW) if both.any() else 1.0
-    print(f"status agree {agree:.5f}, both tracked {both.sum()}, within {TOL_FLOW}: {within:.5f}")
-    assert agree >= agree_min and within >= within_min
+# Smaller supports are worse conditioned, so FP32 and FP64 trajectories part ways
+# more often (tau 8 on the driving-scene pair: an FP32 restatement of the oracle,
+# with the same masks by construction, changes the status of about 7.5% of the
+# points); the bars come from that restatement's spread on the same inputs.
+CROSS_CASES = [(1, 20.0), (2, 20.0), (2, 8.0)]
 
 
-# Bars per (workload, tau). Smaller supports are worse conditioned, so FP32 and FP64
-# trajectories part ways more often: an FP32 restatement of the oracle (same masks by
-# construction) agrees with FP64 on 99.90% / 98.55% / 92.41% of statuses and on 100% /
-# 99.76% / 97.83% of both-tracked flows within 1e-2 px for these three cases; the bars
-# sit just below those figures.
-CROSS_BARS = {(1, 20.0): (0.998, 0.999), (2, 20.0): (0.98, 0.995), (2, 8.0): (0.91, 0.97)}
-
-
-@pytest.mark.parametrize("config,tau", list(CROSS_BARS))
+@pytest.mark.parametrize("config,tau", CROSS_CASES)
 def test_cross_workloads_parity(dgf, config, tau):
     p = synth.make_pair(config)
     pts, _, _ = oracle.degraf_detect(p.I1, p.win, p.win, p.step)
     pts = pts.astype(np.float32).astype(np.float64)
     prm = dgf.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4, cross_tau=tau)
     fg, sg = track_gpu(dgf, p.I1, p.I2, pts, prm)
-    fo, so, _, _ = oracle.rlof_track(p.I1, p.I2, pts, oracle.RlofParams(levels=p.levels, radius=p.radius,
-                                                                       max_iter=p.max_iter, model=4, cross_tau=tau))
-    bars(fg, sg, fo, so, *CROSS_BARS[(config, tau)])
+    oprm = oracle.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4, cross_tau=tau)
+    fs.check(fg, sg, fs.frames_spread(p.I1, p.I2, pts, oprm), f"workload {config} tau {tau}")
 
 
 def test_huge_tau_reproduces_the_square_support_kernel(dgf):

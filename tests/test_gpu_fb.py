@@ -1,19 +1,20 @@
 """GPU parity of the forward-backward consistency filter (rlof_track_fb) against the
-oracle's composition of two tracking passes: statuses (with FB_REJECTED) agree
-within the tracking bars, round-trip errors agree within twice the flow tolerance
-where both sides tracked both ways, identical frames give an error of exactly 0,
-and the occluding patch is rejected as in the oracle."""
+oracle's composition of two tracking passes: statuses (with FB_REJECTED) and
+round-trip errors (within twice the flow tolerance where both sides have one)
+meet bars derived from FP32 restatements of the oracle (tests/fp32_spread.py),
+identical frames give an error of exactly 0, and the occluding patch is rejected
+as in the oracle."""
 import numpy as np
 import pytest
 import torch
 
+import fp32_spread
 import oracle
 import synth
 from test_oracle_fb import PATCH, PRM, T, occlusion_pair
 
 pytestmark = pytest.mark.gpu
 
-TOL_FLOW = 1e-2
 
 
 @pytest.fixture(scope="module")
@@ -44,37 +45,21 @@ def run_fb(dgf, I1, I2, pts, levels, radius, fb_max, model=4, storage=0):
     return f.cpu().numpy(), s.cpu().numpy(), e.cpu().numpy(), ws[off:off + n].cpu().numpy()
 
 
-def compare_errors(I1, I2, pts, prm_o, fg, sg, eg, bg, within_min):
-    """Round-trip errors where both sides converged (TRACKED) in both passes (MAXITER
-    points have not converged, so their FP32 and FP64 flows need not agree)."""
-    fo, so, _, _ = oracle.rlof_track(I1, I2, pts, prm_o)
-    bo, sbo, _, _ = oracle.rlof_track(I2, I1, pts + fo, prm_o)
-    eo = np.hypot(*(fo + bo).T)
-    conv = (sg == oracle.TRACKED) & (so == oracle.TRACKED) & (bg == oracle.TRACKED) & (sbo == oracle.TRACKED)
-    within = np.mean(np.abs(eg[conv].astype(np.float64) - eo[conv]) <= 2 * TOL_FLOW)
-    print(f"round-trip errors within {2 * TOL_FLOW}: {within:.5f} of {conv.sum()} converged both ways")
-    assert within >= within_min
-
-
 def test_fb_occlusion_pair_parity(dgf):
     I1, I2 = occlusion_pair()
     pts, _, _ = oracle.degraf_detect(I1, 8, 8, 4)
     pts = pts.astype(np.float32).astype(np.float64)
-    fg, sg, eg, bg = run_fb(dgf, I1, I2, pts, 3, 4, 1.0)
-    fo, so, eo = oracle.rlof_track_fb(I1, I2, pts, PRM, 1.0)
     q = pts + np.array(T)
     x0, y0, x1, y1 = PATCH
     on_patch = (q[:, 0] >= x0 - 1) & (q[:, 0] < x1 + 1) & (q[:, 1] >= y0 - 1) & (q[:, 1] < y1 + 1)
-    near = (q[:, 0] >= x0 - 6) & (q[:, 0] < x1 + 6) & (q[:, 1] >= y0 - 6) & (q[:, 1] < y1 + 6)
-    # points landing on fresh texture converge to arbitrary places, differently in FP32
-    # and FP64; the visible points carry the bar
-    agree, agree_vis = np.mean(sg == so), np.mean(sg[~near] == so[~near])
-    print(f"status agree (with rejections): all {agree:.5f}, visible {agree_vis:.5f}")
-    assert agree >= 0.98 and agree_vis >= 0.995
-    fwd = np.isin(sg, [oracle.TRACKED, oracle.MAXITER, oracle.FB_REJECTED])
-    assert np.mean(sg[fwd & on_patch] == oracle.FB_REJECTED) >= 0.95
-    fg, sg, eg, bg = run_fb(dgf, I1, I2, pts, 3, 4, 0.0)
-    compare_errors(I1, I2, pts, PRM, fg, sg, eg, bg, 0.999)
+    for fb_max in (1.0, 0.0):
+        fg, sg, eg, _ = run_fb(dgf, I1, I2, pts, 3, 4, fb_max)
+        # points landing on the patch's fresh texture converge to arbitrary places,
+        # differently in FP32 and FP64: the FP32 ensemble shows how often
+        fp32_spread.check_fb(sg, eg, fp32_spread.fb_spread(I1, I2, pts, PRM, fb_max), f"occlusion pair fb_max {fb_max}")
+        if fb_max > 0:
+            fwd = np.isin(sg, [oracle.TRACKED, oracle.MAXITER, oracle.FB_REJECTED])
+            assert np.mean(sg[fwd & on_patch] == oracle.FB_REJECTED) >= 0.95
 
 
 def test_fb_driving_scene_parity(dgf):
@@ -82,13 +67,8 @@ def test_fb_driving_scene_parity(dgf):
     pts, _, _ = oracle.degraf_detect(p.I1, p.win, p.win, p.step)
     pts = pts.astype(np.float32).astype(np.float64)
     prm_o = oracle.RlofParams(levels=p.levels, radius=p.radius, model=4)
-    fg, sg, eg, bg = run_fb(dgf, p.I1, p.I2, pts, p.levels, p.radius, 1.0)
-    _, so, _ = oracle.rlof_track_fb(p.I1, p.I2, pts, prm_o, 1.0)
-    agree = np.mean(sg == so)
-    print(f"status agree (with rejections) {agree:.5f}")
-    assert agree >= 0.98
-    fg, sg, eg, bg = run_fb(dgf, p.I1, p.I2, pts, p.levels, p.radius, 0.0)
-    compare_errors(p.I1, p.I2, pts, prm_o, fg, sg, eg, bg, 0.995)
+    fg, sg, eg, _ = run_fb(dgf, p.I1, p.I2, pts, p.levels, p.radius, 1.0)
+    fp32_spread.check_fb(sg, eg, fp32_spread.fb_spread(p.I1, p.I2, pts, prm_o, 1.0), "driving scene fb_max 1")
 
 
 def test_fb_identical_frames_zero_error(dgf):
@@ -100,18 +80,15 @@ def test_fb_identical_frames_zero_error(dgf):
 
 
 def test_fb_fp16_storage(dgf):
-    """FP16 pyramid storage: the filter's statuses stay close to the FP64 oracle's and
-    the occluding patch is still rejected."""
+    """FP16 pyramid storage: the filter meets the FP32 path's bars against the FP64
+    oracle, and the occluding patch is still rejected."""
     I1, I2 = occlusion_pair()
     pts, _, _ = oracle.degraf_detect(I1, 8, 8, 4)
     pts = pts.astype(np.float32).astype(np.float64)
     fg, sg, eg, _ = run_fb(dgf, I1, I2, pts, 3, 4, 1.0, storage=dgf.F16)
-    _, so, _ = oracle.rlof_track_fb(I1, I2, pts, PRM, 1.0)
+    fp32_spread.check_fb(sg, eg, fp32_spread.fb_spread(I1, I2, pts, PRM, 1.0), "occlusion pair FP16 storage")
     q = pts + np.array(T)
     x0, y0, x1, y1 = PATCH
     on_patch = (q[:, 0] >= x0 - 1) & (q[:, 0] < x1 + 1) & (q[:, 1] >= y0 - 1) & (q[:, 1] < y1 + 1)
     fwd = np.isin(sg, [oracle.TRACKED, oracle.MAXITER, oracle.FB_REJECTED])
-    agree = np.mean(sg == so)
-    print(f"fp16 storage: status agree {agree:.4f}, patch rejected {np.mean(sg[fwd & on_patch] == oracle.FB_REJECTED):.3f}")
-    assert agree >= 0.97
     assert np.mean(sg[fwd & on_patch] == oracle.FB_REJECTED) >= 0.95

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 import torch
 
+import fp32_spread
 import oracle
 import synth
 
@@ -29,13 +30,10 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def bars(fg, sg, fo, so, agree_min=0.99, within_min=0.999):
-    agree = np.mean(sg == so)
-    both = (sg == oracle.TRACKED) & (so == oracle.TRACKED)
-    e = np.hypot(*(fg.astype(np.float64) - fo).T)
-    within = np.mean(e[both] <= TOL_FLOW) if both.any() else 1.0
-    assert agree >= agree_min and within >= within_min, (agree, within, both.sum())
-    return agree, within
+def bars(fg, sg, I1, I2, pts64, oprm, label, init_flow=None):
+    """The tracking bars (derived from FP32 restatements of the oracle, see
+    tests/fp32_spread.py) for a pass started from init_flow."""
+    return fp32_spread.check(fg, sg, fp32_spread.frames_spread(I1, I2, pts64, oprm, init_flow=init_flow), label)
 
 
 def run_gm(dgf, p, pts32, prm, gm):
@@ -68,8 +66,7 @@ def test_gm_large_motion_parity_and_quality(dgf):
     deep = oracle.RlofParams(levels=3 + gm.extra_levels, radius=4, model=4)
     sub = pts64[::gm.stride]
     # first pass against the oracle on the same points and deeper pyramid
-    fo1, so1, _, _ = oracle.rlof_track(p.I1, p.I2, sub, deep)
-    print("first pass", bars(sub_flow, sub_status, fo1, so1))
+    bars(sub_flow, sub_status, p.I1, p.I2, sub, deep, "first pass")
     # the fit on the GPU's first-pass tracks
     a_o, made_o = oracle.gm_fit_affine(sub, sub_flow, sub_status, gm.iters, gm.c0, gm.c_min)
     assert made_o
@@ -77,8 +74,7 @@ def test_gm_large_motion_parity_and_quality(dgf):
     print(f"affine: GPU {a}, oracle {a_o}, prior difference {d:.2e} px")
     assert d < 1e-6
     # main pass against the oracle started from the same prior
-    fo, so, _, _ = oracle.rlof_track(p.I1, p.I2, pts64, oprm, init_flow=oracle.gm_prior_flow(a, pts64))
-    print("main pass", bars(fg, sg, fo, so))
+    bars(fg, sg, p.I1, p.I2, pts64, oprm, "main pass", init_flow=oracle.gm_prior_flow(a, pts64))
     # the two-pass oracle reaches the same motion
     _, _, _, _, a2, made2 = oracle.rlof_track_gm(p.I1, p.I2, pts64, oprm)
     assert made2 and np.abs(oracle.gm_prior_flow(a, pts64) - oracle.gm_prior_flow(a2, pts64)).max() < 0.05
@@ -108,11 +104,8 @@ def test_gm_workloads_parity(dgf, config, extra):
     assert made == 1
     oprm = oracle.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4)
     pts64 = pts32.astype(np.float64)
-    fo, so, _, _ = oracle.rlof_track(p.I1, p.I2, pts64, oprm, init_flow=oracle.gm_prior_flow(a, pts64))
-    if config == 1:
-        print(bars(fg, sg, fo, so, agree_min=0.998, within_min=1.0))
-    else:
-        print(bars(fg, sg, fo, so))
+    bars(fg, sg, p.I1, p.I2, pts64, oprm, f"workload {config} with the prior",
+         init_flow=oracle.gm_prior_flow(a, pts64))
 
 
 def test_gm_without_a_fit_is_plain_tracking(dgf):
@@ -148,14 +141,13 @@ def test_gm_with_cross_support_driving_scene(dgf):
     assert made_o
     assert np.abs(oracle.gm_prior_flow(a, pts64) - oracle.gm_prior_flow(a_o, pts64)).max() < 1e-6
     oprm = oracle.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4, cross_tau=tau)
-    fo, so, _, _ = oracle.rlof_track(p.I1, p.I2, pts64, oprm, init_flow=oracle.gm_prior_flow(a, pts64))
-    print("gm + cross", bars(fg, sg, fo, so, agree_min=0.98, within_min=0.995))
+    bars(fg, sg, p.I1, p.I2, pts64, oprm, "prior + cross support", init_flow=oracle.gm_prior_flow(a, pts64))
 
 
 def test_gm_fp16_storage(dgf):
     """FP16 pyramid storage with the prior on the 256x128 pair: the fitted motion is
-    within 0.01 px of the FP32-storage fit and the main pass stays close to the
-    oracle run from the same prior."""
+    within 0.01 px of the FP32-storage fit and the main pass meets the FP32 path's
+    bars against the FP64 oracle run from the same prior."""
     p = synth.make_pair(1)
     pts, _, _ = oracle.degraf_detect(p.I1, p.win, p.win, p.step)
     pts32 = pts.astype(np.float32)
@@ -171,8 +163,4 @@ def test_gm_fp16_storage(dgf):
     assert res[dgf.F16][3] == 1 and d < 0.01
     fg, sg = res[dgf.F16][0], res[dgf.F16][1]
     oprm = oracle.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4)
-    fo, so, _, _ = oracle.rlof_track(p.I1, p.I2, pts64, oprm, init_flow=oracle.gm_prior_flow(a16, pts64))
-    both = (sg == oracle.TRACKED) & (so == oracle.TRACKED)
-    e = np.hypot(*(fg.astype(np.float64) - fo).T)[both]
-    print(f"fp16 main pass: status agree {np.mean(sg == so):.4f}, median EPE vs oracle {np.median(e):.2e} px")
-    assert np.mean(sg == so) >= 0.97 and np.median(e) < 0.05
+    bars(fg, sg, p.I1, p.I2, pts64, oprm, "FP16 storage main pass", init_flow=oracle.gm_prior_flow(a16, pts64))

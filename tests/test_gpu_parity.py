@@ -3,15 +3,19 @@ seeded inputs.
 
 Bars: bit-exact integer window sums, key-point count and order; key-points within
 1e-4 px; FP32 pyramid bit-exact, FP16 pyramid equal to the oracle value rounded to
-FP16; tracked flow within 1e-2 px endpoint error on points that converge
-(TRACKED) on both sides, with status agreement and the converged-point fraction
-within tolerance asserted per workload (an iterative, discontinuous method can
-take another branch on a few FP32 trajectories; those are counted and printed).
+FP16; tracked flow within 1e-2 px of the FP64 oracle on the points TRACKED or
+MAXITER on both sides, and the same statuses, except where an FP32 restatement of
+the oracle also parts from FP64: the number of disagreements of each kind is
+bounded by what an ensemble of FP32 restatements shows on the same inputs, most of
+the GPU's disagreements must be points where that ensemble disagrees too, and the
+bulk of the tracked points must be as close to FP64 as the restatement's
+(tests/fp32_spread.py states the bars).
 """
 import numpy as np
 import pytest
 import torch
 
+import fp32_spread as fs
 import golden
 import oracle
 import synth
@@ -135,15 +139,7 @@ def test_pyramid_parity(dgf, size, levels, storage):
 
 # ----------------------------------------------------------------- tracking
 
-def compare_tracks(flow_g, st_g, flow_o, st_o):
-    """Return (status agreement, converged-both mask, endpoint error per point)."""
-    agree = np.mean(st_g == st_o)
-    both = (st_g == oracle.TRACKED) & (st_o == oracle.TRACKED)
-    e = np.hypot(*(flow_g.astype(np.float64) - flow_o).T)
-    return agree, both, e
-
-
-def run_both(dgf, I1, I2, pts64, prm_o, storage=0, lanes=0):
+def run_gpu(dgf, I1, I2, pts64, prm_o, storage=0, lanes=0):
     H, W = I1.shape
     prm = dgf.RlofParams(levels=prm_o.levels, radius=prm_o.radius, max_iter=prm_o.max_iter,
                          model=prm_o.model, storage=storage, eps=prm_o.eps, hampel_a=prm_o.hampel_a,
@@ -157,36 +153,41 @@ def run_both(dgf, I1, I2, pts64, prm_o, storage=0, lanes=0):
         torch.cuda.synchronize()
     finally:
         dgf.set_lanes(prev)
-    fo, so, io, lo = oracle.rlof_track(I1, I2, pts32.astype(np.float64), prm_o)
-    return (flow.cpu().numpy(), st.cpu().numpy(), it.cpu().numpy(), il.cpu().numpy()), (fo, so, io, lo)
+    return flow.cpu().numpy(), st.cpu().numpy(), it.cpu().numpy(), il.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def workload_spreads():
+    """FP64 oracle results and FP32 spreads of the two workloads, per model."""
+    cache = {}
+
+    def get(config, model):
+        if (config, model) not in cache:
+            p = synth.make_pair(config)
+            pts, _, _ = oracle.degraf_detect(p.I1, p.win, p.win, p.step)
+            pts = pts.astype(np.float32).astype(np.float64)
+            prm = oracle.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=model)
+            cache[(config, model)] = (p, pts, prm, fs.frames_spread(p.I1, p.I2, pts, prm))
+        return cache[(config, model)]
+    return get
 
 
 @pytest.mark.parametrize("config,model,lanes", [(1, 4, 0), (1, 2, 0), (1, 4, 16), (1, 4, 32),
                                                 (2, 4, 0), (2, 2, 0)])
-def test_track_parity_workloads(dgf, config, model, lanes):
-    p = synth.make_pair(config)
-    pts, _, _ = oracle.degraf_detect(p.I1, p.win, p.win, p.step)
-    prm = oracle.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=model)
-    (fg, sg, ig, lg), (fo, so, io, lo) = run_both(dgf, p.I1, p.I2, pts, prm, lanes=lanes)
-    agree, both, e = compare_tracks(fg, sg, fo, so)
-    within = np.mean(e[both] <= TOL_FLOW)
-    bad = np.flatnonzero(both & (e > TOL_FLOW))
-    print(f"workload {config} model {model}: status agree {agree:.5f}, converged both {both.sum()}, "
-          f"within {TOL_FLOW}: {within:.5f}, mismatches {bad[:10]} epe {e[bad[:10]]}")
-    if config == 1:
-        # the final status is a discontinuous function of rounding at the stopping
-        # rule and the iteration cap: an FP32 restatement of the oracle already
-        # flips 0.05-0.5% of statuses against FP64, so 3 of 1,953 may differ
-        assert agree >= 0.998 and within == 1.0
-    else:
-        assert agree >= 0.99 and within >= 0.999
+def test_track_parity_workloads(dgf, workload_spreads, config, model, lanes):
+    p, pts, prm, sp = workload_spreads(config, model)
+    fg, sg, ig, lg = run_gpu(dgf, p.I1, p.I2, pts, prm, lanes=lanes)
+    fs.check(fg, sg, sp, f"workload {config} model {model} lanes {lanes}")
     # the lost-point outputs are zero on the GPU as in the oracle
     lost = (sg != oracle.TRACKED) & (sg != oracle.MAXITER)
     assert np.all(fg[lost] == 0)
     if model == 4:
-        # illumination (gain m, offset c in intensity levels) on the points whose flow
-        # agrees: the stopping rule bounds only the flow update, so c is looser
-        ok = both & (e <= TOL_FLOW)
+        # illumination (gain m, offset c in intensity levels) on the points TRACKED on
+        # both sides whose flows agree: the stopping rule bounds only the flow update,
+        # so c is looser
+        _, _, _, lo = oracle.rlof_track(p.I1, p.I2, pts, prm)
+        e = np.hypot(*(fg.astype(np.float64) - sp.flow64).T)
+        ok = (sg == oracle.TRACKED) & (sp.status64 == oracle.TRACKED) & (e <= fs.TOL_FLOW)
         assert np.abs(lg[ok, 0] - lo[ok, 0]).max() < 5e-3
         assert np.abs(lg[ok, 1] - lo[ok, 1]).max() < 0.5
 
@@ -200,34 +201,35 @@ def test_track_parity_shapes(dgf, radius, levels, n, model):
     W, H = 640, 480
     p = synth.make_translation_pair(W, H, t=(2.5, -1.75), seed=radius * 10 + levels, noise_sigma=0.0)
     rng = np.random.default_rng(n)
-    pts = np.stack([rng.uniform(0, W - 1, n), rng.uniform(0, H - 1, n)], 1)
+    pts = np.stack([rng.uniform(0, W - 1, n), rng.uniform(0, H - 1, n)], 1).astype(np.float32).astype(np.float64)
     prm = oracle.RlofParams(levels=levels, radius=radius, model=model)
-    (fg, sg, _, _), (fo, so, _, _) = run_both(dgf, p.I1, p.I2, pts, prm)
-    agree, both, e = compare_tracks(fg, sg, fo, so)
-    assert np.sum(sg != so) <= max(1, 0.01 * n)
-    assert np.sum(e[both] > TOL_FLOW) <= max(1, 0.01 * both.sum())
+    fg, sg, _, _ = run_gpu(dgf, p.I1, p.I2, pts, prm)
+    fs.check(fg, sg, fs.frames_spread(p.I1, p.I2, pts, prm), f"radius {radius} levels {levels} n {n}")
 
 
 @pytest.mark.parametrize("config", [1, 4])
-def test_track_fp16_storage_error(dgf, config):
-    """FP16 storage: endpoint error against the FP64 oracle is reported beside the
-    FP32-storage error on the same points (no fixed bar; the converged points must
-    stay close)."""
+def test_track_fp16_storage(dgf, config):
+    """FP16 storage: against the FP64 oracle on exact pyramids the FP16-storage path
+    meets the FP32 path's bars (the same spread, so no looser), and against the oracle
+    run on the FP16-rounded pyramids it meets that computation's FP32 spread; the
+    endpoint error of both storages against FP64 is printed."""
     p = synth.make_pair(config)
     pts, _, _ = oracle.degraf_detect(p.I1, p.win, p.win, p.step)
     if config == 4:
-        pts = pts[::7]  # a sample of the 1242x375 pair keeps the oracle fast
-    prm = oracle.RlofParams(levels=p.levels, radius=p.radius, model=4)
+        pts = pts[::3]  # a third of the 1242x375 pair keeps the oracle ensembles fast
+    pts = pts.astype(np.float32).astype(np.float64)
+    prm = oracle.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4)
+    sp = fs.frames_spread(p.I1, p.I2, pts, prm)
     res = {}
     for storage in (0, 1):
-        (fg, sg, _, _), (fo, so, _, _) = run_both(dgf, p.I1, p.I2, pts, prm, storage=storage)
-        agree, both, e = compare_tracks(fg, sg, fo, so)
-        res[storage] = (agree, both, e)
-        print(f"workload {config} storage {'f16' if storage else 'f32'}: status agree {agree:.4f}, "
-              f"EPE vs FP64 oracle on converged points: mean {e[both].mean():.2e} median {np.median(e[both]):.2e} "
-              f"p99 {np.percentile(e[both], 99):.2e} max {e[both].max():.2e}")
-    agree, both, e = res[1]
-    assert agree >= 0.97 and np.median(e[both]) < 0.05
+        fg, sg, _, _ = run_gpu(dgf, p.I1, p.I2, pts, prm, storage=storage)
+        res[storage] = fs.check(fg, sg, sp, f"workload {config} storage {'f16' if storage else 'f32'} vs FP64")
+    sp16 = fs.pyramids_spread(fs.fp16_pyramid(p.I1, p.levels), fs.fp16_pyramid(p.I2, p.levels), p.W, p.H, pts, prm)
+    fs.check(fg, sg, sp16, f"workload {config} storage f16 vs the oracle on FP16-rounded pyramids")
+    both = (sg == oracle.TRACKED) & (sp.status64 == oracle.TRACKED)
+    e = np.hypot(*(fg.astype(np.float64) - sp.flow64).T)[both]
+    print(f"workload {config} FP16 storage vs FP64: mean {e.mean():.2e} median {np.median(e):.2e} "
+          f"p99 {np.percentile(e, 99):.2e} max {e.max():.2e} px")
 
 
 def test_track_exact_shift(dgf):
@@ -237,7 +239,8 @@ def test_track_exact_shift(dgf):
     I2 = np.roll(np.roll(I1, -2, axis=0), 3, axis=1)
     pts = np.array([[x, y] for x in range(40, 216, 16) for y in range(30, 100, 12)], np.float64)
     prm = oracle.RlofParams(levels=3, radius=4, model=2, eps=1e-4, max_iter=60)
-    (fg, sg, _, _), (fo, so, _, _) = run_both(dgf, I1, I2, pts, prm)
+    fg, sg, _, _ = run_gpu(dgf, I1, I2, pts, prm)
+    fo, so, _, _ = oracle.rlof_track(I1, I2, pts, prm)
     ok = (sg == 0) & (so == 0)
     assert ok.mean() > 0.9
     assert np.abs(fg[ok] - [3, -2]).max() < 1e-2 and np.abs(fo[ok] - [3, -2]).max() < 1e-2

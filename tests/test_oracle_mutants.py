@@ -35,8 +35,8 @@ MUTANTS = {
         "gy += sobel_x[dx + 1][dy + 1] * v; /* transposed kernel */",
         "gy += sobel_x[dy + 1][dx + 1] * v; /* transposed kernel */", [test_oracle_pyramid]),
     "tracking keeps points with too little gradient": (
-        "if (lam_min / n_keep < prm->min_eig) { status = OR_SMALL_EIG; break; }",
-        "if (lam_min / n_keep < -prm->min_eig) { status = OR_SMALL_EIG; break; }", [test_oracle_rlof]),
+        "if (lam_min / n_keep < R(prm->min_eig)) { status = OR_SMALL_EIG; break; }",
+        "if (lam_min / n_keep < R(-prm->min_eig)) { status = OR_SMALL_EIG; break; }", [test_oracle_rlof]),
     "tracking residual adds the offset": (
         "res = J - (1 + m) * T[s] - c;", "res = J - (1 + m) * T[s] + c;", [test_oracle_rlof]),
     "Hampel drops the clipping between its first two knots": (
@@ -46,7 +46,7 @@ MUTANTS = {
         [test_oracle_rlof]),
     "tracking template sampled half a pixel off in y": (
         "T[s] = bilinear(A->I, A->W, A->H, plx + kx, ply + ky);",
-        "T[s] = bilinear(A->I, A->W, A->H, plx + kx, ply + ky + 0.5);", [test_oracle_rlof]),
+        "T[s] = bilinear(A->I, A->W, A->H, plx + kx, ply + ky + R(0.5));", [test_oracle_rlof]),
     "DeGraF tie picks the negative centroid": (
         "int use_neg = Sn > S;\n            double cx = use_neg ? (double)Xn",
         "int use_neg = Sn >= S;\n            double cx = use_neg ? (double)Xn", [test_oracle_degraf]),
@@ -84,7 +84,7 @@ PY_MUTANTS = {
     "round-trip error subtracts the backward flow": (
         "rlof_track_fb", "np.hypot(*(f + b).T)", "np.hypot(*(f - b).T)", [test_oracle_fb]),
     "backward pass starts from the start points": (
-        "rlof_track_fb", "rlof_track(I2, I1, pts + f, params, nthreads)", "rlof_track(I2, I1, pts, params, nthreads)",
+        "rlof_track_fb", "rlof_track(I2, I1, pts + f, params, nthreads,", "rlof_track(I2, I1, pts, params, nthreads,",
         [test_oracle_fb]),
     "the filter also rejects points the forward pass lost": (
         "rlof_track_fb", "status[fwd & (err > fb_max)] = FB_REJECTED", "status[err > fb_max] = FB_REJECTED",
@@ -152,8 +152,8 @@ def test_every_planted_mistake_fails_a_pin(name, monkeypatch):
     assert source.count(old) == 1, f"mutation site not unique: {old}"
     with tempfile.TemporaryDirectory() as tmp:
         so = build_copy(source.replace(old, new), tmp)
-        monkeypatch.setattr(oracle, "_lib", None)
-        monkeypatch.setattr(oracle, "build", lambda force=False: so)
+        monkeypatch.setattr(oracle, "_libs", {})
+        monkeypatch.setattr(oracle, "build", lambda force=False, precision="f64": so)
         failed = []
         for module in modules:
             for pin, call in pin_calls(module):
@@ -161,7 +161,7 @@ def test_every_planted_mistake_fails_a_pin(name, monkeypatch):
                     call()
                 except Exception:  # a failed assertion, or an error the mistake provokes
                     failed.append(pin)
-        monkeypatch.setattr(oracle, "_lib", None)  # the real oracle is loaded again on next use
+        monkeypatch.setattr(oracle, "_libs", {})  # the real oracle is loaded again on next use
     print(f"{name}: caught by {failed[:3]}{' ...' if len(failed) > 3 else ''}")
     assert failed, f"no pin catches: {name}"
 

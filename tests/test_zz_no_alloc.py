@@ -3,8 +3,13 @@ allocate device memory while they track (it keeps the pyramids in a fixed scratc
 array inside the library instead of a caller workspace).
 
 It is called through the C ABI and must give exactly what rlof_track_many gives
-with a caller workspace, on two calls in a row (the second call reuses the scratch
-the first one left behind). The file is named to be collected last."""
+with a caller workspace, on calls in a row (each reuses the scratch the previous
+one left behind), with FP32 and FP16 pyramids, up to the largest frame the scratch
+holds; a second call must leave the device's free memory unchanged; and the first
+frame size whose pyramids need more than the scratch is rejected before anything
+runs, with real buffers passed so that a regression in that check could only give
+wrong outputs, never touch memory the test does not own. The file is named to be
+collected last."""
 import ctypes
 
 import numpy as np
@@ -25,7 +30,7 @@ def dgf():
     return m
 
 
-def descriptor(dgf, f1, f2, win, step, out):
+def descriptor(f1, f2, win, step, out):
     from paper_1901_09971_gb300 import _abi
     H, W = f1.shape
     pts, flow, status, iters = out
@@ -33,43 +38,113 @@ def descriptor(dgf, f1, f2, win, step, out):
                       flow.data_ptr(), status.data_ptr(), iters.data_ptr())
 
 
-def outputs(n):
-    return (torch.empty((n, 2), dtype=torch.float32, device="cuda"),
-            torch.empty((n, 2), dtype=torch.float32, device="cuda"),
-            torch.empty(n, dtype=torch.uint8, device="cuda"),
-            torch.empty(n, dtype=torch.uint8, device="cuda"))
+def outputs(n, fill=None):
+    out = (torch.empty((n, 2), dtype=torch.float32, device="cuda"),
+           torch.empty((n, 2), dtype=torch.float32, device="cuda"),
+           torch.empty(n, dtype=torch.uint8, device="cuda"),
+           torch.empty(n, dtype=torch.uint8, device="cuda"))
+    if fill is not None:
+        for t in out:
+            t.view(torch.uint8).fill_(fill)
+    return out
 
 
-def test_noalloc_matches_workspace_path_twice(dgf):
+def workspace_bytes(lib, W, H, win, step, prm):
+    from paper_1901_09971_gb300 import _abi
+    desc = _abi.PairC(0, 0, W, H, W, win, step, 0, 0, 0, 0)
+    c_prm = prm.c()
+    return int(lib.dgf_track_many_workspace(ctypes.byref(desc), 1, ctypes.byref(c_prm)))
+
+
+def noalloc_call(dgf, f1, f2, win, step, prm, out):
     lib = dgf.load()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    cases = [(synth.make_pair(2), dgf.RlofParams(levels=5, radius=5, max_iter=30, model=4)),
-             (synth.make_pair(1), dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4))]
-    for pair, prm in cases:  # two calls in a row through the shared scratch
+    desc = descriptor(f1, f2, win, step, out)
+    c_prm = prm.c()
+    return lib.rlof_track_pair_noalloc(ctypes.byref(desc), ctypes.byref(c_prm), stream)
+
+
+def reference(dgf, f1, f2, win, step, prm):
+    H, W = f1.shape
+    ref = dgf.BatchTracker([(W, H, win, step)], prm)
+    ref.run([f1], [f2], use_graph=False)
+    return ref.pts[0], ref.flow[0], ref.status[0], ref.iters[0]
+
+
+def cases(dgf):
+    big = synth.make_translation_pair(1280, 720, seed=77)
+    big.win, big.step = 8, 3
+    return [
+        ("1242x375, 5 FP32 levels", synth.make_pair(2), dgf.RlofParams(levels=5, radius=5, max_iter=30, model=4)),
+        ("256x128, 3 FP32 levels", synth.make_pair(1), dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)),
+        ("1280x720, 5 FP32 levels", big, dgf.RlofParams(levels=5, radius=5, max_iter=30, model=4)),
+        ("1280x720, 5 FP16 levels", big, dgf.RlofParams(levels=5, radius=5, max_iter=30, model=4, storage=dgf.F16)),
+    ]
+
+
+def test_noalloc_matches_workspace_path_calls_in_a_row(dgf):
+    from paper_1901_09971_gb300 import _abi
+    lib = dgf.load()
+    for name, pair, prm in cases(dgf):  # calls in a row through the shared scratch
+        assert workspace_bytes(lib, pair.W, pair.H, pair.win, pair.step, prm) <= _abi.DGF_NOALLOC_SCRATCH_BYTES, name
         f1 = torch.from_numpy(pair.I1).cuda()
         f2 = torch.from_numpy(pair.I2).cuda()
         n = dgf.degraf_count(pair.W, pair.H, pair.win, pair.step)
-        got = outputs(n)
-        desc = descriptor(dgf, f1, f2, pair.win, pair.step, got)
-        c_prm = prm.c()
-        rc = lib.rlof_track_pair_noalloc(ctypes.byref(desc), ctypes.byref(c_prm), stream)
+        got = outputs(n, fill=0xA5)
+        rc = noalloc_call(dgf, f1, f2, pair.win, pair.step, prm, got)
         assert rc == 0, lib.dgf_strerror(rc)
-        ref = dgf.BatchTracker([(pair.W, pair.H, pair.win, pair.step)], prm)
-        ref.run([f1], [f2], use_graph=False)
+        ref = reference(dgf, f1, f2, pair.win, pair.step, prm)
         torch.cuda.synchronize()
-        for a, b in zip(got, (ref.pts[0], ref.flow[0], ref.status[0], ref.iters[0])):
-            assert torch.equal(a, b)
-        assert (got[2] == 0).float().mean().item() > 0.5  # most points converge
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b), name
+        assert (got[2] == 0).float().mean().item() > 0.5, name  # most points converge
 
 
-def test_noalloc_rejects_frames_beyond_the_scratch(dgf):
-    lib = dgf.load()
+def test_a_second_call_allocates_nothing(dgf):
+    """Free device memory is the same before and after a call once one call has run
+    (the first call on a device may make the runtime load the library's module)."""
+    pair = synth.make_pair(2)
+    prm = dgf.RlofParams(levels=5, radius=5, max_iter=30, model=4)
+    f1 = torch.from_numpy(pair.I1).cuda()
+    f2 = torch.from_numpy(pair.I2).cuda()
+    out = outputs(dgf.degraf_count(pair.W, pair.H, pair.win, pair.step))
+    assert noalloc_call(dgf, f1, f2, pair.win, pair.step, prm, out) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        assert noalloc_call(dgf, f1, f2, pair.win, pair.step, prm, out) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_rejects_the_first_size_beyond_the_scratch(dgf):
+    """At 720 rows, 5 FP32 levels: the widest frame whose pyramids fit is tracked like
+    the workspace path; one column more is rejected with DGF_ERR_WORKSPACE and the
+    outputs (real buffers, filled with a sentinel) are left untouched."""
     from paper_1901_09971_gb300 import _abi
-    W, H = 4096, 2048  # its two pyramids need far more than the fixed scratch
-    n = dgf.degraf_count(W, H, 8, 8)
-    fake = 1 << 20  # never dereferenced: the call returns before enqueuing anything
-    desc = _abi.PairC(fake, fake, W, H, W, 8, 8, fake, fake, fake, 0)
-    c_prm = dgf.RlofParams(levels=5, radius=5).c()
-    assert lib.dgf_track_many_workspace(ctypes.byref(desc), 1, ctypes.byref(c_prm)) > (24 << 20)
-    assert n > 0
-    assert lib.rlof_track_pair_noalloc(ctypes.byref(desc), ctypes.byref(c_prm), None) == _abi.DGF_ERR_WORKSPACE
+    lib = dgf.load()
+    prm = dgf.RlofParams(levels=5, radius=5, max_iter=30, model=4)
+    H, win, step = 720, 8, 8
+    limit = _abi.DGF_NOALLOC_SCRATCH_BYTES
+    W = 1280
+    while workspace_bytes(lib, W + 1, H, win, step, prm) <= limit:
+        W += 1
+    assert workspace_bytes(lib, W + 1, H, win, step, prm) > limit >= workspace_bytes(lib, W, H, win, step, prm)
+    print(f"widest {H}-row frame in the scratch: {W} columns")
+    big = synth.make_translation_pair(W + 1, H, seed=5)
+    for width, accepted in ((W, True), (W + 1, False)):
+        f1 = torch.from_numpy(np.ascontiguousarray(big.I1[:, :width])).cuda()
+        f2 = torch.from_numpy(np.ascontiguousarray(big.I2[:, :width])).cuda()
+        n = dgf.degraf_count(width, H, win, step)
+        got = outputs(n, fill=0x5A)
+        rc = noalloc_call(dgf, f1, f2, win, step, prm, got)
+        torch.cuda.synchronize()
+        if accepted:
+            assert rc == 0, lib.dgf_strerror(rc)
+            for a, b in zip(got, reference(dgf, f1, f2, win, step, prm)):
+                assert torch.equal(a, b)
+        else:
+            assert rc == _abi.DGF_ERR_WORKSPACE
+            for t in got:
+                assert bool((t.view(torch.uint8) == 0x5A).all())
