@@ -99,8 +99,13 @@ int degraf_detect(const uint8_t* img, int W, int H, int pitch, int win_w, int wi
  * Planes are stored I_0 .. I_{L-1}, then (with_grad) Ix_0 .. Ix_{L-1},
  * Iy_0 .. Iy_{L-1}; every plane starts on a 256-byte boundary and its rows are
  * `pitch` elements apart (a multiple of 128 bytes). The intensity planes sit at the
- * same offsets with or without gradients.
+ * same offsets with or without gradients. off_I/off_Ix/off_Iy locate pixel (0, 0);
+ * around it each plane carries a border of DGF_PYR_APRON pixels on every side that
+ * repeats the plane's edge (pixel (x, y) outside the level holds the value at the
+ * clamped position), so readers of bilinear taps near the border need no clamping.
  */
+#define DGF_PYR_APRON 12
+
 typedef struct {
     int levels, storage, with_grad;
     int W[DGF_MAX_LEVELS], H[DGF_MAX_LEVELS], pitch[DGF_MAX_LEVELS]; /* pitch in elements */

@@ -4,7 +4,7 @@ The compute lives in libdegraf.so (C ABI, include/degraf.h); this package is the
 thin torch binding. Nothing here computes on the CPU.
 """
 from ._abi import (  # noqa: F401
-    DegrafError, F16, F32, FB_REJECTED, MAXITER, OOB, SINGULAR, SMALL_EIG, TRACKED, load,
+    DegrafError, F16, F32, FB_REJECTED, MAXITER, OOB, PYR_APRON, SINGULAR, SMALL_EIG, TRACKED, load,
 )
 from .api import (  # noqa: F401
     BatchTracker, DeGraFDetect, DenseFlow, EpicParams, GmParams, PairTracker, RLOFTrack, RlofParams, build_pyramid, degraf_count, detect,

@@ -27,6 +27,7 @@ GM_PARAMS_VERSION = 1
 EPIC_PARAMS_VERSION = 1
 EPIC_MAX_K = 256
 DGF_NOALLOC_SCRATCH_BYTES = 24 << 20  # scratch of rlof_track_pair_noalloc
+PYR_APRON = 12  # replicated border of every pyramid plane (pixels)
 
 # Every entry point that include/degraf.h declares.
 EXPORTS = (

@@ -29,12 +29,21 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Rounds v up to a multiple of a, a power of two.
 __host__ __device__ __forceinline__ size_t round_up(size_t v, size_t a) { return (v + a - 1) & ~(a - 1); }
 
+// Width of the replicated border (apron) around every pyramid plane, in pixels
+// (DGF_PYR_APRON): pixel (x, y) of a plane may be read for x in [-A, W + A) and
+// y in [-A, H + A), and outside [0, W) x [0, H) it holds the value at the clamped
+// position. Tracking reads its bilinear taps without clamping; A covers the taps of
+// the largest support (radius 7) around any position in, or half a pixel beyond, a
+// level, and keeps pixel (0, 0) of every plane on a boundary of four elements (16
+// bytes FP32, 8 bytes FP16), the widest store the pyramid builder issues.
+constexpr int kApron = DGF_PYR_APRON;
+
 // Geometry of one pyramid level inside a pyramid buffer (see dgf_pyramid_layout):
-// planes I_0..I_{L-1}, then Ix_0..Ix_{L-1}, Iy_0..Iy_{L-1}; each plane starts on a
-// 256-byte boundary, rows are padded to 128 bytes.
+// planes I_0..I_{L-1}, then Ix_0..Ix_{L-1}, Iy_0..Iy_{L-1}; each plane (its apron
+// included) starts on a 256-byte boundary, rows are padded to 128 bytes.
 struct LevelGeom {
     int W, H, pitch;            // size and row pitch (elements)
-    size_t off_I, off_Ix, off_Iy;  // byte offsets (gradient offsets valid when built with them)
+    size_t off_I, off_Ix, off_Iy;  // byte offsets of pixel (0, 0) (gradient offsets valid when built with them)
     size_t bytes_all, bytes_intensity;  // buffer size with / without gradient planes
 };
 
@@ -46,13 +55,13 @@ __host__ __device__ inline bool level_geom(int W, int H, int levels, int es, int
     int w = W, h = H;
     for (int k = 0; k < levels; ++k) {
         if (w < 1 || h < 1) return false;
-        const int pitch = (int)round_up((size_t)w, (size_t)(128 / es));
-        const size_t plane = round_up((size_t)pitch * h * es, 256);
+        const int pitch = (int)round_up((size_t)w + 2 * kApron, (size_t)(128 / es));
+        const size_t plane = round_up((size_t)pitch * (h + 2 * kApron) * es, 256);
         if (k == l) {
             g->W = w;
             g->H = h;
             g->pitch = pitch;
-            pre = tot;
+            pre = tot + ((size_t)kApron * pitch + kApron) * es;
         }
         tot += plane;
         w /= 2;

@@ -15,7 +15,9 @@
 // keeps its own misalignment (0..3 bytes) and every read adds it. Then the CTA walks
 // down the levels, forming each level's values on its halo'd region from the
 // previous one with 2x2 means and writing I, Ix, Iy of the tile with coalesced rows
-// (16-byte stores at level 0). Tall tiles mean few staging round trips per SM; the
+// (16-byte stores at level 0). Tiles on the frame's edge also write the planes'
+// replicated borders (kApron pixels wide; the clamped values, so that tracking reads
+// its taps without clamping). Tall tiles mean few staging round trips per SM; the
 // frame is read about once from DRAM and every output byte is written once.
 #include "common.cuh"
 #include "batch.cuh"
@@ -82,6 +84,31 @@ struct Staged {
 
 namespace dgf {
 
+// Writes value v of pixel (x, y) of a W x H plane into the apron positions whose
+// clamped position it is (the plane's replicated border, kApron pixels wide): left
+// of column 0, right of column W - 1, above row 0, below row H - 1, and the corner
+// blocks. Pixels off the edge return at once.
+template <typename TS>
+__device__ __forceinline__ void apron_pixel(TS* P, int pitch, int W, int H, int x, int y, float v)
+{
+    const bool l = x == 0, r = x == W - 1, t = y == 0, b = y == H - 1;
+    if (!(l || r || t || b)) return;
+    TS* row = P + (ptrdiff_t)y * pitch;
+    for (int k = 1; k <= kApron; ++k) {
+        if (l) st(row - k, v);
+        if (r) st(row + x + k, v);
+    }
+    if (t || b) {
+        const int c0 = l ? x - kApron : x, c1 = r ? x + kApron : x;  // inclusive span, corners included
+        for (int k = 1; k <= kApron; ++k) {
+            for (int c = c0; c <= c1; ++c) {
+                if (t) st(P + (ptrdiff_t)(y - k) * pitch + c, v);
+                if (b) st(P + (ptrdiff_t)(y + k) * pitch + c, v);
+            }
+        }
+    }
+}
+
 // Level 0 of the tile: I and Sobel / 8 straight from the staged bytes, four
 // pixels per item. INTERIOR: the halo'd region lies inside the frame, so no
 // neighbour needs clamping.
@@ -147,6 +174,15 @@ __device__ __forceinline__ void level0(const PyrFrame& F, const LevelGeom& g, co
                 }
             }
         }
+        if (!INTERIOR) {  // tiles inside the frame hold no edge pixel
+            for (int k = 0; k < 4 && X0 + tx + k < F.W; ++k) {
+                apron_pixel(I, g.pitch, F.W, F.H, X0 + tx + k, y, vI[k]);
+                if (F.with_grad) {
+                    apron_pixel(Ix, g.pitch, F.W, F.H, X0 + tx + k, y, vx[k]);
+                    apron_pixel(Iy, g.pitch, F.W, F.H, X0 + tx + k, y, vy[k]);
+                }
+            }
+        }
     }
 }
 
@@ -200,7 +236,9 @@ __device__ __forceinline__ void coarse_levels(const PyrFrame& F, const LevelGeom
             const int xm = INTERIOR ? xc - 1 : max(x - 1, 0) - ox, xp = INTERIOR ? xc + 1 : min(x + 1, g.W - 1) - ox;
             const int ym = INTERIOR ? yc - 1 : max(y - 1, 0) - oy, yp = INTERIOR ? yc + 1 : min(y + 1, g.H - 1) - oy;
             const size_t o = (size_t)y * g.pitch + x;
-            st(I + o, cur[yc * rw + xc]);
+            const float v = cur[yc * rw + xc];
+            st(I + o, v);
+            if (!INTERIOR) apron_pixel(I, g.pitch, g.W, g.H, x, y, v);
             if (F.with_grad) {
                 const float gx = (cur[ym * rw + xp] - cur[ym * rw + xm]) + 2.f * (cur[yc * rw + xp] - cur[yc * rw + xm]) +
                                  (cur[yp * rw + xp] - cur[yp * rw + xm]);
@@ -208,6 +246,10 @@ __device__ __forceinline__ void coarse_levels(const PyrFrame& F, const LevelGeom
                                  (cur[yp * rw + xp] - cur[ym * rw + xp]);
                 st(Ix + o, gx * 0.125f);
                 st(Iy + o, gy * 0.125f);
+                if (!INTERIOR) {
+                    apron_pixel(Ix, g.pitch, g.W, g.H, x, y, gx * 0.125f);
+                    apron_pixel(Iy, g.pitch, g.W, g.H, x, y, gy * 0.125f);
+                }
             }
         }
     }

@@ -147,21 +147,6 @@ __device__ __forceinline__ float2 ld2(const __half* p)
     return __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
 }
 
-// Sample pair whose taps are all inside the plane; p points at tap a0. EVEN: a0
-// sits on an 8-byte (FP32) or 4-byte (FP16) boundary, so (a0, a1) and (b0, b1)
-// load as pairs; otherwise (a1, a2) and (b1, b2) do.
-template <typename TS, bool EVEN>
-__device__ __forceinline__ float2 pair_inside(const TS* p, int pitch, const PairWeights& w)
-{
-    if (EVEN) {
-        const float2 a01 = ld2(p), b01 = ld2(p + pitch);
-        return bilinear_pair(w, a01.x, a01.y, dgf::ld(p + 2), b01.x, b01.y, dgf::ld(p + pitch + 2));
-    } else {
-        const float2 a12 = ld2(p + 1), b12 = ld2(p + pitch + 1);
-        return bilinear_pair(w, dgf::ld(p), a12.x, a12.y, dgf::ld(p + pitch), b12.x, b12.y);
-    }
-}
-
 // Sample pair at integer tap origin (xi, yi) with every tap clamped to the border.
 template <typename TS>
 __device__ __forceinline__ float2 pair_clamped(const TS* P, int pitch, int W, int H, int xi, int yi,
@@ -196,6 +181,60 @@ __device__ __forceinline__ float2 vpair_clamped(const TS* P, int pitch, int W, i
     return bilinear_vpair(w, dgf::ld(r0 + xa), dgf::ld(r0 + xb), dgf::ld(r1 + xa), dgf::ld(r1 + xb), dgf::ld(r2 + xa),
                           dgf::ld(r2 + xb));
 }
+
+// The taps of one point's support at integer origin (bx, by) of a plane, read
+// without clamping (the pyramid planes carry a replicated border wide enough for
+// any support around a position inside the level). One code path serves both
+// parities e of the first column, so the two points of a warp never split into two
+// load sequences run one after the other: for a horizontal pair at element offset
+// off, the aligned pair load u holds (a0, a1) when e = 0 and (a1, a2) when e = 1,
+// the scalar s the remaining tap (a2 or a0), and the bilinear weights swap with the
+// parity instead of the taps: J = wP u + wQ Q (+ the row below), Q = (a1, a2) or
+// (a0, a1). A generic slot holds a horizontal or a vertical pair: sample A's four
+// taps, then the two taps sample B adds at stored offsets (right column or row
+// below).
+template <typename TS>
+struct TapBlock {
+    const TS *base, *base_u, *base_s;
+    int pitch, e;
+    float2 wP, wQ, wPb, wQb;
+    __device__ __forceinline__ TapBlock(const TS* plane, int pitch_, int bx, int by, const PairWeights& pw)
+    {
+        pitch = pitch_;
+        base = plane + (ptrdiff_t)by * pitch + bx;
+        e = bx & 1;
+        base_u = base + e;
+        base_s = base + (2 - 2 * e);
+        wP = e ? pw.w01 : pw.w00;
+        wQ = e ? pw.w00 : pw.w01;
+        wPb = e ? pw.w11 : pw.w10;
+        wQb = e ? pw.w10 : pw.w11;
+    }
+    __device__ __forceinline__ float2 pair(int off) const
+    {
+        const TS* pu = base_u + off;
+        const TS* ps = base_s + off;
+        const float2 u = ld2(pu), ub = ld2(pu + pitch);
+        const float sa = dgf::ld(ps), sb = dgf::ld(ps + pitch);
+        const float2 Q = make_float2(e ? sa : u.y, e ? u.x : sa);
+        const float2 Qb = make_float2(e ? sb : ub.y, e ? ub.x : sb);
+        float2 J = __fmul2_rn(wP, u);
+        J = __ffma2_rn(wQ, Q, J);
+        J = __ffma2_rn(wPb, ub, J);
+        return __ffma2_rn(wQb, Qb, J);
+    }
+    __device__ __forceinline__ float2 generic(int off, int eo0, int eo1, bool vert, const PairWeights& pw) const
+    {
+        const TS* p = base + off;
+        const float a0 = dgf::ld(p), a1 = dgf::ld(p + 1), b0 = dgf::ld(p + pitch), b1 = dgf::ld(p + pitch + 1);
+        const float e0 = dgf::ld(base + eo0), e1 = dgf::ld(base + eo1);
+        const float t0 = vert ? b0 : a1, t1 = vert ? b1 : e0, t2 = vert ? e0 : b1;
+        float2 J = __fmul2_rn(pw.w00, make_float2(a0, t0));
+        J = __ffma2_rn(pw.w01, make_float2(a1, t1), J);
+        J = __ffma2_rn(pw.w10, make_float2(b0, t2), J);
+        return __ffma2_rn(pw.w11, make_float2(b1, e1), J);
+    }
+};
 
 __device__ __forceinline__ float rcp_approx(float x)
 {
@@ -346,14 +385,13 @@ __host__ __device__ constexpr int first_generic_slot()
 // Accumulates the weighted normal equations of the lane's pairs at one iterate.
 // acc[0..9] = sum w (TxTx, TxTy, TxT, Tx, TyTy, TyT, Ty, TT, T, 1); acc[10..13] =
 // sum w r (Tx, Ty, T, 1), each as .x/.y partial sums of a pair's two samples.
-// MODE 0: taps inside, even first column; 1: inside, odd; 2: clamped taps.
-template <typename TS, int G, int SLP, int MODEL, int MODE, int RC, bool CROSS>
-__device__ __forceinline__ void accumulate(const Support<SLP>& S, float2 (&acc)[14], const TS* I2, int pitch, int W,
-                                           int H, int bx, int by, const PairWeights& pw, int lane, int np, int pc,
-                                           float g1, float c, float ha, float icb, float hc_icb)
+// Taps are read without clamping (TapBlock).
+template <typename TS, int G, int SLP, int MODEL, int RC, bool CROSS>
+__device__ __forceinline__ void accumulate(const Support<SLP>& S, float2 (&acc)[14], const TapBlock<TS>& tb,
+                                           const PairWeights& pw, int lane, int np, float g1, float c, float ha,
+                                           float icb, float hc_icb)
 {
     constexpr int FG = first_generic_slot<G, SLP, RC>();
-    const TS* base = I2 + (ptrdiff_t)by * pitch + bx;
     const float2 ng1 = f2(-g1), nc = f2(-c);
 #pragma unroll
     for (int j = 0; j < SLP; ++j) {
@@ -363,45 +401,8 @@ __device__ __forceinline__ void accumulate(const Support<SLP>& S, float2 (&acc)[
         if (j == SLP - 1 && q >= np) break;
         float2 T, Tx, Ty;
         S.get(j, T, Tx, Ty);
-        float2 J;
-        if (j >= FG) {
-            // slot with vertical pairs: sample A's four taps, then the two taps
-            // sample B adds (right column for a horizontal pair, row below for a
-            // vertical one) from their stored offsets
-            const bool vert = (S.vbits >> (j - FG)) & 1u;
-            if (MODE == 2) {
-                if (q < Layout<RC>::nh) {
-                    const int ky = q / RC, kp = q - ky * RC;
-                    J = pair_clamped(I2, pitch, W, H, bx + 2 * kp, by + ky, pw);
-                } else {
-                    J = vpair_clamped(I2, pitch, W, H, bx + 2 * RC, by + 2 * (q - Layout<RC>::nh), pw);
-                }
-            } else {
-                const TS* p = base + S.off[j];
-                float a0, a1, b0, b1;
-                if (MODE == 0) {
-                    const float2 a = ld2(p), b = ld2(p + pitch);
-                    a0 = a.x; a1 = a.y; b0 = b.x; b1 = b.y;
-                } else {
-                    const float2 a = ld2(p + 1), b = ld2(p + pitch + 1);
-                    a0 = dgf::ld(p); a1 = a.x; b0 = dgf::ld(p + pitch); b1 = b.x;
-                }
-                const float e0 = dgf::ld(base + S.eo0[j - FG]), e1 = dgf::ld(base + S.eo1[j - FG]);
-                const float t0 = vert ? b0 : a1, t1 = vert ? b1 : e0, t2 = vert ? e0 : b1;
-                float2 Jp = __fmul2_rn(pw.w00, make_float2(a0, t0));
-                Jp = __ffma2_rn(pw.w01, make_float2(a1, t1), Jp);
-                Jp = __ffma2_rn(pw.w10, make_float2(b0, t2), Jp);
-                J = __ffma2_rn(pw.w11, make_float2(b1, e1), Jp);
-            }
-        } else if (MODE == 0) {
-            J = pair_inside<TS, true>(base + S.off[j], pitch, pw);
-        } else if (MODE == 1) {
-            J = pair_inside<TS, false>(base + S.off[j], pitch, pw);
-        } else {
-            const int ppr = RC ? RC : pc;  // horizontal pairs per row
-            const int ky = q / ppr, kp = q - ky * ppr;
-            J = pair_clamped(I2, pitch, W, H, bx + 2 * kp, by + ky, pw);
-        }
+        const float2 J = j >= FG ? tb.generic(S.off[j], S.eo0[j - FG], S.eo1[j - FG], (S.vbits >> (j - FG)) & 1u, pw)
+                                 : tb.pair(S.off[j]);
         float2 r;
         if (MODEL == 4)
             r = __fadd2_rn(__ffma2_rn(ng1, T, J), nc);
@@ -518,6 +519,12 @@ __device__ __forceinline__ bool setup_level(Support<SLP>& S, const LevelView<TS>
     const float fx0 = floorf(plx), fy0 = floorf(ply);
     const int bx = (int)fx0 - R, by = (int)fy0 - R;
     const PairWeights pw(plx - fx0, ply - fy0);
+    // the template's taps read without clamping when they lie within the planes'
+    // replicated border, as they do for every point inside the frame (points given
+    // outside it take the clamped reads)
+    const bool direct = bx >= -dgf::kApron && bx + 2 * R + 2 <= L.W + dgf::kApron - 1 && by >= -dgf::kApron &&
+                        by + 2 * R + 1 <= L.H + dgf::kApron - 1;
+    const TapBlock<TS> tT(L.I1, L.pitch, bx, by, pw), tX(L.I1x, L.pitch, bx, by, pw), tY(L.I1y, L.pitch, bx, by, pw);
     float2 g00 = f2(0.f), g01 = f2(0.f), g11 = f2(0.f);
     float kept = 0.f;  // cross-based support: kept samples of the lane
     int* arm = nullptr;
@@ -554,24 +561,31 @@ __device__ __forceinline__ bool setup_level(Support<SLP>& S, const LevelView<TS>
                 y = 2 * (q - Layout<RC>::nh);
             }
             off = y * L.pitch + x;
-            if (vert) {
-                msk = y + 1 < side ? 1.f : 0.f;
+            msk = (vert ? y : x) + 1 < side ? 1.f : 0.f;
+            // taps sample B adds in a generic slot: right column (horizontal), row
+            // below (vertical), or, for the masked sample, two of A's own taps so
+            // that every load stays inside the tap block
+            const int e0 = vert ? (msk != 0.f ? off + 2 * L.pitch : off) : off + 2;
+            const int e1 = vert ? e0 + 1 : off + L.pitch + 2;
+            if (direct && j >= FG) {
+                T = tT.generic(off, e0, e1, vert, pw);
+                Tx = tX.generic(off, e0, e1, vert, pw);
+                Ty = tY.generic(off, e0, e1, vert, pw);
+            } else if (direct) {
+                T = tT.pair(off);
+                Tx = tX.pair(off);
+                Ty = tY.pair(off);
+            } else if (vert) {
                 T = vpair_clamped(L.I1, L.pitch, L.W, L.H, bx + x, by + y, pw);
                 Tx = vpair_clamped(L.I1x, L.pitch, L.W, L.H, bx + x, by + y, pw);
                 Ty = vpair_clamped(L.I1y, L.pitch, L.W, L.H, bx + x, by + y, pw);
             } else {
-                msk = x + 1 < side ? 1.f : 0.f;
                 T = pair_clamped(L.I1, L.pitch, L.W, L.H, bx + x, by + y, pw);
                 Tx = pair_clamped(L.I1x, L.pitch, L.W, L.H, bx + x, by + y, pw);
                 Ty = pair_clamped(L.I1y, L.pitch, L.W, L.H, bx + x, by + y, pw);
             }
             if (msk == 0.f) T.y = Tx.y = Ty.y = 0.f;
             if (j >= FG) {
-                // taps sample B adds: right column (horizontal), row below
-                // (vertical), or, for the masked sample, two of A's own taps so
-                // that every load stays inside the tap block
-                const int e0 = vert ? (msk != 0.f ? off + 2 * L.pitch : off) : off + 2;
-                const int e1 = vert ? e0 + 1 : off + L.pitch + 2;
                 S.eo0[j - FG] = e0;
                 S.eo1[j - FG] = e1;
                 if (vert) S.vbits |= 1u << (j - FG);
@@ -624,7 +638,9 @@ __device__ __forceinline__ bool setup_level(Support<SLP>& S, const LevelView<TS>
 }
 
 // One Gauss-Newton step at iterate q (inside the level): accumulates, reduces and
-// solves the weighted normal equations. Returns false on a non-positive pivot.
+// solves the weighted normal equations. Returns false on a non-positive pivot. The
+// tap block of a position inside the level lies within the planes' replicated
+// border (columns bx .. bx + 2R + 2, rows by .. by + 2R + 1), so no tap is clamped.
 template <typename TS, int G, int SLP, int MODEL, int RC, bool CROSS>
 __device__ __forceinline__ bool gn_step(const Support<SLP>& S, const LevelView<TS>& L, float qx, float qy, float m,
                                         float c, int lane, unsigned mask, int R, float ha, float icb, float hc_icb,
@@ -634,22 +650,11 @@ __device__ __forceinline__ bool gn_step(const Support<SLP>& S, const LevelView<T
     const float fx0 = floorf(qx), fy0 = floorf(qy);
     const int bx = (int)fx0 - R, by = (int)fy0 - R;
     const PairWeights pw(qx - fx0, qy - fy0);
-    // the tap block spans columns bx .. bx + 2R + 2 (the masked last sample
-    // included) and rows by .. by + 2R + 1
-    const bool inside = bx >= 0 && bx + 2 * R + 2 <= L.W - 1 && by >= 0 && by + 2 * R + 1 <= L.H - 1;
     float2 acc[14];
 #pragma unroll
     for (int k = 0; k < 14; ++k) acc[k] = f2(0.f);
-    const float g1 = 1.f + m;
-    if (inside && (bx & 1) == 0)
-        accumulate<TS, G, SLP, MODEL, 0, RC, CROSS>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
-                                         hc_icb);
-    else if (inside)
-        accumulate<TS, G, SLP, MODEL, 1, RC, CROSS>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
-                                         hc_icb);
-    else
-        accumulate<TS, G, SLP, MODEL, 2, RC, CROSS>(S, acc, L.I2, L.pitch, L.W, L.H, bx, by, pw, lane, np, pc, g1, c, ha, icb,
-                                         hc_icb);
+    const TapBlock<TS> tb(L.I2, L.pitch, bx, by, pw);
+    accumulate<TS, G, SLP, MODEL, RC, CROSS>(S, acc, tb, pw, lane, np, 1.f + m, c, ha, icb, hc_icb);
     float h[16];
     if (MODEL == 4) {
         float v[16];

@@ -180,7 +180,8 @@ def fb_disagreements(status, err, status64, err64) -> dict:
     """status: the final status (with FB_REJECTED) differs; error: both round-trip
     errors finite and more than twice the flow tolerance apart."""
     fin = np.isfinite(err) & np.isfinite(err64)
-    d = np.where(fin, np.abs(np.asarray(err, np.float64) - err64), 0.0)
+    d = np.zeros(len(err64))
+    d[fin] = np.abs(np.asarray(err, np.float64)[fin] - err64[fin])
     return {"status": status != status64, "error": fin & (d > 2 * TOL_FLOW)}
 
 

@@ -71,10 +71,17 @@ def test_pyramid_layout(storage):
     b = dgf.pyramid_layout(1242, 375, 5, storage, False)
     assert a["W"] == [1242, 621, 310, 155, 77] and a["H"] == [375, 187, 93, 46, 23]
     assert a["off_I"] == b["off_I"]  # intensity planes independent of the gradient planes
+    A = _abi.PYR_APRON
+    spans = []
     for l in range(5):
-        assert a["pitch"][l] * es % 128 == 0 and a["pitch"][l] >= a["W"][l]
+        p = a["pitch"][l]
+        assert p * es % 128 == 0 and p >= a["W"][l] + 2 * A
         for off in (a["off_I"][l], a["off_Ix"][l], a["off_Iy"][l]):
-            assert off % 256 == 0
+            start = off - (A * p + A) * es  # the plane with its replicated border
+            assert start % 256 == 0 and off % (4 * es) == 0  # the builder stores four values at once
+            spans.append((start, start + p * (a["H"][l] + 2 * A) * es))
+    spans.sort()
+    assert all(e0 <= s1 for (_, e0), (s1, _) in zip(spans, spans[1:])) and spans[-1][1] <= a["bytes"]
     assert a["bytes"] > b["bytes"] and dgf.pyramid_bytes(1242, 375, 5, storage, True) == a["bytes"]
     assert dgf.pyramid_bytes(1242, 375, 7, storage, True) == 0
     assert dgf.pyramid_bytes(3, 3, 3, storage, True) == 0  # empty coarsest level
@@ -314,6 +321,7 @@ def test_probe_host_checks_and_flop_count():
 
 def test_noalloc_scratch_size_matches_the_header():
     text = open(HEADER).read()
+    assert re.search(r"#define DGF_PYR_APRON (\d+)", text).group(1) == str(_abi.PYR_APRON)
     m = re.search(r"#define DGF_NOALLOC_SCRATCH_BYTES \((\d+)u << (\d+)\)", text)
     assert m and int(m.group(1)) << int(m.group(2)) == _abi.DGF_NOALLOC_SCRATCH_BYTES
 

@@ -135,6 +135,15 @@ def test_pyramid_parity(dgf, size, levels, storage):
         for g, o in zip(planes, oref):
             assert np.array_equal(g.cpu().numpy(), o.astype(dt)), f"level {l}"
         assert np.array_equal(planes2[0].cpu().numpy(), oref[0].astype(dt))
+    # the replicated border around every plane holds the clamped values
+    A, es = dgf.PYR_APRON, (4 if storage == 0 else 2)
+    host = buf.cpu().numpy()
+    for l, oref in enumerate(ref):
+        Wl, Hl, p = lay["W"][l], lay["H"][l], lay["pitch"][l]
+        for key, o in zip(("off_I", "off_Ix", "off_Iy"), oref):
+            start = lay[key][l] - (A * p + A) * es
+            padded = host[start:start + p * (Hl + 2 * A) * es].view(dt).reshape(Hl + 2 * A, p)[:, :Wl + 2 * A]
+            assert np.array_equal(padded, np.pad(o, A, mode="edge").astype(dt)), f"level {l} {key} border"
 
 
 # ----------------------------------------------------------------- tracking

@@ -49,11 +49,21 @@ def outputs(n, fill=None):
     return out
 
 
+_QUERY_BUF = []
+
+
 def workspace_bytes(lib, W, H, win, step, prm):
+    """dgf_track_many_workspace of one W x H pair: a host-side size query that reads
+    no buffer (it still wants non-null, aligned pointers, so it gets a real one)."""
     from paper_1901_09971_gb300 import _abi
-    desc = _abi.PairC(0, 0, W, H, W, win, step, 0, 0, 0, 0)
+    if not _QUERY_BUF:
+        _QUERY_BUF.append(torch.zeros(256, dtype=torch.uint8, device="cuda"))
+    a = _QUERY_BUF[0].data_ptr()
+    desc = _abi.PairC(a, a, W, H, W, win, step, a, a, a, a)
     c_prm = prm.c()
-    return int(lib.dgf_track_many_workspace(ctypes.byref(desc), 1, ctypes.byref(c_prm)))
+    n = int(lib.dgf_track_many_workspace(ctypes.byref(desc), 1, ctypes.byref(c_prm)))
+    assert n > 0, "size query rejected its arguments"
+    return n
 
 
 def noalloc_call(dgf, f1, f2, win, step, prm, out):
@@ -127,9 +137,7 @@ def test_noalloc_rejects_the_first_size_beyond_the_scratch(dgf):
     prm = dgf.RlofParams(levels=5, radius=5, max_iter=30, model=4)
     H, win, step = 720, 8, 8
     limit = _abi.DGF_NOALLOC_SCRATCH_BYTES
-    W = 1280
-    while workspace_bytes(lib, W + 1, H, win, step, prm) <= limit:
-        W += 1
+    W = next(w for w in range(1280, 4096) if workspace_bytes(lib, w + 1, H, win, step, prm) > limit)
     assert workspace_bytes(lib, W + 1, H, win, step, prm) > limit >= workspace_bytes(lib, W, H, win, step, prm)
     print(f"widest {H}-row frame in the scratch: {W} columns")
     big = synth.make_translation_pair(W + 1, H, seed=5)
