@@ -43,6 +43,17 @@ __host__ __device__ constexpr int block_threads()
     return G == 8 ? 32 : 128;
 }
 
+// Resident blocks the register budget is sized for: 512 threads a SM (128 registers
+// a thread), except at 8 lanes and radius 5, where 12 one-warp blocks (168
+// registers, no spills) measured 1.6% faster than 16 (128 registers, 12 bytes of
+// spills) on the 1242x375 pair, 1.203 against 1.223 ms; at radius 4 16 stay faster
+// (0.220 against 0.232 ms on its step-4 pair).
+template <int G, int RC>
+__host__ __device__ constexpr int min_blocks()
+{
+    return G == 8 && RC == 5 ? 12 : 512 / block_threads<G>();
+}
+
 template <int G>
 __device__ __forceinline__ float group_sum(float v, unsigned mask)
 {
@@ -408,7 +419,10 @@ __device__ __forceinline__ void accumulate(const Support<SLP>& S, float2 (&acc)[
             r = __fadd2_rn(__ffma2_rn(ng1, T, J), nc);
         else
             r = __ffma2_rn(f2(-1.f), T, J);
-        float2 w = make_float2(hampel_weight(r.x, ha, icb, hc_icb), hampel_weight(r.y, ha, icb, hc_icb) * S.msk[j]);
+        // only a generic slot (and any slot of the runtime layout) can hold a sample
+        // past the support
+        float2 w = make_float2(hampel_weight(r.x, ha, icb, hc_icb), hampel_weight(r.y, ha, icb, hc_icb));
+        if (RC == 0 || j >= FG) w.y *= S.msk[j];
         if (CROSS) w = __fmul2_rn(w, S.mk[32 * j]);
         const float2 wTx = __fmul2_rn(w, Tx), wTy = __fmul2_rn(w, Ty);
         acc[0] = __ffma2_rn(wTx, Tx, acc[0]);
@@ -782,9 +796,8 @@ std::atomic<int> g_lanes_override{0};
 template <typename TS, int MODEL, int G, int SLP, int RC>
 int launch_one(const TrackBatch& a, cudaStream_t stream)
 {
-    // four blocks of 128 threads per SM (128 registers a thread)
     const long long total = (long long)a.total * G;
-    constexpr int BT = block_threads<G>(), MINB = 512 / BT;  // 128 registers a thread
+    constexpr int BT = block_threads<G>(), MINB = min_blocks<G, RC>();
     const unsigned grid = (unsigned)((total + BT - 1) / BT);
     if (a.cross_tau > 0.f)
         rlof_kernel<TS, G, SLP, MODEL, MINB, RC, true><<<grid, BT, 0, stream>>>(a);
@@ -820,10 +833,12 @@ int launch(const TrackBatch& a, int lanes, cudaStream_t stream)
 int choose_lanes(int radius, int set)
 {
     // 8 and 16 lanes are built for radius 4 and 5 only; other radii use 32 lanes.
-    // Measured on GB300: radius 5 fastest at 16 lanes, radius 4 at 8.
+    // Measured on GB300: both radii fastest at 8 lanes (radius 5 on the 1242x375 pair:
+    // 1.25 ms against 1.40 ms at 16 lanes, once no two points of a warp take
+    // different tap-load paths; radius 4 on its step-4 pair: 0.224 against 0.226 ms).
     if (radius != 4 && radius != 5) return 32;
     if (set) return set;
-    return radius == 5 ? 16 : 8;
+    return 8;
 }
 
 }  // namespace rlof_detail

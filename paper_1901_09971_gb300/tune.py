@@ -1,7 +1,7 @@
 """Autotuner of the tracking launch shape (lanes per point) for a batch of pairs.
 
-The library picks 16 lanes per point at radius 5 and 8 at radius 4, the fastest
-shapes on the single-pair and mixed-batch workloads. A batch of other sizes,
+The library picks 8 lanes per point at radius 4 and 5, the fastest shape on the
+single-pair and mixed-batch workloads. A batch of other sizes,
 steps or parameters may prefer another shape, so ``tune`` times rlof_track_many
 on the caller's frames for every lane count the library honours at the batch's
 radius, keeps the fastest, and records it in a JSON cache keyed by the GPU, the

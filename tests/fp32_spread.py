@@ -25,7 +25,8 @@ disagreements; and when the bulk of its tracked points is as close to FP64 as th
 FP32 restatement's: the median and the 90th percentile of the endpoint difference
 over the points TRACKED on both sides at most 1.5 times those of the restatement on
 the unmoved key-points (plus 1e-6 px; the moved members track slightly different
-points, whose true flows differ by the flow field's slope times an ulp).
+points, whose true flows differ by the flow field's slope times an ulp), once 100
+or more points are compared.
 A mistake that moves points by more than 1e-2 px, moves a different set of points,
 or shifts the bulk by more than rounding does, fails one of the three.
 """
@@ -40,6 +41,7 @@ import oracle
 TOL_FLOW = 1e-2
 CATEGORIES = ("status", "tracked", "maxiter")
 PERCENTILES = (50, 90)
+MIN_FOR_QUANTILES = 100  # points compared before the bulk bar applies
 
 
 def disagreements(flow, status, flow64, status64, tol: float = TOL_FLOW) -> dict:
@@ -125,9 +127,10 @@ def check(flow, status, sp: Spread, label: str = "") -> dict:
            "quantiles": {p: float(f"{v:.3g}") for p, v in qs.items()},
            "fp32_quantiles": {p: float(f"{v:.3g}") for p, v in sp.quantiles.items()}}
     print(f"{label}: {fig}")
-    for p in PERCENTILES:
-        lim = 1.5 * sp.quantiles[p] + 1e-6
-        assert qs[p] <= lim, f"{label}: percentile {p} of the tracked endpoint difference {qs[p]:.3g} above {lim:.3g}"
+    if both.sum() >= MIN_FOR_QUANTILES:  # a few points' percentiles are single FP32 roundings
+        for p in PERCENTILES:
+            lim = 1.5 * sp.quantiles[p] + 1e-6
+            assert qs[p] <= lim, f"{label}: percentile {p} of the tracked endpoint difference {qs[p]:.3g} above {lim:.3g}"
     for c in CATEGORIES:
         assert got[c] <= sp.bound(c), f"{label}: {c} disagreements {got[c]} above the FP32 bound {sp.bound(c):.1f}"
     if n_out >= 20:
@@ -223,9 +226,11 @@ def check_fb(status, err, sp: FbSpread, label: str = "") -> dict:
            "quantiles": {p: float(f"{v:.3g}") for p, v in qs.items()},
            "fp32_quantiles": {p: float(f"{v:.3g}") for p, v in sp.quantiles.items()}}
     print(f"{label}: {fig}")
-    for p in PERCENTILES:
-        lim = 1.5 * sp.quantiles[p] + 1e-6
-        assert qs[p] <= lim, f"{label}: percentile {p} of the round-trip error difference {qs[p]:.3g} above {lim:.3g}"
+    fin = int((np.isfinite(err) & np.isfinite(sp.err64)).sum())
+    if fin >= MIN_FOR_QUANTILES:
+        for p in PERCENTILES:
+            lim = 1.5 * sp.quantiles[p] + 1e-6
+            assert qs[p] <= lim, f"{label}: percentile {p} of the round-trip error difference {qs[p]:.3g} above {lim:.3g}"
     for c in FB_CATEGORIES:
         assert got[c] <= sp.bound(c), f"{label}: {c} disagreements {got[c]} above the FP32 bound {sp.bound(c):.1f}"
     if n_out >= 20:
