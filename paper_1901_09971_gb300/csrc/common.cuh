@@ -34,8 +34,9 @@ __host__ __device__ __forceinline__ size_t round_up(size_t v, size_t a) { return
 // y in [-A, H + A), and outside [0, W) x [0, H) it holds the value at the clamped
 // position. Tracking reads its bilinear taps without clamping; A covers the taps of
 // the largest support (radius 7) around any position in, or half a pixel beyond, a
-// level, and keeps pixel (0, 0) of every plane on a boundary of four elements (16
-// bytes FP32, 8 bytes FP16), the widest store the pyramid builder issues.
+// level. Each row starts 128 bytes before its pixel 0 (the left apron in the last
+// A elements of that space), so every row of the level itself starts on a 128-byte
+// boundary, as the builder's full-line stores want.
 constexpr int kApron = DGF_PYR_APRON;
 
 // Geometry of one pyramid level inside a pyramid buffer (see dgf_pyramid_layout):
@@ -55,13 +56,14 @@ __host__ __device__ inline bool level_geom(int W, int H, int levels, int es, int
     int w = W, h = H;
     for (int k = 0; k < levels; ++k) {
         if (w < 1 || h < 1) return false;
-        const int pitch = (int)round_up((size_t)w + 2 * kApron, (size_t)(128 / es));
+        const int lead = 128 / es;  // elements before pixel 0 of a row (>= kApron)
+        const int pitch = (int)round_up((size_t)w + lead + kApron, (size_t)(128 / es));
         const size_t plane = round_up((size_t)pitch * (h + 2 * kApron) * es, 256);
         if (k == l) {
             g->W = w;
             g->H = h;
             g->pitch = pitch;
-            pre = tot + ((size_t)kApron * pitch + kApron) * es;
+            pre = tot + ((size_t)kApron * pitch + lead) * es;
         }
         tot += plane;
         w /= 2;

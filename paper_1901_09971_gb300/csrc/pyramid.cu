@@ -84,29 +84,39 @@ struct Staged {
 
 namespace dgf {
 
-// Writes value v of pixel (x, y) of a W x H plane into the apron positions whose
-// clamped position it is (the plane's replicated border, kApron pixels wide): left
-// of column 0, right of column W - 1, above row 0, below row H - 1, and the corner
-// blocks. Pixels off the edge return at once.
-template <typename TS>
-__device__ __forceinline__ void apron_pixel(TS* P, int pitch, int W, int H, int x, int y, float v)
+// The replicated border (kApron pixels wide) that a tile on a level's edge owns:
+// outside the level, beside the tile's columns [x0, xe] and rows [y0, ye] (its part
+// of the level), every position takes the values at its clamped position, which
+// lies in the tile. The left and right strips include the corner blocks. All
+// threads of the block share the strips; value(x, y, I, Ix, Iy) forms the values of
+// tile pixel (x, y) from the data the block already holds.
+template <typename TS, typename Value>
+__device__ __forceinline__ void apron_strips(TS* I, TS* Ix, TS* Iy, bool grad, int pitch, int W, int H, int x0,
+                                             int y0, int xe, int ye, Value value)
 {
-    const bool l = x == 0, r = x == W - 1, t = y == 0, b = y == H - 1;
-    if (!(l || r || t || b)) return;
-    TS* row = P + (ptrdiff_t)y * pitch;
-    for (int k = 1; k <= kApron; ++k) {
-        if (l) st(row - k, v);
-        if (r) st(row + x + k, v);
-    }
-    if (t || b) {
-        const int c0 = l ? x - kApron : x, c1 = r ? x + kApron : x;  // inclusive span, corners included
-        for (int k = 1; k <= kApron; ++k) {
-            for (int c = c0; c <= c1; ++c) {
-                if (t) st(P + (ptrdiff_t)(y - k) * pitch + c, v);
-                if (b) st(P + (ptrdiff_t)(y + k) * pitch + c, v);
-            }
+    if (xe < x0 || ye < y0) return;  // the tile holds no pixel of this level
+    const bool L = x0 == 0, R = xe == W - 1, T = y0 == 0, B = ye == H - 1;
+    if (!(L || R || T || B)) return;
+    const int ry0 = T ? -kApron : y0, ry1 = B ? H - 1 + kApron : ye;  // rows of the side strips
+    const int sh = ry1 - ry0 + 1, tw = xe - x0 + 1;
+    auto put = [&](int ax, int ay) {
+        float vI, vx, vy;
+        value(min(max(ax, 0), W - 1), min(max(ay, 0), H - 1), vI, vx, vy);
+        const ptrdiff_t o = (ptrdiff_t)ay * pitch + ax;
+        st(I + o, vI);
+        if (grad) {
+            st(Ix + o, vx);
+            st(Iy + o, vy);
         }
-    }
+    };
+    if (L)
+        for (int i = threadIdx.x; i < kApron * sh; i += blockDim.x) put(i % kApron - kApron, ry0 + i / kApron);
+    if (R)
+        for (int i = threadIdx.x; i < kApron * sh; i += blockDim.x) put(W + i % kApron, ry0 + i / kApron);
+    if (T)
+        for (int i = threadIdx.x; i < kApron * tw; i += blockDim.x) put(x0 + i % tw, i / tw - kApron);
+    if (B)
+        for (int i = threadIdx.x; i < kApron * tw; i += blockDim.x) put(x0 + i % tw, H + i / tw);
 }
 
 // Level 0 of the tile: I and Sobel / 8 straight from the staged bytes, four
@@ -174,15 +184,21 @@ __device__ __forceinline__ void level0(const PyrFrame& F, const LevelGeom& g, co
                 }
             }
         }
-        if (!INTERIOR) {  // tiles inside the frame hold no edge pixel
-            for (int k = 0; k < 4 && X0 + tx + k < F.W; ++k) {
-                apron_pixel(I, g.pitch, F.W, F.H, X0 + tx + k, y, vI[k]);
-                if (F.with_grad) {
-                    apron_pixel(Ix, g.pitch, F.W, F.H, X0 + tx + k, y, vx[k]);
-                    apron_pixel(Iy, g.pitch, F.W, F.H, X0 + tx + k, y, vy[k]);
-                }
-            }
-        }
+    }
+    if (!INTERIOR) {  // tiles inside the frame hold no edge pixel; values from the staged bytes
+        auto value = [&](int x, int y, float& vI, float& vx, float& vy) {
+            const unsigned char* rm = R.row(max(y - 1, 0) - gy0);
+            const unsigned char* rc = R.row(y - gy0);
+            const unsigned char* rp = R.row(min(y + 1, F.H - 1) - gy0);
+            const int xm = max(x - 1, 0) - gx0, xc = x - gx0, xp = min(x + 1, F.W - 1) - gx0;
+            const int sx = ((int)rm[xp] - rm[xm]) + 2 * ((int)rc[xp] - rc[xm]) + ((int)rp[xp] - rp[xm]);
+            const int sy = ((int)rp[xm] - rm[xm]) + 2 * ((int)rp[xc] - rm[xc]) + ((int)rp[xp] - rm[xp]);
+            vI = (float)rc[xc];
+            vx = (float)sx * 0.125f;
+            vy = (float)sy * 0.125f;
+        };
+        apron_strips(I, Ix, Iy, F.with_grad, g.pitch, F.W, F.H, X0, Y0, min(X0 + kTX, F.W) - 1,
+                     min(Y0 + TY, F.H) - 1, value);
     }
 }
 
@@ -238,7 +254,6 @@ __device__ __forceinline__ void coarse_levels(const PyrFrame& F, const LevelGeom
             const size_t o = (size_t)y * g.pitch + x;
             const float v = cur[yc * rw + xc];
             st(I + o, v);
-            if (!INTERIOR) apron_pixel(I, g.pitch, g.W, g.H, x, y, v);
             if (F.with_grad) {
                 const float gx = (cur[ym * rw + xp] - cur[ym * rw + xm]) + 2.f * (cur[yc * rw + xp] - cur[yc * rw + xm]) +
                                  (cur[yp * rw + xp] - cur[yp * rw + xm]);
@@ -246,11 +261,24 @@ __device__ __forceinline__ void coarse_levels(const PyrFrame& F, const LevelGeom
                                  (cur[yp * rw + xp] - cur[ym * rw + xp]);
                 st(Ix + o, gx * 0.125f);
                 st(Iy + o, gy * 0.125f);
-                if (!INTERIOR) {
-                    apron_pixel(Ix, g.pitch, g.W, g.H, x, y, gx * 0.125f);
-                    apron_pixel(Iy, g.pitch, g.W, g.H, x, y, gy * 0.125f);
-                }
             }
+        }
+        if (!INTERIOR) {  // values from the level's region in shared memory
+            auto value = [&](int x, int y, float& vI, float& vx, float& vy) {
+                const int xc = x - ox, yc = y - oy;
+                const int xm = max(x - 1, 0) - ox, xp = min(x + 1, g.W - 1) - ox;
+                const int ym = max(y - 1, 0) - oy, yp = min(y + 1, g.H - 1) - oy;
+                vI = cur[yc * rw + xc];
+                const float gx = (cur[ym * rw + xp] - cur[ym * rw + xm]) + 2.f * (cur[yc * rw + xp] - cur[yc * rw + xm]) +
+                                 (cur[yp * rw + xp] - cur[yp * rw + xm]);
+                const float gy = (cur[yp * rw + xm] - cur[ym * rw + xm]) + 2.f * (cur[yp * rw + xc] - cur[ym * rw + xc]) +
+                                 (cur[yp * rw + xp] - cur[ym * rw + xp]);
+                vx = gx * 0.125f;
+                vy = gy * 0.125f;
+            };
+            const int x0 = X0 >> l, y0 = Y0 >> l;
+            apron_strips(I, Ix, Iy, F.with_grad, g.pitch, g.W, g.H, x0, y0, min(x0 + tw, g.W) - 1,
+                         min(y0 + th, g.H) - 1, value);
         }
     }
 }

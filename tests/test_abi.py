@@ -77,9 +77,11 @@ def test_pyramid_layout(storage):
         p = a["pitch"][l]
         assert p * es % 128 == 0 and p >= a["W"][l] + 2 * A
         for off in (a["off_I"][l], a["off_Ix"][l], a["off_Iy"][l]):
-            start = off - (A * p + A) * es  # the plane with its replicated border
-            assert start % 256 == 0 and off % (4 * es) == 0  # the builder stores four values at once
-            spans.append((start, start + p * (a["H"][l] + 2 * A) * es))
+            assert off % 128 == 0  # every row of the level starts on a 128-byte boundary
+            first = off - (A * p + A) * es  # pixel (-A, -A) of the replicated border
+            last = off + ((a["H"][l] + A - 1) * p + a["W"][l] + A) * es  # one past (W + A - 1, H + A - 1)
+            assert first >= 0
+            spans.append((first, last))
     spans.sort()
     assert all(e0 <= s1 for (_, e0), (s1, _) in zip(spans, spans[1:])) and spans[-1][1] <= a["bytes"]
     assert a["bytes"] > b["bytes"] and dgf.pyramid_bytes(1242, 375, 5, storage, True) == a["bytes"]
