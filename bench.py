@@ -221,11 +221,16 @@ def run_batched(dgf, torch, dev, reps: int = 10):
     t_dp = timed(1 | 2, 10 * reps)
     npts = sum(bt.n)
     # algorithmic bytes of detection + both pyramids: frame 1 read twice, frame 2
-    # once, key-points written, 3 FP32 planes of frame 1 and 1 of frame 2 per level
-    nbytes = 0
+    # once, key-points written, 3 FP32 planes of frame 1 and 1 of frame 2 per level,
+    # each with its replicated border (DGF_PYR_APRON pixels on every side: the
+    # clamped taps tracking reads without clamping), which the builder must write too
+    A = dgf.PYR_APRON
+    nbytes = nbytes_inner = 0
     for (W, H, win, step), n in zip(specs, bt.n):
         px = sum((W >> l) * (H >> l) for l in range(prm.levels))
-        nbytes += 3 * W * H + 8 * n + 4 * 4 * px
+        px_b = sum(((W >> l) + 2 * A) * ((H >> l) + 2 * A) for l in range(prm.levels))
+        nbytes += 3 * W * H + 8 * n + 4 * 4 * px_b
+        nbytes_inner += 3 * W * H + 8 * n + 4 * 4 * px
     gbs = nbytes / (t_dp / 1e3) / 1e9
     return {"workload": "64 mixed pairs 640x480..1280x720, step 2..6, window 8, 3 levels, 9x9, model 4, FP32, "
                         "one rlof_track_many call replayed from a CUDA graph",
@@ -236,7 +241,9 @@ def run_batched(dgf, torch, dev, reps: int = 10):
             "autotune": {"lanes_per_point": tuned["lanes"], "ms_per_batch_by_lanes": tuned["ms"]},
             "detect_pyramid": {"ms": t_dp, "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
                                "frac_of_measured_hbm": gbs / HBM_PEAK_GBS, "peak_gbs": HBM_PEAK_GBS,
-                               "peak_source": PEAK_SOURCE}}
+                               "peak_source": PEAK_SOURCE,
+                               "bytes_without_border": nbytes_inner,
+                               "frac_without_border": nbytes_inner / (t_dp / 1e3) / 1e9 / HBM_PEAK_GBS}}
 
 
 def _timed(torch, dev, fn, reps, flush):
@@ -299,8 +306,10 @@ def hbm_context(W: int, H: int, n: int, ms_per_step: float):
     """The whole step's HBM fraction under two byte models, reported beside the FP32
     fraction of tracking (the step is ALU-bound, so both are small): I/O only (both
     frames in; points, flow and status out) and with the pyramid materialised (4
-    FP32 planes over the levels written once and read once, the points re-read)."""
-    px = sum((W >> l) * (H >> l) for l in range(WORKLOAD["levels"]))
+    FP32 planes over the levels, their replicated borders included, written once
+    and read once, the points re-read)."""
+    A = 12  # the pyramid planes' replicated border (DGF_PYR_APRON)
+    px = sum(((W >> l) + 2 * A) * ((H >> l) + 2 * A) for l in range(WORKLOAD["levels"]))
     io = 2 * W * H + n * (8 + 8 + 1)
     mat = io + 2 * 4 * 4 * px + 8 * n
     gbs = lambda b: b / (ms_per_step / 1e3) / 1e9

@@ -59,6 +59,19 @@ const char* dgf_strerror(int code);
 /* Library ABI version (major * 100 + minor). */
 int dgf_version(void);
 
+/*
+ * Device status of the current device: *stalls = the number of thread blocks that
+ * gave up waiting for their staging copies since the last reset (detection and the
+ * pyramid stage frame rows with bulk asynchronous copies when the frame's base,
+ * pitch and width are multiples of 16; a block whose copies never complete gives up
+ * after a bounded wait, leaves its outputs unwritten and counts here; 0 means every
+ * launch ran to the end). reset = 1 also clears it. Synchronous: it waits for the
+ * device's pending work. The first call on a device, or the first launch of those
+ * kernels, looks the word's address up; make it before any stream capture.
+ * Returns DGF_ERR_ARG for a null stalls, DGF_ERR_CUDA if the word cannot be read.
+ */
+int dgf_device_status(unsigned* stalls, int reset);
+
 /* ---- DeGraF detection (Section 2, Eq. 1-2) ------------------------------- */
 
 /*

@@ -37,7 +37,7 @@ EXPORTS = (
     "dgf_degraf_backward_workspace", "degraf_detect_backward", "dgf_rlof_backward_workspace", "rlof_track_backward",
     "dgf_gm_params_default", "dgf_gm_workspace", "rlof_track_gm", "dgf_fb_workspace", "rlof_track_fb",
     "dgf_epic_params_default", "dgf_epic_workspace", "epic_interpolate",
-    "dgf_fp32_probe", "dgf_fp32_probe_flops", "dgf_epic_exp_neg",
+    "dgf_fp32_probe", "dgf_fp32_probe_flops", "dgf_epic_exp_neg", "dgf_device_status",
 )
 
 
@@ -146,6 +146,7 @@ def load(build_if_missing: bool = True):
     L.dgf_fp32_probe.argtypes, L.dgf_fp32_probe.restype = [P, I, I, I, I, P], I
     L.dgf_fp32_probe_flops.argtypes, L.dgf_fp32_probe_flops.restype = [I, I, I, I], ctypes.c_double
     L.dgf_epic_exp_neg.argtypes, L.dgf_epic_exp_neg.restype = [P, P, I, P], I
+    L.dgf_device_status.argtypes, L.dgf_device_status.restype = [ctypes.POINTER(ctypes.c_uint), I], I
     _lib = L
     return L
 

@@ -135,6 +135,15 @@ class EpicParams:
                                 self.min_spread)
 
 
+def device_status(reset: bool = False) -> int:
+    """Thread blocks of detection or the pyramid that gave up waiting for their
+    staging copies on the current device since the last reset (0: every launch ran
+    to the end). Synchronises the device."""
+    v = ctypes.c_uint(0)
+    check("dgf_device_status", load().dgf_device_status(ctypes.byref(v), int(reset)))
+    return int(v.value)
+
+
 def version() -> int:
     return int(load().dgf_version())
 

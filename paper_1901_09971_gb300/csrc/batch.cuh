@@ -15,10 +15,12 @@ struct PyrFrame {
     int W, H, pitch, with_grad;
     char* base;     // pyramid buffer
     int cta_begin;  // first CTA of this frame in the launch
+    int bulk;       // set by launch_pyramids: frame base, pitch and width multiples of 16 (bulk row copies)
 };
 
 struct PyrBatch {
     int levels, n_frames;
+    unsigned* status;  // the device status word (nullable)
     PyrFrame frames[2 * kMaxBatchPairs];
 };
 
@@ -32,10 +34,12 @@ struct DetectJob {
     int32_t* sums;
     int cta_begin;  // first CTA of this frame in the launch
     int tiles_x;    // CTAs per row of windows
+    int bulk;       // set by launch_detect: frame base, pitch and width multiples of 16 (bulk row copies)
 };
 
 struct DetectBatch {
     int ww, wh, by, vr, staged, tile_w, tile_h, n_jobs;  // vr: windows per thread along y
+    unsigned* status;  // the device status word (nullable)
     DetectJob jobs[kMaxBatchPairs];
 };
 

@@ -26,6 +26,56 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Bulk asynchronous copies (cp.async.bulk: the tensor-memory-access engine's
+// untiled form, sm_90+) of contiguous global bytes into shared memory, completed
+// on a shared-memory mbarrier that counts the bytes. Source and destination must
+// be 16-byte aligned and the size a multiple of 16.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// One arrival that also announces the bytes the phase's copies will deliver.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_copy_to_smem(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// Waits for phase `parity` of the barrier to complete, giving up after max_tries
+// polls (each may suspend the thread for a short while); returns false then.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned max_tries)
+{
+    const unsigned a = smem_addr(bar);
+    for (unsigned i = 0; i < max_tries; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// Polls of a staging wait before a block gives up on its copies (far beyond the
+// microseconds a copy takes; reaching it means the copy engine stopped answering).
+constexpr unsigned kStageWaitTries = 1u << 22;
+
+// Device address of the library's status word on the current device (counts
+// staging waits that gave up; read by dgf_device_status), or null if it cannot be
+// looked up. The first call on a device looks the address up (outside any stream
+// capture); later calls return the cached value.
+unsigned* status_word();
+
 // Rounds v up to a multiple of a, a power of two.
 __host__ __device__ __forceinline__ size_t round_up(size_t v, size_t a) { return (v + a - 1) & ~(a - 1); }
 

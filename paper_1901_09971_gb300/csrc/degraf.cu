@@ -56,13 +56,14 @@ __device__ __forceinline__ void emit(const DetectJob& J, int ww, int wh, int u, 
 }
 
 // Staged tile rows: byte (r, c) of the tile (frame pixel (x0 + c, y0 + r)) sits at
-// tile[r * stride + mis(r) + c], where mis(r) is the misalignment of that frame row's
-// byte x0 (rows advance by the pitch, so it steps by pitch mod 4).
+// tile[r * stride + mis(r) + c]. Word copies: mis(r) is the misalignment of that
+// frame row's byte x0 (rows advance by the pitch, so it steps by pitch mod 4, mask
+// 3). Bulk copies: every row has the same offset, x0 mod 16 (pmod 0, mask 15).
 struct Tile {
     const uint8_t* bytes;
     int stride;
-    unsigned mis0, pmod;
-    __device__ __forceinline__ unsigned mis(int r) const { return (mis0 + (unsigned)r * pmod) & 3u; }
+    unsigned mis0, pmod, mask;
+    __device__ __forceinline__ unsigned mis(int r) const { return (mis0 + (unsigned)r * pmod) & mask; }
 };
 
 // Window sums of a window of width <= 8 at tile column c0, row r0: per row, the
@@ -91,7 +92,7 @@ __device__ __forceinline__ void window_sums_packed(const Tile& T, int c0, int r0
         y += i * rs;
         mx = __vmaxu4(mx, __vmaxu4(lo, hi));
         base += T.stride >> 2;
-        mis = (mis + T.pmod) & 3u;  // next row's misalignment
+        mis = (mis + T.pmod) & T.mask;  // next row's offset
     }
     mx = __vmaxu4(mx, mx >> 16);
     mx = __vmaxu4(mx, mx >> 8);
@@ -135,7 +136,7 @@ __device__ __forceinline__ void column_window_sums(const Tile& T, int c0, int r0
         Q[r + 1] = Q[r] + r * rs;
         PX[r + 1] = PX[r] + rx;
         rm[r] = __vmaxu4(lo, hi);
-        mis = (mis + T.pmod) & 3u;
+        mis = (mis + T.pmod) & T.mask;
     }
     // pairwise maxima over 2 and 4 consecutive rows (unused entries are never formed)
     unsigned m2[R], m4[R];
@@ -193,8 +194,9 @@ __device__ __forceinline__ void window_sums_bytes(const uint8_t* w0, int rstride
 // Each thread owns a window column and vr consecutive windows along it; a CTA covers
 // 32 x (by vr) windows of one frame, and the CTAs of all frames of the batch share
 // one grid. When windows overlap (step < window) the CTA stages the union of their
-// pixels with asynchronous 4-byte copies of the aligned words holding them (large
-// tiles: few staging round trips per SM), otherwise threads read the frame directly.
+// pixels (large tiles: few staging round trips per SM): with one bulk copy per row
+// when the frame's base, pitch and width are multiples of 16, else with 4-byte
+// copies of the aligned words holding them; otherwise threads read the frame directly.
 __global__ void __launch_bounds__(256) degraf_detect_kernel(const __grid_constant__ DetectBatch a)
 {
     extern __shared__ __align__(16) uint8_t tile[];
@@ -214,22 +216,44 @@ __global__ void __launch_bounds__(256) degraf_detect_kernel(const __grid_constan
     const int u0 = (t % J.tiles_x) * kBX, v0 = (t / J.tiles_x) * wy;
     const int x0 = u0 * J.step, y0 = v0 * J.step;
     const long long org = (long long)(uintptr_t)J.img + (long long)y0 * J.pitch + x0;
-    const Tile T{tile, a.tile_w, (unsigned)org & 3u, (unsigned)J.pitch & 3u};
+    const Tile T = J.bulk ? Tile{tile, a.tile_w, (unsigned)x0 & 15u, 0u, 15u}
+                          : Tile{tile, a.tile_w, (unsigned)org & 3u, (unsigned)J.pitch & 3u, 3u};
     if (a.staged) {
-        // every aligned word holding a byte of the tile (such a word lies inside the
-        // frame's allocation); tile rows past the frame are never read
+        // tile rows past the frame are never read
         const int tw = min((kBX - 1) * J.step + a.ww, J.W - x0);
         const int th = min((wy - 1) * J.step + a.wh, J.H - y0);
-        const int nwr = (tw + 3 + 3) >> 2;  // words per row, misalignment included
-        const int nthr = kBX * blockDim.y;
-        for (int i = threadIdx.y * kBX + threadIdx.x; i < th * nwr; i += nthr) {
-            const int r = i / nwr, k = i - r * nwr;
-            const int c_lo = 4 * k - (int)T.mis(r);  // tile column of the word's first byte
-            if (c_lo >= tw) continue;
-            cp_async4(tile + r * a.tile_w + 4 * k, J.img + (long long)(y0 + r) * J.pitch + x0 + c_lo);
+        const int nthr = kBX * blockDim.y, tid = threadIdx.y * kBX + threadIdx.x;
+        if (J.bulk) {
+            // frame base, pitch and width multiples of 16: one bulk copy per row of
+            // the 16-byte aligned span covering the tile's columns (it stays inside
+            // the row), all completing on one barrier
+            __shared__ __align__(8) uint64_t bar;
+            if (tid == 0) mbar_init(&bar, 1);
+            __syncthreads();
+            const int a_lo = x0 & ~15, a_hi = (x0 + tw + 15) & ~15;
+            if (tid == 0) mbar_arrive_expect_tx(&bar, (unsigned)(th * (a_hi - a_lo)));
+            for (int r = tid; r < th; r += nthr)
+                bulk_copy_to_smem(tile + r * a.tile_w, J.img + (long long)(y0 + r) * J.pitch + a_lo,
+                                  (unsigned)(a_hi - a_lo), &bar);
+            const bool ok = mbar_wait(&bar, 0, kStageWaitTries);
+            if (!__syncthreads_and(ok)) {  // the copy engine stopped answering: record, drain, leave
+                if (tid == 0 && a.status) atomicAdd(a.status, 1u);
+                mbar_wait(&bar, 0, kStageWaitTries);
+                return;
+            }
+        } else {
+            // every aligned word holding a byte of the tile (such a word lies inside
+            // the frame's allocation)
+            const int nwr = (tw + 3 + 3) >> 2;  // words per row, misalignment included
+            for (int i = tid; i < th * nwr; i += nthr) {
+                const int r = i / nwr, k = i - r * nwr;
+                const int c_lo = 4 * k - (int)T.mis(r);  // tile column of the word's first byte
+                if (c_lo >= tw) continue;
+                cp_async4(tile + r * a.tile_w + 4 * k, J.img + (long long)(y0 + r) * J.pitch + x0 + c_lo);
+            }
+            cp_async_wait_all();
+            __syncthreads();
         }
-        cp_async_wait_all();
-        __syncthreads();
     }
     const int u = u0 + threadIdx.x;
     if (u >= J.nu) return;
@@ -283,9 +307,10 @@ int launch_detect(DetectBatch& a, cudaStream_t stream)
         max_step = a.jobs[f].step > max_step ? a.jobs[f].step : max_step;
         overlap = overlap && (a.jobs[f].step < a.ww || a.jobs[f].step < a.wh);
     }
-    // row stride: the tile's bytes, up to 3 bytes of row misalignment, and room for
-    // the packed path's three aligned word loads from a window's first byte
-    const int tile_w = ((kBX - 1) * max_step + a.ww + 3 + 12 + 3) / 4 * 4;
+    // row stride: the tile's bytes, up to 15 bytes of row offset, and room for the
+    // packed path's three aligned word loads from a window's first byte; a multiple
+    // of 16 for the bulk row copies
+    const int tile_w = ((kBX - 1) * max_step + a.ww + 15 + 12 + 15) / 16 * 16;
     int by = 8, vr = 4;
     auto tile_h = [&]() { return (by * vr - 1) * max_step + a.wh; };
     while (tile_w * tile_h() > kSmemMax && (vr > 1 || by > 1)) {
@@ -300,8 +325,12 @@ int launch_detect(DetectBatch& a, cudaStream_t stream)
     a.tile_w = tile_w;  // row stride of the staged tile
     a.tile_h = tile_h();
     long long ctas = 0;
+    a.status = status_word();
     for (int f = 0; f < a.n_jobs; ++f) {
         DetectJob& J = a.jobs[f];
+        // rows whose 16-byte spans end at or before the row's last byte: no copy reads
+        // past the frame, whatever lies beyond its last row
+        J.bulk = aligned(J.img, 16) && J.pitch % 16 == 0 && J.W % 16 == 0;
         J.tiles_x = (J.nu + kBX - 1) / kBX;
         J.cta_begin = (int)ctas;
         ctas += (long long)J.tiles_x * ((J.nv + by * vr - 1) / (by * vr));

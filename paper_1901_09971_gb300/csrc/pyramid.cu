@@ -31,8 +31,9 @@ __host__ __device__ constexpr int tile_h(int levels) { return levels <= 4 ? 128 
 __host__ __device__ constexpr int halo(int levels) { return levels >= 2 ? 1 << (levels - 1) : 1; }
 __host__ __device__ constexpr int region_w(int levels) { return kTX + 2 * halo(levels); }
 __host__ __device__ constexpr int region_h(int levels) { return tile_h(levels) + 2 * halo(levels); }
-// staged row pitch: the region's bytes plus up to 3 bytes of row misalignment
-__host__ __device__ constexpr int region_pitch(int levels) { return (region_w(levels) + 3 + 3) & ~3; }
+// staged row pitch: the region's bytes plus up to 15 bytes of row offset on either
+// side (bulk copies move 16-byte-aligned spans), a multiple of 16
+__host__ __device__ constexpr int region_pitch(int levels) { return (region_w(levels) + 32 + 15) & ~15; }
 
 __host__ __device__ inline int frame_ctas(int W, int H, int levels)
 {
@@ -68,15 +69,16 @@ __device__ __forceinline__ void store4<__half>(__half* p, float a, float b, floa
 }
 
 // Staged region rows: byte (r, c) of the halo'd region (frame pixel (gx0 + c,
-// gy0 + r)) sits at raw[r * RWP + mis(r) + c], where mis(r) is the misalignment of
-// that frame row's byte gx0 (rows advance by the pitch, so it steps by pitch mod 4).
+// gy0 + r)) sits at raw[r * RWP + mis(r) + c]. Word copies: mis(r) is the
+// misalignment of that frame row's byte gx0 (rows advance by the pitch, so it steps
+// by pitch mod 4, mask 3). Bulk copies: every row has the same offset, gx0 mod 16.
 struct Staged {
     const unsigned char* raw;
-    unsigned mis0, pmod;
+    unsigned mis0, pmod, mask;
     int RWP;
     __device__ __forceinline__ const unsigned char* row(int r) const
     {
-        return raw + r * RWP + ((mis0 + (unsigned)r * pmod) & 3u);
+        return raw + r * RWP + ((mis0 + (unsigned)r * pmod) & mask);
     }
 };
 
@@ -315,7 +317,8 @@ __global__ void __launch_bounds__(kThreads, pyramid_min_blocks<L>()) pyramid_ker
     __syncthreads();
     const PyrFrame& F = a.frames[frame];
     constexpr int h = halo(L), TY = tile_h(L);
-    constexpr int RW = region_w(L), RH = region_h(L), RWP = region_pitch(L), NWR = RWP / 4;
+    constexpr int RW = region_w(L), RH = region_h(L), RWP = region_pitch(L);
+    constexpr int NWR = (RW + 3 + 3) / 4;  // aligned words per row for the word copies (misalignment included)
     const int t = blockIdx.x - F.cta_begin;
     const int tiles_x = (F.W + kTX - 1) / kTX;
     const int X0 = (t % tiles_x) * kTX, Y0 = (t / tiles_x) * TY;
@@ -323,21 +326,46 @@ __global__ void __launch_bounds__(kThreads, pyramid_min_blocks<L>()) pyramid_ker
     // the halo'd region inside the frame: no clamping at any level
     const bool interior = gx0 >= 0 && gy0 >= 0 && gx0 + RW <= F.W && gy0 + RH <= F.H;
 
-    // 1. stage the frame bytes under the tile and its halo: every aligned 4-byte word
-    // that holds a byte of the region inside the frame (such a word lies inside the
-    // frame's allocation), copied asynchronously; bytes outside the frame are never read
-    const long long org = (long long)(uintptr_t)F.img + (long long)gy0 * F.pitch + gx0;
-    Staged R{smem, (unsigned)org & 3u, (unsigned)F.pitch & 3u, RWP};
-    const int cx0 = max(gx0, 0) - gx0, cx1 = min(gx0 + RW, F.W) - gx0;  // region columns inside the frame
-    for (int i = threadIdx.x; i < RH * NWR; i += kThreads) {
-        const int r = i / NWR, k = i - r * NWR;
-        const int gy = gy0 + r;
-        const int c_lo = 4 * k - (int)((R.mis0 + (unsigned)r * R.pmod) & 3u);  // region column of the word's first byte
-        if (gy < 0 || gy >= F.H || c_lo + 3 < cx0 || c_lo >= cx1) continue;
-        cp_async4(smem + r * RWP + 4 * k, F.img + (long long)gy * F.pitch + gx0 + c_lo);
+    // 1. stage the frame bytes under the tile and its halo (rows and columns inside the
+    // frame; bytes outside it are never read)
+    Staged R;
+    if (F.bulk) {
+        // frame base, pitch and width multiples of 16: one bulk copy per row of the
+        // 16-byte aligned span covering the row's columns inside the frame (it stays
+        // inside the row), all completing on one barrier
+        __shared__ __align__(8) uint64_t bar;
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        const int r_lo = max(gy0, 0) - gy0, r_hi = min(gy0 + RH, F.H) - gy0;
+        const int a_lo = max(gx0, 0) & ~15, a_hi = (min(gx0 + RW, F.W) + 15) & ~15;  // frame byte span
+        const int base = gx0 & ~15;  // frame column at staged byte 0 of every row
+        if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, (unsigned)((r_hi - r_lo) * (a_hi - a_lo)));
+        for (int r = r_lo + (int)threadIdx.x; r < r_hi; r += kThreads)
+            bulk_copy_to_smem(smem + r * RWP + (a_lo - base), F.img + (long long)(gy0 + r) * F.pitch + a_lo,
+                              (unsigned)(a_hi - a_lo), &bar);
+        const bool ok = mbar_wait(&bar, 0, kStageWaitTries);
+        if (!__syncthreads_and(ok)) {  // the copy engine stopped answering: record, drain, leave
+            if (threadIdx.x == 0 && a.status) atomicAdd(a.status, 1u);
+            mbar_wait(&bar, 0, kStageWaitTries);
+            return;
+        }
+        R = Staged{smem, (unsigned)(gx0 - base), 0u, 15u, RWP};
+    } else {
+        // otherwise every aligned 4-byte word that holds a byte of the region (such a
+        // word lies inside the frame's allocation), copied asynchronously
+        const long long org = (long long)(uintptr_t)F.img + (long long)gy0 * F.pitch + gx0;
+        R = Staged{smem, (unsigned)org & 3u, (unsigned)F.pitch & 3u, 3u, RWP};
+        const int cx0 = max(gx0, 0) - gx0, cx1 = min(gx0 + RW, F.W) - gx0;  // region columns inside the frame
+        for (int i = threadIdx.x; i < RH * NWR; i += kThreads) {
+            const int r = i / NWR, k = i - r * NWR;
+            const int gy = gy0 + r;
+            const int c_lo = 4 * k - (int)((R.mis0 + (unsigned)r * R.pmod) & 3u);  // region column of the word's first byte
+            if (gy < 0 || gy >= F.H || c_lo + 3 < cx0 || c_lo >= cx1) continue;
+            cp_async4(smem + r * RWP + 4 * k, F.img + (long long)gy * F.pitch + gx0 + c_lo);
+        }
+        cp_async_wait_all();
+        __syncthreads();
     }
-    cp_async_wait_all();
-    __syncthreads();
 
     if (interior) {
         level0<TS, true, TY>(F, geo[0], R, X0, Y0, h);
@@ -353,9 +381,14 @@ int launch_pyramids(PyrBatch& a, int storage, cudaStream_t stream)
 {
     long long ctas = 0;
     for (int f = 0; f < a.n_frames; ++f) {
-        a.frames[f].cta_begin = (int)ctas;
-        ctas += frame_ctas(a.frames[f].W, a.frames[f].H, a.levels);
+        PyrFrame& F = a.frames[f];
+        F.cta_begin = (int)ctas;
+        // rows whose 16-byte spans end at or before the row's last byte: no copy reads
+        // past the frame, whatever lies beyond its last row
+        F.bulk = aligned(F.img, 16) && F.pitch % 16 == 0 && F.W % 16 == 0;
+        ctas += frame_ctas(F.W, F.H, a.levels);
     }
+    a.status = status_word();
     if (ctas == 0) return DGF_OK;
     if (ctas > 0x7fffffffLL) return DGF_ERR_ARG;
     const size_t smem = smem_bytes(a.levels);

@@ -319,6 +319,7 @@ def test_probe_host_checks_and_flop_count():
     assert lib.dgf_epic_exp_neg(None, None, -1, None) == _abi.DGF_ERR_ARG
     assert lib.dgf_epic_exp_neg(None, None, 5, None) == _abi.DGF_ERR_ARG
     assert lib.dgf_epic_exp_neg(None, None, 0, None) == _abi.DGF_OK
+    assert lib.dgf_device_status(None, 0) == _abi.DGF_ERR_ARG
 
 
 def test_noalloc_scratch_size_matches_the_header():

@@ -109,6 +109,30 @@ def test_detect_pitched_frame(dgf):
     assert np.abs(pts_g - pts_o).max() <= TOL_PTS
 
 
+@pytest.mark.parametrize("W,pitch", [(160, 192), (1024, 1024), (150, 192)])
+def test_bulk_and_word_staging_agree_with_the_oracle(dgf, W, pitch):
+    """Detection and the pyramid stage frame rows with bulk copies when the frame's
+    base, pitch and width are multiples of 16 (the first two cases) and with word
+    copies otherwise (the last): key-points, exact sums and FP32 pyramid planes equal
+    the oracle's either way, and no block gave up waiting for its copies."""
+    H = 90
+    rng = np.random.default_rng(W + pitch)
+    big = rng.integers(0, 256, size=(H, pitch)).astype(np.uint8)
+    dev = to_dev(big)[:, :W]
+    assert dev.stride(0) == pitch and dev.data_ptr() % 16 == 0
+    dgf.device_status(reset=True)
+    pts_g, sums_g = dgf.detect(dev, 7, 3, with_sums=True)
+    pts_o, sums_o, _ = oracle.degraf_detect(big[:, :W].copy(), 7, 7, 3)
+    assert np.array_equal(sums_g.cpu().numpy().astype(np.int64), sums_o[:, :4])
+    assert np.abs(pts_g.cpu().numpy() - pts_o).max() <= TOL_PTS
+    buf = dgf.build_pyramid(dev, 3, 0, True)
+    lay = dgf.pyramid_layout(W, H, 3, 0, True)
+    for planes, oref in zip(dgf.pyramid_planes(buf, lay), oracle.pyramid(big[:, :W].copy(), 3)):
+        for g, o in zip(planes, oref):
+            assert np.array_equal(g.cpu().numpy(), o.astype(np.float32))
+    assert dgf.device_status() == 0
+
+
 def test_detect_empty(dgf):
     pts = dgf.detect(torch.zeros((5, 40), dtype=torch.uint8, device="cuda"), 8, 4)
     assert pts.shape == (0, 2)
