@@ -191,13 +191,16 @@ def run_batched(dgf, torch, dev, reps: int = 10):
     """The mixed-size batch workload: 64 pairs (640x480 .. 1280x720, step 2..6,
     window 8, 3 levels, 9x9 support) through one rlof_track_many call replayed from
     a CUDA graph; detection + pyramids are also timed alone (stages 1|2) for their
-    HBM roofline."""
+    HBM roofline. Under torchrun every rank tracks its longest-processing-time
+    share of the batch (shard.ShardedBatch) and the time is the slowest rank's."""
+    from paper_1901_09971_gb300 import shard
     specs = [(W, H, 8, st) for (W, H, st) in synth.make_batch_specs(64, 3000)]
-    frames = [synth.make_translation_pair(W, H, seed=3000 + i) for i, (W, H, _, _) in enumerate(specs)]
+    prm = dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)
+    runner = shard.ShardedBatch(specs, prm, dev)
+    frames = [synth.make_translation_pair(specs[i][0], specs[i][1], seed=3000 + i) for i in runner.indices]
     d1 = [torch.from_numpy(p.I1).to(dev) for p in frames]
     d2 = [torch.from_numpy(p.I2).to(dev) for p in frames]
-    prm = dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)
-    bt = dgf.BatchTracker(specs, prm, dev)
+    bt = runner.tracker
     bt.bind(d1, d2)
     with tempfile.TemporaryDirectory() as tmp:  # the launch shape, tuned on this batch
         tuned = bt.autotune(reps=3, path=os.path.join(tmp, "tune.json"))
@@ -209,17 +212,18 @@ def run_batched(dgf, torch, dev, reps: int = 10):
         for _ in range(3):
             bt.run(use_graph=True, stages=stages)
         torch.cuda.synchronize(dev)
+        shard.barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(reps):
             bt.run(use_graph=True, stages=stages)
         b.record(stream)
         b.synchronize()
-        return a.elapsed_time(b) / reps
+        return shard.reduce_scalar(a.elapsed_time(b) / reps, "max", device=dev)
 
     t_all = timed(7, reps)
     t_dp = timed(1 | 2, 10 * reps)
-    npts = sum(bt.n)
+    specs = runner.specs  # byte model below: this rank's share
     # algorithmic bytes of detection + both pyramids: frame 1 read twice, frame 2
     # once, key-points written, 3 FP32 planes of frame 1 and 1 of frame 2 per level,
     # each with its replicated border (DGF_PYR_APRON pixels on every side: the
@@ -231,19 +235,24 @@ def run_batched(dgf, torch, dev, reps: int = 10):
         px_b = sum(((W >> l) + 2 * A) * ((H >> l) + 2 * A) for l in range(prm.levels))
         nbytes += 3 * W * H + 8 * n + 4 * 4 * px_b
         nbytes_inner += 3 * W * H + 8 * n + 4 * 4 * px
+    nbytes = shard.reduce_scalar(nbytes, "sum", device=dev)
+    nbytes_inner = shard.reduce_scalar(nbytes_inner, "sum", device=dev)
+    npts = int(shard.reduce_scalar(sum(bt.n), "sum", device=dev))
     gbs = nbytes / (t_dp / 1e3) / 1e9
     return {"workload": "64 mixed pairs 640x480..1280x720, step 2..6, window 8, 3 levels, 9x9, model 4, FP32, "
-                        "one rlof_track_many call replayed from a CUDA graph",
+                        "one rlof_track_many call replayed from a CUDA graph"
+                        + (f", sharded over {runner.world} ranks by longest processing time" if runner.world > 1 else ""),
             "timing": f"{reps} (detect + pyramids alone: {10 * reps}) back-to-back runs between two CUDA events "
                       "(working set > L2, no flush)",
             "pairs": 64, "points": npts, "ms_per_batch": t_all, "points_per_s": npts / (t_all / 1e3),
             "pairs_per_s": 64 / (t_all / 1e3),
             "autotune": {"lanes_per_point": tuned["lanes"], "ms_per_batch_by_lanes": tuned["ms"]},
             "detect_pyramid": {"ms": t_dp, "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
-                               "frac_of_measured_hbm": gbs / HBM_PEAK_GBS, "peak_gbs": HBM_PEAK_GBS,
+                               "frac_of_measured_hbm": gbs / (HBM_PEAK_GBS * runner.world),
+                               "peak_gbs": HBM_PEAK_GBS * runner.world,
                                "peak_source": PEAK_SOURCE,
                                "bytes_without_border": nbytes_inner,
-                               "frac_without_border": nbytes_inner / (t_dp / 1e3) / 1e9 / HBM_PEAK_GBS}}
+                               "frac_without_border": nbytes_inner / (t_dp / 1e3) / 1e9 / (HBM_PEAK_GBS * runner.world)}}
 
 
 def _timed(torch, dev, fn, reps, flush):
@@ -650,7 +659,11 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    pair = synth.make_pair(2, index=rank)
+    # the step's pairs: one driving-scene pair per rank, split by the same
+    # longest-processing-time partition as any batch (equal costs: pair k on rank k)
+    step_pairs = [(1242, 375, WORKLOAD["win"], WORKLOAD["step"])] * world
+    (mine,), _ = shard.shard_specs(step_pairs, WORKLOAD["levels"], WORKLOAD["radius"], rank, world)
+    pair = synth.make_pair(2, index=mine)
     W, H = pair.W, pair.H
     prm = dgf.RlofParams(levels=WORKLOAD["levels"], radius=WORKLOAD["radius"], max_iter=WORKLOAD["max_iter"],
                          model=WORKLOAD["model"])
@@ -733,12 +746,16 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
     e2e_s = shard.reduce_scalar(e2e_s, "max", device=dev)
     e2e_value = world * n_pts * args.steps / e2e_s
 
+    # the 64-pair batch, every rank tracking its share (all ranks take part)
+    batched = None if args.no_batched else run_batched(dgf, torch, dev)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(WORKLOAD, points_per_pair=n_pts, l2="flushed between steps (256 MiB write)",
-                               parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+                               parallelism=f"pairs sharded over {world} ranks (one pair each per step)"
+                               if world > 1 else "single GPU"),
                 "pairs_per_s": world * args.steps / total_s,
                 "rlof_ms": float(rlof_ms.mean()), "detect_pyramid_ms": float((step_ms - rlof_ms).mean()),
                 "tracked_fraction": float(np.mean((status == 0) | (status == 4))),
@@ -754,9 +771,10 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
                 "gpu_launches": 4 * args.steps,
                 "clocks": clocks.summary()}
         line["hbm_context"] = hbm_context(W, H, n_pts, 1e3 * total_s / args.steps)
+        if batched is not None:
+            line["batched"] = batched
         if not args.no_batched:
             line["small_pair"] = run_small_pair(dgf, torch, dev)
-            line["batched"] = run_batched(dgf, torch, dev)
             line["fp16_storage"] = run_fp16(dgf, torch, dev)
             line["adjoint"] = run_adjoint(dgf, torch, dev)
             line["gm_prior"] = run_gm_prior(dgf, torch, dev, pair)

@@ -59,18 +59,26 @@ const char* dgf_strerror(int code);
 /* Library ABI version (major * 100 + minor). */
 int dgf_version(void);
 
+/* device-side failures (dgf_device_status bits) */
+#define DGF_DEV_STAGE_WAIT 1u     /* a detection or pyramid block gave up waiting for its staging copies */
+#define DGF_DEV_EPIC_PASSES 2u    /* epic_interpolate: the labelling did not settle (pass limit or barrier) */
+#define DGF_DEV_EPIC_CAPACITY 4u  /* epic_interpolate: a neighbourhood search outgrew its largest layout */
+
 /*
- * Device status of the current device: *stalls = the number of thread blocks that
- * gave up waiting for their staging copies since the last reset (detection and the
- * pyramid stage frame rows with bulk asynchronous copies when the frame's base,
- * pitch and width are multiples of 16; a block whose copies never complete gives up
- * after a bounded wait, leaves its outputs unwritten and counts here; 0 means every
- * launch ran to the end). reset = 1 also clears it. Synchronous: it waits for the
- * device's pending work. The first call on a device, or the first launch of those
- * kernels, looks the word's address up; make it before any stream capture.
- * Returns DGF_ERR_ARG for a null stalls, DGF_ERR_CUDA if the word cannot be read.
+ * Device-side failures on the current device since the last reset, as a set of
+ * DGF_DEV_* bits in *bits (0: every launch ran to the end). Kernels report what the
+ * host cannot check before launching here instead of synchronising the caller's
+ * stream: detection and the pyramid stage frame rows with bulk asynchronous copies
+ * when the frame's base, pitch and width are multiples of 16, and a block whose
+ * copies never complete gives up after a bounded wait and leaves its outputs
+ * unwritten; epic_interpolate reports a labelling that did not settle and a search
+ * that outgrew its layout (its dense field is then incomplete). reset = 1 also
+ * clears the word. Synchronous: waits for the device's pending work. The first
+ * call on a device, or the first launch of those kernels, looks the word's address
+ * up; make it before any stream capture.
+ * Returns DGF_ERR_ARG for a null bits, DGF_ERR_CUDA if the word cannot be read.
  */
-int dgf_device_status(unsigned* stalls, int reset);
+int dgf_device_status(unsigned* bits, int reset);
 
 /* ---- DeGraF detection (Section 2, Eq. 1-2) ------------------------------- */
 
@@ -358,13 +366,16 @@ size_t dgf_epic_workspace(int W, int H, int n);
  *   dbg         host struct of nullable device outputs, or NULL.
  *   workspace   device, >= dgf_epic_workspace(W, H, n) bytes, 256-byte aligned.
  * Limits: W + H <= DGF_EPIC_MAX_W_PLUS_H, n <= DGF_EPIC_MAX_POINTS.
- * Synchronises `stream`: the host reads the labelling's convergence counter every
- * four relaxation passes and the device status word at the end (so the call
- * cannot be captured into a CUDA graph).
+ * Asynchronous on `stream` like every entry point: the labelling's passes run in
+ * one cooperative launch that stops at the first pass that changes nothing (at
+ * most 4096), with no host round trip, so the call can follow tracking back to
+ * back and be captured into a CUDA graph (after the first call on the device,
+ * which looks up the status word). A labelling that did not settle and a
+ * neighbourhood search that outgrew its largest shared-memory layout (more than
+ * 8192 discovered or settled seeds) are reported through dgf_device_status
+ * (DGF_DEV_EPIC_PASSES, DGF_DEV_EPIC_CAPACITY).
  * Returns DGF_ERR_ARG for bad arguments or parameters, DGF_ERR_WORKSPACE for a
- * short workspace, DGF_ERR_TIMEOUT if the labelling has not converged after 4096
- * passes, DGF_ERR_DEVICE if a neighbourhood search outgrew its largest
- * shared-memory layout (more than 8192 discovered or settled seeds), else DGF_OK.
+ * short workspace, DGF_ERR_CUDA for a failed launch, else DGF_OK.
  */
 int epic_interpolate(const uint8_t* img, int W, int H, int pitch, const float* pts, const float* flow,
                      const uint8_t* status, int n, const dgf_epic_params* p, float* dense, const dgf_epic_debug* dbg,

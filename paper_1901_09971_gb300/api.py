@@ -599,8 +599,9 @@ class DenseFlow:
     (fb_max > 0; both pyramids then carry gradients), and EPIC interpolation of the
     tracked points into a dense flow field. Pyramids, key-points, workspaces and the
     dense field are allocated once; ``run`` returns the dense field [H, W, 2] and the
-    sparse (points, flow, status). EPIC reads a convergence counter on the host, so a
-    run synchronises the stream."""
+    sparse (points, flow, status). A run only enqueues work on the current stream (no
+    host round trip; device-side failures go to ``device_status``), so it may be
+    captured into a CUDA graph once it has run eagerly on the device."""
 
     def __init__(self, W: int, H: int, win: int, step: int, params: RlofParams, gm: GmParams | None = None,
                  epic: EpicParams | None = None, fb_max: float = 0.0, device: torch.device | str = "cuda"):

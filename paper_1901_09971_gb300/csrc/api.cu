@@ -21,7 +21,7 @@ extern "C" int dgf_version(void) { return 100; }
 
 namespace {
 
-// Staging waits that gave up, on each device that loaded the library.
+// DGF_DEV_* bits of the device-side failures on each device that loaded the library.
 __device__ unsigned g_status_word;
 
 constexpr int kMaxDevices = 64;
@@ -43,11 +43,11 @@ unsigned* dgf::status_word()
     return addr[dev];
 }
 
-extern "C" int dgf_device_status(unsigned* stalls, int reset)
+extern "C" int dgf_device_status(unsigned* bits, int reset)
 {
-    if (!stalls) return DGF_ERR_ARG;
+    if (!bits) return DGF_ERR_ARG;
     if (!dgf::status_word()) return DGF_ERR_CUDA;
-    if (cudaMemcpyFromSymbol(stalls, g_status_word, sizeof(unsigned)) != cudaSuccess) return DGF_ERR_CUDA;
+    if (cudaMemcpyFromSymbol(bits, g_status_word, sizeof(unsigned)) != cudaSuccess) return DGF_ERR_CUDA;
     if (reset) {
         const unsigned zero = 0;
         if (cudaMemcpyToSymbol(g_status_word, &zero, sizeof(unsigned)) != cudaSuccess) return DGF_ERR_CUDA;

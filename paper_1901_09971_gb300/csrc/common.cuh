@@ -70,10 +70,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsign
 // microseconds a copy takes; reaching it means the copy engine stopped answering).
 constexpr unsigned kStageWaitTries = 1u << 22;
 
-// Device address of the library's status word on the current device (counts
-// staging waits that gave up; read by dgf_device_status), or null if it cannot be
-// looked up. The first call on a device looks the address up (outside any stream
-// capture); later calls return the cached value.
+// Device address of the library's status word on the current device (the DGF_DEV_*
+// bits of the device-side failures since the last reset; read by
+// dgf_device_status), or null if it cannot be looked up. The first call on a device
+// looks the address up (outside any stream capture); later calls return the cached
+// value.
 unsigned* status_word();
 
 // Rounds v up to a multiple of a, a power of two.

@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256) degraf_detect_kernel(const __grid_constan
                                   (unsigned)(a_hi - a_lo), &bar);
             const bool ok = mbar_wait(&bar, 0, kStageWaitTries);
             if (!__syncthreads_and(ok)) {  // the copy engine stopped answering: record, drain, leave
-                if (tid == 0 && a.status) atomicAdd(a.status, 1u);
+                if (tid == 0 && a.status) atomicOr(a.status, (unsigned)DGF_DEV_STAGE_WAIT);
                 mbar_wait(&bar, 0, kStageWaitTries);
                 return;
             }

@@ -32,6 +32,8 @@
 //   10. dense flow: every pixel evaluates its seed's model.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace {
@@ -42,13 +44,13 @@ constexpr unsigned long long kIdxMask = (1ull << kIdxBits) - 1;
 constexpr long long kDistLimit = 1ll << 40;  // the distance field of a packed key
 constexpr int kTile = 32;                    // Voronoi tiles: 32 x 32 pixels, 32 x 8 threads
 constexpr int kMaxPasses = 4096;
-constexpr int kPassBatch = 4;
 constexpr int kThreads = 256;
 
 constexpr long long kNoLink = 0xffffffffll;  // min link weight of a seed without links
 
 // Device status bits (any of them makes the call return DGF_ERR_DEVICE).
-enum : int { kErrFrontier = 1, kErrFill = 4, kErrRange = 8 };
+enum : int { kErrFrontier = 1, kErrFill = 4, kErrRange = 8, kErrPasses = 16, kErrSync = 32 };
+constexpr unsigned kBarrierTries = 1u << 24;  // polls (100 ns naps) before a grid barrier gives up
 
 __device__ __forceinline__ bool is_tracked(uint8_t s) { return s == DGF_TRACKED || s == DGF_MAXITER; }
 
@@ -99,12 +101,15 @@ __device__ __forceinline__ void relax(unsigned long long& best, unsigned long lo
     if (kn != kNone) best = min(best, kn + ((unsigned long long)w << kIdxBits));
 }
 
-__global__ void __launch_bounds__(kThreads) epic_voronoi_kernel(const int* cost, unsigned long long* key, int W, int H,
-                                                                int* changed, int pass)
+// One relaxation pass over the 32 x 32 tile at (x0, y0): the tile and a one-pixel
+// halo in shared memory, Jacobi min-plus sweeps until the tile is stable, improved
+// keys written back with atomicMin; counts the tile in changed[pass] if any key
+// improved. Called by every thread of the block.
+__device__ __forceinline__ void voronoi_tile(const int* cost, unsigned long long* key, int W, int H, int* changed,
+                                             int pass, int x0, int y0)
 {
     __shared__ unsigned long long sk[kTile + 2][kTile + 2];
     __shared__ int sc[kTile + 2][kTile + 2];
-    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     for (int e = tid; e < (kTile + 2) * (kTile + 2); e += kThreads) {
         const int ly = e / (kTile + 2), lx = e - ly * (kTile + 2);
@@ -162,6 +167,61 @@ __global__ void __launch_bounds__(kThreads) epic_voronoi_kernel(const int* cost,
         }
     }
     if (__syncthreads_or(improved) && tid == 0) atomicAdd(&changed[pass], 1);
+    __syncthreads();  // the next tile reuses sk and sc
+}
+
+// Barrier of all blocks of a cooperative launch (all co-resident): arrivals on a
+// counter that grows by the grid size per use; the waits are bounded, and false
+// comes back once a block gave up.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        __threadfence();  // this block's key and counter updates before its arrival
+        atomicAdd(count, 1u);
+        int ok = 0;
+        for (unsigned i = 0; i < kBarrierTries; ++i) {
+            if (*reinterpret_cast<volatile unsigned*>(count) >= target) {
+                ok = 1;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Geodesic Voronoi labelling in one cooperative launch: every pass relaxes all tiles
+// (block b takes tiles b, b + grid, ...), a grid barrier closes it, and the passes
+// stop at the first that changed nothing (every block reads the same count after
+// the barrier) or after kMaxPasses, which is recorded as a failure; so is a barrier
+// that gave up. No host round trip between passes.
+__global__ void __launch_bounds__(kThreads) epic_voronoi_kernel(const int* cost, unsigned long long* key, int W, int H,
+                                                                int* changed, unsigned* sync_count, int* err)
+{
+    const int tiles_x = (W + kTile - 1) / kTile, n_tiles = tiles_x * ((H + kTile - 1) / kTile);
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0;
+    for (int pass = 0; pass < kMaxPasses; ++pass) {
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x)
+            voronoi_tile(cost, key, W, H, changed, pass, (t % tiles_x) * kTile, (t / tiles_x) * kTile);
+        if (!grid_barrier(sync_count, (unsigned)(pass + 1) * gridDim.x)) {
+            if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(err, kErrSync);
+            return;
+        }
+        if (*reinterpret_cast<volatile int*>(changed + pass) == 0) return;
+    }
+    if (lead) atomicOr(err, kErrPasses);
+}
+
+// Records a device-side failure of the call in the library's status word.
+__global__ void epic_report_kernel(const int* err, unsigned* status)
+{
+    const int e = *err;
+    if (e && status) atomicOr(status, e & (kErrPasses | kErrSync) ? DGF_DEV_EPIC_PASSES : DGF_DEV_EPIC_CAPACITY);
 }
 
 // Seed-graph links of pixel o with its right and lower neighbours.
@@ -912,7 +972,7 @@ EpicLayout epic_layout(int W, int H, int n)
     L.adj_i = take(nl * 16);
     L.models = take((size_t)n * 48);
     L.retry = take((size_t)n * 4);
-    L.counters = take((kMaxPasses + 2) * 4);  // pass counters, the status word, the retry count
+    L.counters = take((kMaxPasses + 3) * 4);  // pass counters, the status word, the retry count, the barrier
     L.total = at;
     return L;
 }
@@ -1000,10 +1060,13 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
     auto* changed = reinterpret_cast<int*>(ws + L.counters);
     int* err = changed + kMaxPasses;
     int* retry_count = err + 1;
+    unsigned* sync_count = reinterpret_cast<unsigned*>(retry_count + 1);
     const float2* p2 = reinterpret_cast<const float2*>(pts);
     const float2* f2 = reinterpret_cast<const float2*>(flow);
 
-    if (cudaMemsetAsync(changed, 0, (kMaxPasses + 2) * sizeof(int), stream) != cudaSuccess) return DGF_ERR_CUDA;
+    unsigned* dev_status = dgf::status_word();
+    if (!dev_status) return DGF_ERR_CUDA;
+    if (cudaMemsetAsync(changed, 0, (kMaxPasses + 3) * sizeof(int), stream) != cudaSuccess) return DGF_ERR_CUDA;
     if (n > 0 && cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), stream) != cudaSuccess) return DGF_ERR_CUDA;
     const dim3 pix_block(32, 8), pix_grid((W + 31) / 32, (H + 7) / 8);
     const unsigned pt_grid = (unsigned)((n + kThreads - 1) / kThreads);
@@ -1015,19 +1078,23 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
     int rc = dgf::launch_status();
     if (rc != DGF_OK) return rc;
 
-    // geodesic Voronoi labelling: passes until one changes nothing
-    const dim3 tile_grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile);
-    int pass = 0;
-    for (;;) {
-        for (int b = 0; b < kPassBatch && pass < kMaxPasses; ++b, ++pass)
-            epic_voronoi_kernel<<<tile_grid, pix_block, 0, stream>>>(cost, key, W, H, changed, pass);
-        if ((rc = dgf::launch_status()) != DGF_OK) return rc;
-        int last = 0;
-        if (cudaMemcpyAsync(&last, changed + pass - 1, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-            cudaStreamSynchronize(stream) != cudaSuccess)
+    // geodesic Voronoi labelling: passes until one changes nothing, in one
+    // cooperative launch of as many blocks as can be resident (at most one a tile)
+    {
+        int per_sm = 0, dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, epic_voronoi_kernel, kThreads, 0) != cudaSuccess ||
+            per_sm < 1)
             return DGF_ERR_CUDA;
-        if (last == 0) break;
-        if (pass >= kMaxPasses) return DGF_ERR_TIMEOUT;
+        const long long tiles = (long long)((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
+        const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)per_sm * sms);
+        const dim3 block(32, 8);
+        void* args[] = {(void*)&cost, (void*)&key, (void*)&W, (void*)&H, (void*)&changed, (void*)&sync_count,
+                        (void*)&err};
+        if (cudaLaunchCooperativeKernel((const void*)epic_voronoi_kernel, dim3(grid), block, args, 0, stream) !=
+            cudaSuccess)
+            return DGF_ERR_CUDA;
     }
 
     if (n > 0) {
@@ -1086,10 +1153,6 @@ extern "C" int epic_interpolate(const uint8_t* img, int W, int H, int pitch, con
     if (d.retried &&
         cudaMemcpyAsync(d.retried, retry_count, sizeof(int), cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
         return DGF_ERR_CUDA;
-    if ((rc = dgf::launch_status()) != DGF_OK) return rc;
-    int status_word = 0;
-    if (cudaMemcpyAsync(&status_word, err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-        cudaStreamSynchronize(stream) != cudaSuccess)
-        return DGF_ERR_CUDA;
-    return status_word ? DGF_ERR_DEVICE : DGF_OK;
+    epic_report_kernel<<<1, 1, 0, stream>>>(err, dev_status);
+    return dgf::launch_status();
 }

@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, pyramid_min_blocks<L>()) pyramid_ker
                               (unsigned)(a_hi - a_lo), &bar);
         const bool ok = mbar_wait(&bar, 0, kStageWaitTries);
         if (!__syncthreads_and(ok)) {  // the copy engine stopped answering: record, drain, leave
-            if (threadIdx.x == 0 && a.status) atomicAdd(a.status, 1u);
+            if (threadIdx.x == 0 && a.status) atomicOr(a.status, (unsigned)DGF_DEV_STAGE_WAIT);
             mbar_wait(&bar, 0, kStageWaitTries);
             return;
         }

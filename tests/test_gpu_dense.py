@@ -52,3 +52,32 @@ def test_pipeline_equals_its_stages(dgf, mode):
     # the frame-2 noise (sigma 2 levels) limits the tracks to about 0.3 px; the
     # interpolation must not add to that
     assert np.median(e) <= np.median(es) + 0.02
+
+
+@pytest.mark.parametrize("mode", ["gm", "plain"])
+def test_pipeline_replays_from_a_captured_cuda_graph(dgf, mode):
+    """No stage of a run waits on the host (EPIC's labelling settles on the device),
+    so a whole run captures into one CUDA graph; replayed on new frame contents it
+    gives what an eager run gives, bit for bit, and no device-side failure is
+    reported."""
+    p, q = synth.make_pair(1), synth.make_pair(1, index=1)
+    prm = dgf.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4)
+    gm = dgf.GmParams(extra_levels=0) if mode == "gm" else None
+    df = dgf.DenseFlow(p.W, p.H, p.win, p.step, prm, gm=gm)
+    f1, f2 = torch.from_numpy(p.I1).cuda(), torch.from_numpy(p.I2).cuda()
+    dgf.device_status(reset=True)
+    df.run(f1, f2)  # eager first: looks up the device status word
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        dense_g, (_, flow_g, status_g) = df.run(f1, f2)
+    f1.copy_(torch.from_numpy(q.I1))
+    f2.copy_(torch.from_numpy(q.I2))
+    g.replay()
+    torch.cuda.synchronize()
+    got = (dense_g.clone(), flow_g.clone(), status_g.clone())
+    ref = dgf.DenseFlow(p.W, p.H, p.win, p.step, prm, gm=gm)
+    dense_e, (_, flow_e, status_e) = ref.run(f1, f2)
+    torch.cuda.synchronize()
+    assert torch.equal(got[0], dense_e) and torch.equal(got[1], flow_e) and torch.equal(got[2], status_e)
+    assert dgf.device_status() == 0

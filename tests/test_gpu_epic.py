@@ -34,9 +34,11 @@ def run_both(dgf, img, pts, flow, status, k=128, model=1, frame=None, **kw):
     pts32, flow32 = pts.astype(np.float32), flow.astype(np.float32)
     prm = dgf.EpicParams(k=k, model=model, **kw)
     fr = to_dev(img) if frame is None else frame
+    dgf.device_status(reset=True)
     dense, d = dgf.epic_interpolate(fr, to_dev(pts32), to_dev(flow32), to_dev(status.astype(np.uint8)), prm,
                                     debug=True)
     torch.cuda.synchronize()
+    assert dgf.device_status() == 0  # the labelling settled and every search fitted its layout
     g = {key: v.cpu().numpy() for key, v in d.items()}
     g["dense"] = dense.cpu().numpy()
     o = oracle.epic_interpolate(img, pts32.astype(np.float64), flow32.astype(np.float64), status,

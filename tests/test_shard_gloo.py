@@ -1,7 +1,8 @@
 """Multi-rank host logic of the sharded path on CPU (gloo, world size 2): every
-rank derives the same split of the 64-pair batch, the shards cover each pair once
-and are balanced, the timing and total reductions agree, and a rank that leaves
-makes the other's next collective fail within its timeout instead of hanging."""
+rank derives the same split of the 64-pair batch (in the ShardedBatch runner as in
+assign_pairs), the shards cover each pair once and are balanced, the timing and
+total reductions agree, and a rank that leaves makes the other's next collective
+fail within its timeout instead of hanging."""
 import datetime
 import os
 import socket
@@ -45,9 +46,16 @@ def _worker(rank, world, port, mode, out):
     costs = batch_costs()
     mine = shard.assign_pairs(costs, world)[rank]
     if mode == "ok":
+        # the runner's share is the same split, derived from the process group
+        from paper_1901_09971_gb300 import RlofParams
+        specs = [(W, H, 8, step) for (W, H, step) in synth.make_batch_specs(64, 3000)]
+        runner = shard.ShardedBatch(specs, RlofParams(levels=3, radius=4), device="cpu")
+        assert (runner.rank, runner.world) == (rank, world) and runner.indices == mine
+        assert runner.specs == [specs[i] for i in mine]
         total = shard.reduce_scalar(sum(costs[i] for i in mine), "sum")
+        points = shard.reduce_scalar(runner.points, "sum")
         slowest = shard.reduce_scalar(1.0 + rank, "max")
-        out.put((rank, mine, total, slowest))
+        out.put((rank, mine, total, slowest, points))
         dist.barrier()
         dist.destroy_process_group()
     else:  # rank 1 leaves between steps; rank 0's next collective must fail, not hang
@@ -75,12 +83,28 @@ def _run(mode):
 
 
 def test_two_ranks_split_and_reduce():
+    """Both ranks' runners derive the split from the process group; their shares
+    cover the 64-pair batch once, and the reduced totals (work, key-points, the
+    slowest rank's time) agree."""
     res = _run("ok")
     costs = batch_costs()
-    (r0, m0, t0, s0), (r1, m1, t1, s1) = res
+    (r0, m0, t0, s0, p0), (r1, m1, t1, s1, p1) = res
     assert sorted(m0 + m1) == list(range(len(costs))) and not set(m0) & set(m1)
     assert t0 == t1 == float(sum(costs))
     assert s0 == s1 == 2.0
+    specs = synth.make_batch_specs(64, 3000)
+    assert p0 == p1 == float(sum(((W - 8) // st + 1) * ((H - 8) // st + 1) for (W, H, st) in specs))
+
+
+def test_runner_without_a_process_group_takes_the_whole_batch():
+    from paper_1901_09971_gb300 import RlofParams
+    specs = [(W, H, 8, step) for (W, H, step) in synth.make_batch_specs(64, 3000)]
+    runner = shard.ShardedBatch(specs, RlofParams(levels=3, radius=4), device="cpu")
+    assert (runner.rank, runner.world) == (0, 1) and runner.indices == list(range(64))
+    shares = [shard.ShardedBatch(specs, RlofParams(levels=3, radius=4), device="cpu", rank=r, world=8) for r in range(8)]
+    assert sorted(i for sh in shares for i in sh.indices) == list(range(64))
+    with pytest.raises(ValueError):
+        shard.ShardedBatch(specs, RlofParams(levels=3, radius=4), rank=2, world=2)
 
 
 def test_departed_rank_fails_collective_instead_of_hanging():
