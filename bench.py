@@ -174,15 +174,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+TRAFFIC_SOURCES = ("rlof.cu", "common.cuh", "batch.cuh")  # what the tracking kernel is compiled from
+
+
+def tracking_sources_digest():
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1901_09971_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def kernel_traffic():
-    """DRAM bytes per rlof launch from the committed ncu summary, or None when the
-    kernel source changed after the capture."""
+    """DRAM bytes per rlof launch from the committed ncu summary, or None when a source
+    of the kernel changed after the capture."""
     path = os.path.join(ROOT, "profiles", "rlof_track_traffic.json")
-    src = os.path.join(ROOT, "paper_1901_09971_gb300", "csrc", "rlof.cu")
     try:
         rec = json.load(open(path))
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        return rec["dram_bytes_per_launch"] if rec.get("rlof_cu_sha256") == digest else None
+        return rec["dram_bytes_per_launch"] if rec.get("sources_sha256") == tracking_sources_digest() else None
     except (OSError, ValueError, KeyError):
         return None
 
