@@ -336,17 +336,22 @@ def hbm_context(W: int, H: int, n: int, ms_per_step: float):
 
 
 def run_small_pair(dgf, torch, dev, reps: int = 50):
-    """The 256x128 translation pair (window 8, step 4, 3 levels, 9x9): one
-    PairTracker step (detection, both pyramids, tracking), device frames."""
+    """The 256x128 translation pair (window 8, step 4, 3 levels, 9x9): one step
+    (detection, both pyramids, tracking) on device frames, as one replayed CUDA graph
+    of the batched entry, and as four separate launches (PairTracker)."""
     p = synth.make_pair(1)
     prm = dgf.RlofParams(levels=p.levels, radius=p.radius, max_iter=p.max_iter, model=4)
-    tr = dgf.PairTracker(p.W, p.H, p.win, p.step, prm, dev)
     f1, f2 = torch.from_numpy(p.I1).to(dev), torch.from_numpy(p.I2).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    t = _timed(torch, dev, lambda: tr.run(f1, f2), reps, flush)
-    n = int(tr.pts.shape[0])
+    bt = dgf.BatchTracker([(p.W, p.H, p.win, p.step)], prm, dev)
+    bt.bind([f1], [f2])
+    t = _timed(torch, dev, lambda: bt.run(use_graph=True), reps, flush)
+    tr = dgf.PairTracker(p.W, p.H, p.win, p.step, prm, dev)
+    t4 = _timed(torch, dev, lambda: tr.run(f1, f2), reps, flush)
+    n = bt.n[0]
     return {"workload": f"256x128 translation pair, window 8, step 4 ({n} points), 3 levels, 9x9, model 4, FP32",
-            "ms_per_step": t, "points_per_s": n / (t / 1e3), "pairs_per_s": 1e3 / t}
+            "ms_per_step": t, "points_per_s": n / (t / 1e3), "pairs_per_s": 1e3 / t,
+            "ms_per_step_four_launches": t4}
 
 
 def run_gm_prior(dgf, torch, dev, pair, reps: int = 20):
@@ -488,12 +493,19 @@ def run_dense_pipeline(dgf, torch, dev, pair, reps: int = 20):
     f1 = torch.from_numpy(pair.I1).to(dev)
     f2 = torch.from_numpy(pair.I2).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    t = _timed(torch, dev, lambda: df.run(f1, f2), reps, flush)
-    dense = df.run(f1, f2)[0].cpu().numpy().astype(np.float64)
+    t_eager = _timed(torch, dev, lambda: df.run(f1, f2), reps, flush)
+    # a run waits on nothing on the host, so it is captured once into a CUDA graph and
+    # replayed (no launch gaps between its 20-odd kernels)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        dense_g = df.run(f1, f2)[0]
+    t = _timed(torch, dev, g.replay, reps, flush)
+    dense = dense_g.cpu().numpy().astype(np.float64)
     e = np.hypot(*(dense - pair.flow_gt).transpose(2, 0, 1))[~pair.occluded]
     return {"workload": "1242x375 driving-scene pair: DeGraF w7 s3 (50,676 points), pyramids, RLOF 5 levels 11x11 "
-                        "with the global-motion prior, EPIC k 128 into a dense field",
-            "ms_per_pair": t, "pairs_per_s": 1e3 / t, "epe_noc_px": float(e.mean()),
+                        "with the global-motion prior, EPIC k 128 into a dense field, one captured CUDA graph "
+                        "replayed per pair",
+            "ms_per_pair": t, "pairs_per_s": 1e3 / t, "ms_per_pair_eager": t_eager, "epe_noc_px": float(e.mean()),
             "fl_noc_over_3px": float(np.mean(e > 3.0)),
             "paper_context": "the paper's C++ pipeline (detection + RLOF + EPIC): 3.2 s per KITTI pair on 4 CPU cores"}
 
@@ -675,21 +687,24 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
     W, H = pair.W, pair.H
     prm = dgf.RlofParams(levels=WORKLOAD["levels"], radius=WORKLOAD["radius"], max_iter=WORKLOAD["max_iter"],
                          model=WORKLOAD["model"])
-    tr = dgf.PairTracker(W, H, WORKLOAD["win"], WORKLOAD["step"], prm, dev)
+    # the library's batched entry for this one pair: detection beside both frames'
+    # pyramids (one launch) in a replayed CUDA graph, then tracking (one launch)
+    spec = [(W, H, WORKLOAD["win"], WORKLOAD["step"])]
+    tr = dgf.BatchTracker(spec, prm, dev)
     if args.lanes:
-        dgf.set_lanes(args.lanes)
+        tr.lanes = args.lanes
     f1 = torch.from_numpy(pair.I1).to(dev)
     f2 = torch.from_numpy(pair.I2).to(dev)
+    tr.bind([f1], [f2])
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    from paper_1901_09971_gb300 import _abi
 
     def one_step(ev):
         ev[0].record(stream)
-        dgf.detect(f1, tr.win, tr.step, out=tr.pts)
-        dgf.build_pyramid(f1, prm.levels, prm.storage, True, out=tr.pyr1)
-        dgf.build_pyramid(f2, prm.levels, prm.storage, False, out=tr.pyr2)
+        tr.run(use_graph=True, stages=_abi.STAGE_DETECT | _abi.STAGE_PYRAMID)
         ev[1].record(stream)
-        dgf.track(tr.pyr1, tr.pyr2, W, H, tr.pts, prm, out=(tr.flow, tr.status, tr.iters, None))
+        tr.run(use_graph=False, stages=_abi.STAGE_TRACK)
         ev[2].record(stream)
 
     for _ in range(args.warmup):
@@ -711,12 +726,12 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
     rlof_ms = np.array([e[1].elapsed_time(e[2]) for e in evs])
     total_s = step_ms.sum() / 1e3
     total_s = shard.reduce_scalar(total_s, "max", device=dev)  # slowest rank
-    n_pts = tr.n
+    n_pts = tr.n[0]
     value = world * n_pts * args.steps / total_s
 
     # dominant kernel: RLOF tracking, algorithmic FLOPs of the last step's trajectories
-    iters = tr.iters.cpu().numpy()
-    status = tr.status.cpu().numpy()
+    iters = tr.iters[0].cpu().numpy()
+    status = tr.status[0].cpu().numpy()
     flops = algorithmic_flops(iters, status, prm.levels, prm.radius, prm.model)
     achieved = flops / (rlof_ms.mean() / 1e3) / 1e12
     fp32 = measure_fp32_peak(dgf, torch, dev)
@@ -729,14 +744,16 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
     o_status = torch.empty(n_pts, dtype=torch.uint8).pin_memory()
     d1 = torch.empty_like(f1)
     d2 = torch.empty_like(f2)
+    te = dgf.BatchTracker(spec, prm, dev, lanes=tr.lanes)
+    te.bind([d1], [d2])
 
     def e2e_step():
         d1.copy_(h1, non_blocking=True)
         d2.copy_(h2, non_blocking=True)
-        pts, flow, st, _ = tr.run(d1, d2)
-        o_pts.copy_(pts, non_blocking=True)
-        o_flow.copy_(flow, non_blocking=True)
-        o_status.copy_(st, non_blocking=True)
+        te.run(use_graph=True)
+        o_pts.copy_(te.pts[0], non_blocking=True)
+        o_flow.copy_(te.flow[0], non_blocking=True)
+        o_status.copy_(te.status[0], non_blocking=True)
 
     for _ in range(3):
         e2e_step()
@@ -776,7 +793,7 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
                 "fp32_peak": fp32,
                 "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": 2 * W * H,
                         "d2h_bytes_per_step": n_pts * (8 + 8 + 1)},
-                "gpu_launches": 4 * args.steps,
+                "gpu_launches": 3 * args.steps,
                 "clocks": clocks.summary()}
         line["hbm_context"] = hbm_context(W, H, n_pts, 1e3 * total_s / args.steps)
         if batched is not None:

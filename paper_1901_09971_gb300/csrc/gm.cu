@@ -3,13 +3,13 @@
 // model used is a global affine motion fitted robustly to a sparse first pass and
 // used as every point's initial flow in the main pass.
 //
-// The fit is an IRLS loop of a few iterations, each two launches: 64 CTAs sum the
+// The fit is an IRLS loop of a few iterations, one launch each: 64 CTAs sum the
 // weighted normal equations of their points in FP64 (GB300's FP64 pipe is narrow,
-// so the sums are spread over the SMs) into per-CTA partials, then one thread adds the
-// partials in CTA order (deterministic) and solves the two 3 x 3 systems. The
-// state (affine, fitted flag, go-on flag) lives in the workspace, so no host round
-// trip separates the stages: the main pass reads the fitted parameters from device
-// memory.
+// so the sums are spread over the SMs) into per-CTA partials; the CTA that finishes
+// last (a ticket counter) adds the partials in CTA order, one thread per sum
+// (deterministic), and solves the two 3 x 3 systems. The state (affine, fitted flag,
+// go-on flag, ticket) lives in the workspace, so no host round trip separates the
+// stages: the main pass reads the fitted parameters from device memory.
 #include "common.cuh"
 #include "batch.cuh"
 
@@ -48,25 +48,31 @@ __device__ bool solve3(const double* m, const double* b, double* x)
 }
 
 // State at the start of the workspace: a[6] (doubles), then int flags at byte 48
-// (1 = fitted) and byte 52 (1 = iterating).
+// (1 = fitted) and byte 52 (1 = iterating), and the CTAs' ticket counter at byte 56.
 __global__ void gm_init_kernel(double* state)
 {
     state[0] = 1; state[1] = 0; state[2] = 0;
     state[3] = 0; state[4] = 1; state[5] = 0;
     reinterpret_cast<int*>(state + 6)[0] = 0;
     reinterpret_cast<int*>(state + 6)[1] = 1;
+    reinterpret_cast<unsigned*>(state + 7)[0] = 0;
 }
 
-// IRLS iteration k, part 1: per-CTA sums over the points of the CTA's grid stride
-// (point i at pts[i * stride]); partial[blockIdx.x][0..11] = the 12 sums,
-// [12] = the number of weighted points.
-__global__ void __launch_bounds__(kPartThreads) gm_partial_kernel(const float* pts, int stride, const float* flow,
-                                                                  const uint8_t* status, int n, int k, double c0,
-                                                                  double c_min, const double* state,
-                                                                  double* partial)
+// IRLS iteration k: per-CTA sums over the points of the CTA's grid stride (point i
+// at pts[i * stride]); partial[blockIdx.x][0..11] = the 12 sums, [12] = the number of
+// weighted points. The last CTA to finish adds the partials in CTA order and solves
+// the two 3 x 3 systems; a step with fewer than 3 weighted points or a singular
+// matrix keeps the previous estimate and stops the loop.
+__global__ void __launch_bounds__(kPartThreads) gm_iteration_kernel(const float* pts, int stride, const float* flow,
+                                                                    const uint8_t* status, int n, int k, double c0,
+                                                                    double c_min, double* state, double* partial)
 {
     __shared__ double part[kPartThreads / 32][kSums + 1];
-    if (!reinterpret_cast<const int*>(state + 6)[1]) return;  // uniform: the fit has stopped
+    __shared__ double tot[kSums + 1];
+    __shared__ int last;
+    int* flags = reinterpret_cast<int*>(state + 6);
+    unsigned* ticket = reinterpret_cast<unsigned*>(state + 7);
+    if (!flags[1]) return;  // uniform: the fit has stopped
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double a[6];
 #pragma unroll
@@ -102,7 +108,7 @@ __global__ void __launch_bounds__(kPartThreads) gm_partial_kernel(const float* p
         s[11] += w * qy;
         s[12] += 1.0;
     }
-    // fixed-order reduction: xor butterfly in each warp, then thread 0 over the warps
+    // fixed-order reduction: xor butterfly in each warp, then one thread a sum over the warps
 #pragma unroll
     for (int j = 0; j <= kSums; ++j)
         for (int o = 16; o > 0; o >>= 1) s[j] += __shfl_xor_sync(0xffffffffu, s[j], o);
@@ -114,24 +120,27 @@ __global__ void __launch_bounds__(kPartThreads) gm_partial_kernel(const float* p
         double t = 0.0;
         for (int w = 0; w < kPartThreads / 32; ++w) t += part[w][threadIdx.x];
         partial[blockIdx.x * (kSums + 1) + threadIdx.x] = t;
+        __threadfence();  // the partial is visible device-wide before this CTA's ticket
     }
-}
-
-// IRLS iteration k, part 2: the partials added in CTA order and the two 3 x 3
-// systems solved; a step with fewer than 3 weighted points or a singular matrix
-// keeps the previous estimate and stops the loop.
-__global__ void gm_solve_kernel(const double* partial, double* state)
-{
-    int* flags = reinterpret_cast<int*>(state + 6);
-    if (!flags[1] || threadIdx.x != 0) return;
-    double t[kSums + 1];
-    for (int j = 0; j <= kSums; ++j) t[j] = 0.0;
-    for (int b = 0; b < kPartBlocks; ++b)
-        for (int j = 0; j <= kSums; ++j) t[j] += partial[b * (kSums + 1) + j];
-    const double m[9] = {t[0], t[1], t[2], t[1], t[3], t[4], t[2], t[4], t[5]};
-    const double bx[3] = {t[6], t[7], t[8]}, by[3] = {t[9], t[10], t[11]};
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    // the last CTA: every other CTA's partial was written before its ticket
+    __threadfence();
+    if (threadIdx.x <= kSums) {
+        double t = 0.0;
+#pragma unroll 8
+        for (int b = 0; b < kPartBlocks; ++b) t += __ldcg(partial + b * (kSums + 1) + threadIdx.x);
+        tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    *ticket = 0;  // for the next iteration's launch
+    const double m[9] = {tot[0], tot[1], tot[2], tot[1], tot[3], tot[4], tot[2], tot[4], tot[5]};
+    const double bx[3] = {tot[6], tot[7], tot[8]}, by[3] = {tot[9], tot[10], tot[11]};
     double sx[3], sy[3];
-    if (t[12] < 3.0 || !solve3(m, bx, sx) || !solve3(m, by, sy)) {
+    if (tot[12] < 3.0 || !solve3(m, bx, sx) || !solve3(m, by, sy)) {
         flags[1] = 0;  // keep the previous estimate
         return;
     }
@@ -146,7 +155,7 @@ bool gm_params_ok(const dgf_gm_params* g)
            g->iters <= 64 && g->c0 > 0 && g->c_min > 0;
 }
 
-// Workspace layout: [a[6], flags; 256 B] [first-pass flow, n_sub x 8 B] [first-pass status, n_sub B]
+// Workspace layout: [a[6], flags, ticket; 256 B] [first-pass flow, n_sub x 8 B] [first-pass status, n_sub B]
 // [per-CTA partial sums, 64 x 13 doubles]
 size_t flow_offset() { return 256; }
 size_t status_offset(long long n_sub) { return dgf::round_up(flow_offset() + (size_t)n_sub * 8, 256); }
@@ -211,9 +220,8 @@ extern "C" int rlof_track_gm(const void* pyr1, const void* pyr2, int W, int H, i
     double* partial = reinterpret_cast<double*>(ws + partial_offset(n_sub));
     gm_init_kernel<<<1, 1, 0, stream>>>(affine);
     for (int k = 0; k < g->iters; ++k) {
-        gm_partial_kernel<<<kPartBlocks, kPartThreads, 0, stream>>>(pts, g->stride, sub_flow, sub_status, (int)n_sub,
-                                                                     k, g->c0, g->c_min, affine, partial);
-        gm_solve_kernel<<<1, 32, 0, stream>>>(partial, affine);
+        gm_iteration_kernel<<<kPartBlocks, kPartThreads, 0, stream>>>(pts, g->stride, sub_flow, sub_status,
+                                                                       (int)n_sub, k, g->c0, g->c_min, affine, partial);
     }
     if ((rc = dgf::launch_status()) != DGF_OK) return rc;
     // 3. main pass from the prior
