@@ -66,10 +66,22 @@ struct Tile {
     __device__ __forceinline__ unsigned mis(int r) const { return (mis0 + (unsigned)r * pmod) & mask; }
 };
 
+// Maximum of the 8 bytes of (lo, hi) and of acc, in two 16-bit lanes: bytes 0, 2 and
+// 1, 3 of each word spread into zero-extended 16-bit lanes (byte permutes), then
+// three-way 16-bit lane maxima (hardware DPX instructions since sm_90). The byte
+// maximum of a row set is the larger of the result's two lanes.
+__device__ __forceinline__ unsigned row_max16(unsigned lo, unsigned hi, unsigned acc)
+{
+    const unsigned el = __byte_perm(lo, 0u, 0x4240), ol = __byte_perm(lo, 0u, 0x4341);
+    const unsigned eh = __byte_perm(hi, 0u, 0x4240), oh = __byte_perm(hi, 0u, 0x4341);
+    return __vimax3_u16x2(__vimax3_u16x2(el, ol, eh), oh, acc);
+}
+__device__ __forceinline__ int lanes_max16(unsigned m) { return (int)max(m & 0xffffu, m >> 16); }
+
 // Window sums of a window of width <= 8 at tile column c0, row r0: per row, the
 // window's bytes become two 32-bit words (funnel shifts of three aligned loads),
 // bytes past the window are masked off, and dp4a forms the row sum and the
-// column-weighted row sum while a bytewise max tracks m.
+// column-weighted row sum while 16-bit lane maxima track m.
 __device__ __forceinline__ void window_sums_packed(const Tile& T, int c0, int r0, int ww, int wh, int& S, int& X,
                                                    int& Y, int& m)
 {
@@ -90,16 +102,14 @@ __device__ __forceinline__ void window_sums_packed(const Tile& T, int c0, int r0
         x += (int)__dp4a(lo, 0x03020100u, __dp4a(hi, 0x07060504u, 0u));
         s += rs;
         y += i * rs;
-        mx = __vmaxu4(mx, __vmaxu4(lo, hi));
+        mx = row_max16(lo, hi, mx);
         base += T.stride >> 2;
         mis = (mis + T.pmod) & T.mask;  // next row's offset
     }
-    mx = __vmaxu4(mx, mx >> 16);
-    mx = __vmaxu4(mx, mx >> 8);
     S = s;
     X = x;
     Y = y;
-    m = (int)(mx & 0xffu);
+    m = lanes_max16(mx);
 }
 
 // Sums of the VR consecutive windows of one column (square windows of width W <= 8,
@@ -107,8 +117,8 @@ __device__ __forceinline__ void window_sums_packed(const Tile& T, int c0, int r0
 // read once (rows shared by overlapping windows are not re-summed); row sums, the
 // column-weighted row sums and row-index-weighted row sums become prefix sums over
 // the rows, so a window's S, X and Y are differences of two prefixes
-// (Y = (Q_e - Q_b) - b S for the window's first row b); the maximum comes from a
-// tree of pairwise maxima of the packed row maxima, shared between windows.
+// (Y = (Q_e - Q_b) - b S for the window's first row b); the maximum is a three-way
+// maximum over the window's row maxima, kept as 16-bit lane pairs.
 template <int W, int S, int VR>
 __device__ __forceinline__ void column_window_sums(const Tile& T, int c0, int r0, int (&Sv)[VR], int (&Xv)[VR],
                                                    int (&Yv)[VR], int (&Mv)[VR])
@@ -135,15 +145,9 @@ __device__ __forceinline__ void column_window_sums(const Tile& T, int c0, int r0
         P[r + 1] = P[r] + rs;
         Q[r + 1] = Q[r] + r * rs;
         PX[r + 1] = PX[r] + rx;
-        rm[r] = __vmaxu4(lo, hi);
+        rm[r] = row_max16(lo, hi, 0u);
         mis = (mis + T.pmod) & T.mask;
     }
-    // pairwise maxima over 2 and 4 consecutive rows (unused entries are never formed)
-    unsigned m2[R], m4[R];
-#pragma unroll
-    for (int r = 0; r + 1 < R; ++r) m2[r] = __vmaxu4(rm[r], rm[r + 1]);
-#pragma unroll
-    for (int r = 0; r + 3 < R; ++r) m4[r] = __vmaxu4(m2[r], m2[r + 2]);
 #pragma unroll
     for (int k = 0; k < VR; ++k) {
         const int b = k * S, e = b + W;
@@ -151,23 +155,13 @@ __device__ __forceinline__ void column_window_sums(const Tile& T, int c0, int r0
         Xv[k] = PX[e] - PX[b];
         Yv[k] = (Q[e] - Q[b]) - b * Sv[k];
         unsigned m = 0u;
-        int i = b;
-        if (W >= 4) {
-            m = m4[i];
-            i += 4;
+#pragma unroll
+        for (int i = b; i < e; i += 2) {
+            unsigned next = 0u;
+            if (i + 1 < e) next = rm[i + 1];
+            m = __vimax3_u16x2(m, rm[i], next);
         }
-        if (e - i >= 4) {
-            m = __vmaxu4(m, m4[i]);
-            i += 4;
-        }
-        if (e - i >= 2) {
-            m = __vmaxu4(m, m2[i]);
-            i += 2;
-        }
-        if (e - i >= 1) m = __vmaxu4(m, rm[i]);
-        m = __vmaxu4(m, m >> 16);
-        m = __vmaxu4(m, m >> 8);
-        Mv[k] = (int)(m & 0xffu);
+        Mv[k] = lanes_max16(m);
     }
 }
 
@@ -197,7 +191,9 @@ __device__ __forceinline__ void window_sums_bytes(const uint8_t* w0, int rstride
 // pixels (large tiles: few staging round trips per SM): with one bulk copy per row
 // when the frame's base, pitch and width are multiples of 16, else with 4-byte
 // copies of the aligned words holding them; otherwise threads read the frame directly.
-__global__ void __launch_bounds__(256) degraf_detect_kernel(const __grid_constant__ DetectBatch a)
+// Four resident blocks per SM (shared memory allows four at the largest tiles): up to 64
+// registers a thread, no spills.
+__global__ void __launch_bounds__(256, 4) degraf_detect_kernel(const __grid_constant__ DetectBatch a)
 {
     extern __shared__ __align__(16) uint8_t tile[];
     int f = 0;
