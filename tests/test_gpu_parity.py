@@ -98,6 +98,27 @@ def test_detect_hand_worked_examples(dgf, case):
     assert np.all(np.abs(g.astype(np.float64) - exact) <= budget)
 
 
+@pytest.mark.parametrize("ww,step", [(8, 2), (8, 3), (8, 4), (8, 6), (7, 3), (6, 2), (5, 3)])
+def test_detect_window_maximum_at_every_position(dgf, ww, step):
+    """The window maximum m (the negative centroid's weights 1 + m - I) is exact
+    wherever in the window it sits: low-valued frames (0..60) with sparse peaks
+    (61..254) put a window's maximum at every row and byte position, odd or even,
+    first or last, of the column-sum and packed-row paths."""
+    rng = np.random.default_rng(ww * 100 + step)
+    H, W = 157, 389
+    img = rng.integers(0, 61, size=(H, W)).astype(np.uint8)
+    peaks = rng.random((H, W)) < 0.02
+    img[peaks] = rng.integers(61, 255, size=int(peaks.sum())).astype(np.uint8)
+    pts_o, sums_o, _ = oracle.degraf_detect(img, ww, ww, step)
+    pts_g, sums_g = dgf.detect(to_dev(img), ww, step, with_sums=True)
+    torch.cuda.synchronize()
+    sg = sums_g.cpu().numpy().astype(np.int64)
+    assert np.array_equal(sg, sums_o[:, :4])
+    m = sums_o[:, 3]
+    assert np.unique(m).size > 100 and np.mean(m <= 60) > 0.05  # maxima of every kind occur
+    assert np.abs(pts_g.cpu().numpy().astype(np.float64) - pts_o).max() <= TOL_PTS
+
+
 def test_detect_pitched_frame(dgf):
     H, W, pitch = 90, 150, 192
     rng = np.random.default_rng(2)
