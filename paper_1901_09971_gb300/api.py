@@ -642,17 +642,92 @@ class DenseFlow:
         return self.dense, (self.pts, flow, status)
 
 
-def track_pair(frame1, frame2, win: int, step: int, params: RlofParams, device="cuda"):
-    """End-to-end call on host or device frames: returns host (pts, flow, status).
+class HostPairTracker:
+    """Host frames in, host results out, for frame pairs of one size and parameter set.
 
-    Host frames (numpy arrays or CPU tensors) are copied to the device, tracked,
-    and the results copied back.
+    The device copies of the two frames, the batched tracker (detection, both
+    pyramids and tracking replayed from one captured CUDA graph) and pinned host
+    outputs are allocated once. ``run`` copies the two host frames to the device,
+    enqueues the pair, copies points, flow and status back to host memory and waits
+    for them, so a call allocates nothing on the device after the first.
+    """
+
+    def __init__(self, W: int, H: int, win: int, step: int, params: RlofParams,
+                 device: torch.device | str = "cuda", lanes=0):
+        self.W, self.H = int(W), int(H)
+        self.device = dev = torch.device(device)
+        if dev.type != "cuda":
+            raise ValueError("HostPairTracker runs on a CUDA device")
+        with torch.cuda.device(dev):
+            self.d1 = torch.empty((self.H, self.W), dtype=torch.uint8, device=dev)
+            self.d2 = torch.empty((self.H, self.W), dtype=torch.uint8, device=dev)
+            self.tracker = BatchTracker([(self.W, self.H, win, step)], params, dev, lanes=lanes)
+            self.tracker.bind([self.d1], [self.d2])
+        self.n = self.tracker.n[0]
+        self.pts = torch.empty((self.n, 2), dtype=torch.float32).pin_memory()
+        self.flow = torch.empty((self.n, 2), dtype=torch.float32).pin_memory()
+        self.status = torch.empty(self.n, dtype=torch.uint8).pin_memory()
+
+    def _host_frame(self, frame, name: str) -> torch.Tensor:
+        f = torch.as_tensor(frame)
+        if f.dtype != torch.uint8 or tuple(f.shape) != (self.H, self.W) or f.is_cuda:
+            raise ValueError(f"{name} must be a host uint8 array of shape ({self.H}, {self.W})")
+        return f
+
+    def run(self, frame1, frame2, out=None):
+        """Tracks one pair of host frames (numpy arrays or CPU tensors; pinned memory
+        makes the copies asynchronous). Returns host (pts, flow, status): the given
+        ``out`` tensors (contiguous, on the host, of the output shapes and dtypes), else
+        this tracker's own pinned buffers, which the next call overwrites."""
+        h1 = self._host_frame(frame1, "frame1")
+        h2 = self._host_frame(frame2, "frame2")
+        if out is None:
+            out = (self.pts, self.flow, self.status)
+        cpu = torch.device("cpu")
+        o_pts = _buffer(out[0], "pts", torch.float32, (self.n, 2), cpu)
+        o_flow = _buffer(out[1], "flow", torch.float32, (self.n, 2), cpu)
+        o_status = _buffer(out[2], "status", torch.uint8, (self.n,), cpu)
+        tr = self.tracker
+        with torch.cuda.device(self.device):
+            self.d1.copy_(h1, non_blocking=True)
+            self.d2.copy_(h2, non_blocking=True)
+            tr.run(use_graph=True)
+            o_pts.copy_(tr.pts[0], non_blocking=True)
+            o_flow.copy_(tr.flow[0], non_blocking=True)
+            o_status.copy_(tr.status[0], non_blocking=True)
+            torch.cuda.current_stream(self.device).synchronize()
+        return o_pts, o_flow, o_status
+
+
+_host_trackers: dict = {}
+_host_trackers_lock = threading.Lock()
+_HOST_TRACKERS_KEPT = 4
+
+
+def track_pair(frame1, frame2, win: int, step: int, params: RlofParams, device="cuda"):
+    """End-to-end call on host frames: returns host (pts, flow, status).
+
+    The frames (uint8 numpy arrays or CPU tensors of equal shape) are copied to the
+    device, detected, pyramided and tracked there, and the results copied back. The
+    device buffers of a frame size and parameter set are made on its first call and
+    kept (the last few sizes), so later calls of that size allocate nothing on the
+    device; the returned tensors are the caller's own.
     """
     f1 = torch.as_tensor(frame1)
     f2 = torch.as_tensor(frame2)
+    if f1.dim() != 2 or f1.shape != f2.shape:
+        raise ValueError("frames must be 2-D arrays of equal shape")
     H, W = f1.shape
-    tr = PairTracker(W, H, win, step, params, device)
-    d1 = f1.to(tr.device, non_blocking=True)
-    d2 = f2.to(tr.device, non_blocking=True)
-    pts, flow, status, _ = tr.run(d1, d2)
-    return pts.cpu(), flow.cpu(), status.cpu()
+    dev = torch.device(device)
+    if dev.type == "cuda" and dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    key = (W, H, win, step, dataclasses.astuple(params), str(dev))
+    with _host_trackers_lock:
+        ht = _host_trackers.pop(key, None)
+        if ht is None:
+            ht = HostPairTracker(W, H, win, step, params, dev)
+        _host_trackers[key] = ht  # most recently used last
+        while len(_host_trackers) > _HOST_TRACKERS_KEPT:
+            _host_trackers.pop(next(iter(_host_trackers)))
+        pts, flow, status = ht.run(f1, f2)
+        return pts.clone(), flow.clone(), status.clone()

@@ -110,3 +110,39 @@ def test_backward_planes_checked(dgf, scene):
     g1, g2 = dgf.track_backward(p1, p2, W, H, pts, prm, flow, illum, status, g)
     torch.cuda.synchronize()
     assert torch.isfinite(g1).all() and torch.isfinite(g2).all()
+
+
+def test_host_buffer_path_equals_the_device_path(dgf):
+    """track_pair / HostPairTracker (host frames in, host results out) give exactly
+    what BatchTracker gives on device copies of the same frames, call after call;
+    track_pair keeps its device buffers between calls of one size (the second call
+    leaves the device's free memory unchanged) and hands back tensors the caller owns."""
+    import numpy as np
+    import synth
+    pair = synth.make_pair(1)
+    prm = dgf.RlofParams(levels=3, radius=4, max_iter=30, model=4)
+    ref = dgf.BatchTracker([(pair.W, pair.H, pair.win, pair.step)], prm)
+    ref.run([torch.from_numpy(pair.I1).cuda()], [torch.from_numpy(pair.I2).cuda()], use_graph=False)
+    want = [t[0].cpu() for t in (ref.pts, ref.flow, ref.status)]
+    first = dgf.track_pair(pair.I1, pair.I2, pair.win, pair.step, prm)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    second = dgf.track_pair(pair.I1, pair.I2, pair.win, pair.step, prm)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    for got in (first, second):
+        for a, b in zip(got, want):
+            assert not a.is_cuda and torch.equal(a, b)
+    assert first[1].data_ptr() != second[1].data_ptr()  # the caller's own copies
+    ht = dgf.HostPairTracker(pair.W, pair.H, pair.win, pair.step, prm)
+    out = (torch.empty((ht.n, 2)).pin_memory(), torch.empty((ht.n, 2)).pin_memory(),
+           torch.empty(ht.n, dtype=torch.uint8).pin_memory())
+    for _ in range(2):
+        got = ht.run(torch.from_numpy(pair.I1).pin_memory(), np.ascontiguousarray(pair.I2), out=out)
+        assert all(g.data_ptr() == o.data_ptr() for g, o in zip(got, out))
+        for a, b in zip(got, want):
+            assert torch.equal(a, b)
+    with pytest.raises(ValueError):
+        ht.run(pair.I1[:, :-1], pair.I2)
+    with pytest.raises(ValueError):
+        ht.run(pair.I1, pair.I2, out=(out[0][:-1], out[1], out[2]))
