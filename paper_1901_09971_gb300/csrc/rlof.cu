@@ -9,7 +9,9 @@
 // first 2r columns form horizontal pairs and the last column vertical ones (radius
 // 5: 61 pairs, four slots of 16 lanes); other radii use (2r+1) x (r+1) horizontal
 // pairs whose last column's second sample is masked out. Lane l of a group owns
-// pairs l, l + G, l + 2G, ...
+// pairs l, l + G, l + 2G, ..., except at 8 lanes (the default for radius 4 and 5),
+// where each lane owns two vertical runs of horizontal pairs whose tap rows are
+// shared along the run (RunLayout) and one vertical pair.
 //
 // The template T, Tx, Ty of the current level is sampled once per level into
 // shared memory (one 16-byte and one 8-byte slot per pair, read back without
@@ -44,14 +46,15 @@ __host__ __device__ constexpr int block_threads()
 }
 
 // Resident blocks the register budget is sized for: 512 threads a SM (128 registers
-// a thread), except at 8 lanes and radius 5, where 12 one-warp blocks (168
-// registers, no spills) measured 1.6% faster than 16 (128 registers, 12 bytes of
-// spills) on the 1242x375 pair, 1.203 against 1.223 ms; at radius 4 16 stay faster
-// (0.220 against 0.232 ms on its step-4 pair).
-template <int G, int RC>
+// a thread), except at 8 lanes and radius 5, where the bound of 14 one-warp blocks
+// gives the fastest code (128 registers, no spills; measured on the 1242x375 pair
+// with the run layout: 12, 13, 14 and 16 blocks 1.096, 1.080, 1.067 and 1.096 ms),
+// and 12 for the cross-based support there (at 14 its arm scan spills).
+template <int G, int RC, bool CROSS>
 __host__ __device__ constexpr int min_blocks()
 {
-    return G == 8 && RC == 5 ? 12 : 512 / block_threads<G>();
+    if (G == 8 && RC == 5) return CROSS ? 12 : 14;
+    return 512 / block_threads<G>();
 }
 
 template <int G>
@@ -234,6 +237,26 @@ struct TapBlock {
         J = __ffma2_rn(wPb, ub, J);
         return __ffma2_rn(wQb, Qb, J);
     }
+    // One tap row of a horizontal pair, read at element offset k rows below the
+    // run's first row (pu, ps: base_u, base_s plus the run's offset): the aligned
+    // pair u and the pair Q the parity completes. pair_rows evaluates the pair whose
+    // top and bottom tap rows these are, in the same order of operations as pair().
+    struct Row {
+        float2 u, Q;
+    };
+    __device__ __forceinline__ Row row(const TS* pu, const TS* ps, int k) const
+    {
+        const float2 u = ld2(pu + k * pitch);
+        const float s = dgf::ld(ps + k * pitch);
+        return Row{u, make_float2(e ? s : u.y, e ? u.x : s)};
+    }
+    __device__ __forceinline__ float2 pair_rows(const Row& t, const Row& b) const
+    {
+        float2 J = __fmul2_rn(wP, t.u);
+        J = __ffma2_rn(wQ, t.Q, J);
+        J = __ffma2_rn(wPb, b.u, J);
+        return __ffma2_rn(wQb, b.Q, J);
+    }
     __device__ __forceinline__ float2 generic(int off, int eo0, int eo1, bool vert, const PairWeights& pw) const
     {
         const TS* p = base + off;
@@ -356,13 +379,104 @@ struct Layout {
     static constexpr int np = nh + RC + 1;   // all pairs
 };
 
+// Run layout (8 lanes, radius 4 and 5): the horizontal pairs of the first 2RC
+// columns are grouped into vertical runs of pairs in one two-column strip; the
+// pairs of a run share their tap rows, so a run of n pairs reads n + 1 rows of taps
+// instead of 2n. Every lane owns two runs (slots 0 .. la - 1 and la .. la + lb - 1),
+// then generic slots. A pair past the support is a pad: zero template, zero weight
+// (only a run's last pairs can be pads; their taps lie at most one row below the
+// tap block, inside the planes' replicated border).
+// * Radius 5 (11 pair rows, five strips), runs of 3: run t = lane + 8k covers strip
+//   t % 5, pair rows 3 (t / 5) .. + 2 (15 runs; lane 7's second run is a pad); the
+//   generic slots hold the pairs of rows 9 and 10 (g = lane + 8 (j - 6) < 10) and
+//   the six vertical pairs of the last column (g >= 10).
+// * Radius 4 (9 pair rows, four strips), a run of 2 and one of 3: strip s holds rows
+//   0-1 (short run of lane s), 2-4 (long run of lane s), 5-6 (short run of lane
+//   s + 4) and 7-9 (long run of lane s + 4, row 9 a pad); the generic slot holds
+//   the five vertical pairs of the last column (g = lane).
+// Measured on GB300 against each other: the radius-5 pair, 1.068 ms with runs of 3
+// against 1.090 with runs of 3 and 4 plus a vertical slot; the radius-4 batch
+// pair, 0.627 ms with runs of 2 and 3 against 0.647 with two runs of 2.
+template <int G, int RC>
+struct RunLayout {
+    static constexpr bool on = G == 8 && (RC == 4 || RC == 5);
+    static constexpr int la = RC == 5 ? 3 : 2;  // pairs of a lane's first run
+    static constexpr int lb = RC == 5 ? 3 : 3;  // pairs of its second run
+    static constexpr int first_generic = la + lb;
+    static constexpr int nhg = RC == 5 ? 10 : 0;  // horizontal pairs in generic slots
+    static constexpr int ng = nhg + RC + 1;       // generic pairs (then the vertical ones)
+    static constexpr int slots = first_generic + (ng + G - 1) / G;
+};
+
+// Strip and first pair row of run k of a lane in the radius-4 run layout.
+__device__ __forceinline__ void run_origin4(int lane, int k, int& strip, int& row)
+{
+    strip = lane & 3;
+    row = k == 0 ? (lane < 4 ? 0 : 5) : (lane < 4 ? 2 : 7);
+}
+
+// Tap origin (x, y) in the support of sample A of slot j of a lane, whether the
+// pair is vertical, and whether the slot holds a pair of the support (false for
+// pads and slots past the support; their template is zeroed).
+template <int G, int RC>
+__device__ __forceinline__ bool slot_origin(int lane, int j, int R, int& x, int& y, bool& vert)
+{
+    vert = false;
+    if constexpr (RunLayout<G, RC>::on) {
+        using RL = RunLayout<G, RC>;
+        if (j < RL::first_generic && RC == 5) {
+            const int t = lane + G * (j / RL::la);  // run index
+            const int tt = t < 15 ? t : 0;          // a pad run reads run 0's taps
+            x = 2 * (tt % RC);
+            y = RL::la * (tt / RC) + j % RL::la;
+            return t < 15;
+        }
+        if (j < RL::first_generic) {
+            const int k = j < RL::la ? 0 : 1;
+            int strip, row;
+            run_origin4(lane, k, strip, row);
+            x = 2 * strip;
+            y = row + (k ? j - RL::la : j);
+            return y < 2 * RC + 1;
+        }
+        const int g = lane + G * (j - RL::first_generic);
+        if (g < RL::nhg) {
+            x = 2 * (g % RC);
+            y = 9 + g / RC;
+        } else {
+            vert = true;
+            x = 2 * RC;
+            y = 2 * (g - RL::nhg);
+        }
+        return g < RL::ng;
+    } else {
+        const int pc = R + 1, np = RC ? Layout<RC>::np : (2 * R + 1) * pc;
+        const int q = lane + G * j;
+        if (RC == 0) {
+            y = q / pc;
+            x = 2 * (q - y * pc);
+        } else if (q < Layout<RC>::nh) {
+            y = q / RC;
+            x = 2 * (q - y * RC);
+        } else {
+            vert = true;
+            x = 2 * RC;
+            y = 2 * (q - Layout<RC>::nh);
+        }
+        return q < np;
+    }
+}
+
 // Per-lane state of one point's support at the current level: the template
 // T, Tx, Ty of each owned pair (in shared memory: (T, Tx) of slot j at tq[32 j],
 // Ty at ty[32 j], so a warp's 16- and 8-byte accesses are conflict-free), the
 // pair's tap offset in the tap block and the mask of its second sample (0 where
 // it lies past the support). Slots that can hold vertical pairs (compile-time
 // layout only; at most the last two) also keep the offsets of the two taps the
-// second sample adds, and a bit per such slot set for a vertical pair.
+// second sample adds, and a bit per such slot set for a vertical pair. In the run
+// layout, each run's first tap row offset and a 0/1 factor on the weights of the
+// pairs that can be pads (0 for a pad); last_ok is false when the lane's last slot
+// lies past the support.
 template <int SLP>
 struct Support {
     float4* tq;
@@ -384,64 +498,116 @@ struct Support {
     float msk[SLP];
     int eo0[2], eo1[2];
     unsigned vbits;
+    int roff[2];
+    float rkeep[2];
+    bool last_ok;
 };
 
 // First slot that can hold a vertical pair (SLP for the runtime layout).
 template <int G, int SLP, int RC>
 __host__ __device__ constexpr int first_generic_slot()
 {
+    if constexpr (RunLayout<G, RC>::on) return RunLayout<G, RC>::first_generic;
     return RC ? Layout<RC>::nh / G : SLP;
+}
+
+// Adds one pair's terms at its interpolated frame-2 values J (template of slot j;
+// hci = (c - b)^-1 c of the Hampel weight, or 0 to give the pair weight 0).
+template <int SLP, int MODEL, int RC, bool CROSS, int FG>
+__device__ __forceinline__ void pair_terms(const Support<SLP>& S, float2 (&acc)[14], int j, float2 J, float2 ng1,
+                                           float2 nc, float ha, float icb, float hci)
+{
+    float2 T, Tx, Ty;
+    S.get(j, T, Tx, Ty);
+    float2 r;
+    if (MODEL == 4)
+        r = __fadd2_rn(__ffma2_rn(ng1, T, J), nc);
+    else
+        r = __ffma2_rn(f2(-1.f), T, J);
+    // only a generic slot (and any slot of the runtime layout) can hold a sample
+    // past the support
+    float2 w = make_float2(hampel_weight(r.x, ha, icb, hci), hampel_weight(r.y, ha, icb, hci));
+    if (RC == 0 || j >= FG) w.y *= S.msk[j];
+    if (CROSS) w = __fmul2_rn(w, S.mk[32 * j]);
+    const float2 wTx = __fmul2_rn(w, Tx), wTy = __fmul2_rn(w, Ty);
+    acc[0] = __ffma2_rn(wTx, Tx, acc[0]);
+    acc[1] = __ffma2_rn(wTx, Ty, acc[1]);
+    acc[4] = __ffma2_rn(wTy, Ty, acc[4]);
+    acc[10] = __ffma2_rn(wTx, r, acc[10]);
+    acc[11] = __ffma2_rn(wTy, r, acc[11]);
+    if (MODEL == 4) {
+        const float2 wT = __fmul2_rn(w, T);
+        acc[2] = __ffma2_rn(wTx, T, acc[2]);
+        acc[3] = __fadd2_rn(acc[3], wTx);
+        acc[5] = __ffma2_rn(wTy, T, acc[5]);
+        acc[6] = __fadd2_rn(acc[6], wTy);
+        acc[7] = __ffma2_rn(wT, T, acc[7]);
+        acc[8] = __fadd2_rn(acc[8], wT);
+        acc[9] = __fadd2_rn(acc[9], w);
+        acc[12] = __ffma2_rn(wT, r, acc[12]);
+        acc[13] = __ffma2_rn(w, r, acc[13]);
+    }
+}
+
+// The terms of run k of the run layout (N pairs from slot j0): each tap row is read
+// once, as the bottom row of one pair and the top row of the next. The pairs that
+// can be pads (all of a radius-5 run, the last of a radius-4 run) take the run's
+// 0/1 weight factor.
+template <typename TS, int SLP, int MODEL, int RC, bool CROSS, int FG, int N>
+__device__ __forceinline__ void run_terms(const Support<SLP>& S, float2 (&acc)[14], const TapBlock<TS>& tb, int k,
+                                          int j0, float2 ng1, float2 nc, float ha, float icb, float hc_icb)
+{
+    constexpr int first_pad = RC == 5 ? 0 : N - 1;  // first pair that can be a pad
+    const float hci_pad = hc_icb * S.rkeep[k];
+    const TS* pu = tb.base_u + S.roff[k];
+    const TS* ps = tb.base_s + S.roff[k];
+    typename TapBlock<TS>::Row top = tb.row(pu, ps, 0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const typename TapBlock<TS>::Row bot = tb.row(pu, ps, i + 1);
+        pair_terms<SLP, MODEL, RC, CROSS, FG>(S, acc, j0 + i, tb.pair_rows(top, bot), ng1, nc, ha, icb,
+                                              i >= first_pad ? hci_pad : hc_icb);
+        top = bot;
+    }
 }
 
 // Accumulates the weighted normal equations of the lane's pairs at one iterate.
 // acc[0..9] = sum w (TxTx, TxTy, TxT, Tx, TyTy, TyT, Ty, TT, T, 1); acc[10..13] =
 // sum w r (Tx, Ty, T, 1), each as .x/.y partial sums of a pair's two samples.
-// Taps are read without clamping (TapBlock).
+// Taps are read without clamping (TapBlock). In the run layout each run walks its
+// len + 1 tap rows once, a row serving as the bottom of one pair and the top of
+// the next.
 template <typename TS, int G, int SLP, int MODEL, int RC, bool CROSS>
 __device__ __forceinline__ void accumulate(const Support<SLP>& S, float2 (&acc)[14], const TapBlock<TS>& tb,
                                            const PairWeights& pw, int lane, int np, float g1, float c, float ha,
                                            float icb, float hc_icb)
 {
     constexpr int FG = first_generic_slot<G, SLP, RC>();
+    constexpr int J0 = RunLayout<G, RC>::on ? FG : 0;  // first slot of the loop below
     const float2 ng1 = f2(-g1), nc = f2(-c);
+    if constexpr (RunLayout<G, RC>::on) {
+        using RL = RunLayout<G, RC>;
+        static_assert(RL::slots == SLP, "run layout slot count");
+        if constexpr (RL::la == RL::lb) {
 #pragma unroll
-    for (int j = 0; j < SLP; ++j) {
-        const int q = lane + G * j;
-        // SLP = ceil(np / G), so only the last slot can hold pairs past the support;
-        // testing it there alone leaves the loads of all other slots free to be hoisted
-        if (j == SLP - 1 && q >= np) break;
-        float2 T, Tx, Ty;
-        S.get(j, T, Tx, Ty);
-        const float2 J = j >= FG ? tb.generic(S.off[j], S.eo0[j - FG], S.eo1[j - FG], (S.vbits >> (j - FG)) & 1u, pw)
-                                 : tb.pair(S.off[j]);
-        float2 r;
-        if (MODEL == 4)
-            r = __fadd2_rn(__ffma2_rn(ng1, T, J), nc);
-        else
-            r = __ffma2_rn(f2(-1.f), T, J);
-        // only a generic slot (and any slot of the runtime layout) can hold a sample
-        // past the support
-        float2 w = make_float2(hampel_weight(r.x, ha, icb, hc_icb), hampel_weight(r.y, ha, icb, hc_icb));
-        if (RC == 0 || j >= FG) w.y *= S.msk[j];
-        if (CROSS) w = __fmul2_rn(w, S.mk[32 * j]);
-        const float2 wTx = __fmul2_rn(w, Tx), wTy = __fmul2_rn(w, Ty);
-        acc[0] = __ffma2_rn(wTx, Tx, acc[0]);
-        acc[1] = __ffma2_rn(wTx, Ty, acc[1]);
-        acc[4] = __ffma2_rn(wTy, Ty, acc[4]);
-        acc[10] = __ffma2_rn(wTx, r, acc[10]);
-        acc[11] = __ffma2_rn(wTy, r, acc[11]);
-        if (MODEL == 4) {
-            const float2 wT = __fmul2_rn(w, T);
-            acc[2] = __ffma2_rn(wTx, T, acc[2]);
-            acc[3] = __fadd2_rn(acc[3], wTx);
-            acc[5] = __ffma2_rn(wTy, T, acc[5]);
-            acc[6] = __fadd2_rn(acc[6], wTy);
-            acc[7] = __ffma2_rn(wT, T, acc[7]);
-            acc[8] = __fadd2_rn(acc[8], wT);
-            acc[9] = __fadd2_rn(acc[9], w);
-            acc[12] = __ffma2_rn(wT, r, acc[12]);
-            acc[13] = __ffma2_rn(w, r, acc[13]);
+            for (int k = 0; k < 2; ++k)
+                run_terms<TS, SLP, MODEL, RC, CROSS, FG, RL::la>(S, acc, tb, k, k * RL::la, ng1, nc, ha, icb, hc_icb);
+        } else {
+            run_terms<TS, SLP, MODEL, RC, CROSS, FG, RL::la>(S, acc, tb, 0, 0, ng1, nc, ha, icb, hc_icb);
+            run_terms<TS, SLP, MODEL, RC, CROSS, FG, RL::lb>(S, acc, tb, 1, RL::la, ng1, nc, ha, icb, hc_icb);
         }
+    }
+#pragma unroll
+    for (int j = J0; j < SLP; ++j) {
+        // only the last slot can hold pairs past the support; testing it there
+        // alone leaves the loads of all other slots free to be hoisted
+        if (j == SLP - 1) {
+            if (RunLayout<G, RC>::on ? !S.last_ok : lane + G * j >= np) break;
+        }
+        // the radius-4 run layout's generic slot holds vertical pairs only
+        const bool vert = (RunLayout<G, RC>::on && RC == 4) || ((S.vbits >> (j - FG)) & 1u);
+        const float2 J = j >= FG ? tb.generic(S.off[j], S.eo0[j - FG], S.eo1[j - FG], vert, pw) : tb.pair(S.off[j]);
+        pair_terms<SLP, MODEL, RC, CROSS, FG>(S, acc, j, J, ng1, nc, ha, icb, hc_icb);
     }
 }
 
@@ -529,7 +695,7 @@ __device__ __forceinline__ bool setup_level(Support<SLP>& S, const LevelView<TS>
                                             unsigned mask, int R, float min_eig, float tau, WarpScratch& ws)
 {
     constexpr int FG = first_generic_slot<G, SLP, RC>();
-    const int side = 2 * R + 1, pc = R + 1, np = RC ? Layout<RC>::np : side * pc;
+    const int side = 2 * R + 1;
     const float fx0 = floorf(plx), fy0 = floorf(ply);
     const int bx = (int)fx0 - R, by = (int)fy0 - R;
     const PairWeights pw(plx - fx0, ply - fy0);
@@ -554,26 +720,16 @@ __device__ __forceinline__ bool setup_level(Support<SLP>& S, const LevelView<TS>
         return kx >= -arm[3 * sy] && kx <= arm[3 * sy + 1] ? 1.f : 0.f;
     };
     S.vbits = 0u;
+    S.last_ok = true;
 #pragma unroll
     for (int j = 0; j < SLP; ++j) {
-        const int q = lane + G * j;
         float2 T = f2(0.f), Tx = f2(0.f), Ty = f2(0.f);
         float msk = 0.f;
         int off = 0;
-        if (q < np) {
-            bool vert = false;
-            int x, y;  // tap origin of sample A in the support
-            if (RC == 0) {
-                y = q / pc;
-                x = 2 * (q - y * pc);
-            } else if (q < Layout<RC>::nh) {
-                y = q / RC;
-                x = 2 * (q - y * RC);
-            } else {
-                vert = true;
-                x = 2 * RC;
-                y = 2 * (q - Layout<RC>::nh);
-            }
+        int x, y;  // tap origin of sample A in the support
+        bool vert;
+        const bool has = slot_origin<G, RC>(lane, j, R, x, y, vert);
+        if (has) {
             off = y * L.pitch + x;
             msk = (vert ? y : x) + 1 < side ? 1.f : 0.f;
             // taps sample B adds in a generic slot: right column (horizontal), row
@@ -607,25 +763,21 @@ __device__ __forceinline__ bool setup_level(Support<SLP>& S, const LevelView<TS>
         } else if (j >= FG) {
             S.eo0[j - FG] = S.eo1[j - FG] = 0;
         }
+        if constexpr (RunLayout<G, RC>::on) {
+            using RL = RunLayout<G, RC>;
+            if (j == 0 || j == RL::la) S.roff[j == 0 ? 0 : 1] = off;  // a run's first tap row
+            // the factor of the run's pads: all of a radius-5 run is a pad or none; the
+            // last pair of a radius-4 run is one whenever any is
+            if (j < FG && (RC == 5 ? j % RL::la == 0 : j == RL::la - 1 || j == FG - 1))
+                S.rkeep[j < RL::la ? 0 : 1] = has ? 1.f : 0.f;
+            if (j == SLP - 1) S.last_ok = has;
+        }
         S.put(j, T, Tx, Ty);
         S.off[j] = off;
         S.msk[j] = msk;
         if (CROSS) {
             float2 mkv = f2(0.f);
-            if (q < np) {
-                int x, y;
-                bool vert = false;
-                if (RC == 0) {
-                    y = q / pc;
-                    x = 2 * (q - y * pc);
-                } else if (q < Layout<RC>::nh) {
-                    y = q / RC;
-                    x = 2 * (q - y * RC);
-                } else {
-                    vert = true;
-                    x = 2 * RC;
-                    y = 2 * (q - Layout<RC>::nh);
-                }
+            if (has) {
                 mkv.x = in_cross(x, y);
                 if (msk != 0.f) mkv.y = vert ? in_cross(x, y + 1) : in_cross(x + 1, y);
             }
@@ -797,12 +949,12 @@ template <typename TS, int MODEL, int G, int SLP, int RC>
 int launch_one(const TrackBatch& a, cudaStream_t stream)
 {
     const long long total = (long long)a.total * G;
-    constexpr int BT = block_threads<G>(), MINB = min_blocks<G, RC>();
+    constexpr int BT = block_threads<G>();
     const unsigned grid = (unsigned)((total + BT - 1) / BT);
     if (a.cross_tau > 0.f)
-        rlof_kernel<TS, G, SLP, MODEL, MINB, RC, true><<<grid, BT, 0, stream>>>(a);
+        rlof_kernel<TS, G, SLP, MODEL, min_blocks<G, RC, true>(), RC, true><<<grid, BT, 0, stream>>>(a);
     else
-        rlof_kernel<TS, G, SLP, MODEL, MINB, RC, false><<<grid, BT, 0, stream>>>(a);
+        rlof_kernel<TS, G, SLP, MODEL, min_blocks<G, RC, false>(), RC, false><<<grid, BT, 0, stream>>>(a);
     return dgf::launch_status();
 }
 
