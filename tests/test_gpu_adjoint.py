@@ -2,8 +2,9 @@
 tests/test_oracle_adjoint.py pins to finite differences).
 
 The tracking adjoint is compared with the oracle VJP evaluated at the GPU's own
-converged state (its flow, illumination and status), so the difference measures
-the FP32 adjoint arithmetic alone. Bars: DeGraF adjoint within 1e-5 of the
+converged state (its flow, illumination and status, with the level-0 position in
+the FP32 the kernel forms it in), so the difference measures the FP32 adjoint
+arithmetic alone. Bars: DeGraF adjoint within 1e-5 of the
 largest gradient magnitude (FP32 quotients of exact integer sums); tracking
 adjoint within 1e-2 relative error in the 2-norm over the image and per pixel
 within 1e-2 of the largest magnitude."""
@@ -57,6 +58,21 @@ def test_degraf_autograd_accumulates(dgf):
     assert np.abs(frame.grad.cpu().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
+def kernel_state_flow(pts, flow):
+    """The flow at which the oracle's VJP evaluates the state the kernel differentiates.
+
+    The adjoint kernel forms the level-0 position q = p + d in FP32 and takes the
+    bilinear cell of each tap from it (an integer decided in floating point); the
+    oracle forms p + d in FP64. A position within FP32 rounding below an integer
+    column (558.99997 rounds to 559.0) then lands in the neighbouring cell on the
+    two sides, and the interpolant's slopes, hence the point's whole VJP, differ.
+    So the oracle gets d' = fl32(p + d) - p (exact in FP64): its p + d' is the
+    kernel's position, and the comparison measures the adjoint's arithmetic alone.
+    """
+    P = np.asarray(pts, np.float32)
+    return (P + np.asarray(flow, np.float32)).astype(np.float64) - P.astype(np.float64)
+
+
 @pytest.mark.parametrize("model", [4, 2])
 def test_rlof_backward_matches_oracle_vjp(dgf, model):
     """The differentiation workload's shape: a 1242x375 translation pair, step 4,
@@ -78,8 +94,9 @@ def test_rlof_backward_matches_oracle_vjp(dgf, model):
     pyr2 = dgf.build_pyramid(torch.from_numpy(p.I2).cuda(), 3, 0, False)
     fl, st2, il = dgf.track(pyr1, pyr2, p.W, p.H, pts, prm, with_illum=True)
     assert torch.equal(fl, flow) and torch.equal(st2, status)
-    r1, r2 = oracle.rlof_vjp(p.I1, p.I2, pts.cpu().numpy(), oracle.RlofParams(levels=3, radius=4, model=model),
-                             fl.cpu().numpy(), il.cpu().numpy(), st, w.cpu().numpy())
+    P = pts.cpu().numpy()
+    r1, r2 = oracle.rlof_vjp(p.I1, p.I2, P, oracle.RlofParams(levels=3, radius=4, model=model),
+                             kernel_state_flow(P, fl.cpu().numpy()), il.cpu().numpy(), st, w.cpu().numpy())
     for got, ref in ((f1.grad.cpu().numpy(), r1), (f2.grad.cpu().numpy(), r2)):
         rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         print(f"model {model}: relative 2-norm error {rel:.2e}")
