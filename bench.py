@@ -737,23 +737,17 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
     fp32 = measure_fp32_peak(dgf, torch, dev)
 
     # end to end through the public API: pinned host frames in, host results out
+    # (HostPairTracker.run: host-to-device copies, the pair, device-to-host copies
+    # and the wait for them)
     h1 = torch.from_numpy(pair.I1).pin_memory()
     h2 = torch.from_numpy(pair.I2).pin_memory()
     o_pts = torch.empty((n_pts, 2), dtype=torch.float32).pin_memory()
     o_flow = torch.empty((n_pts, 2), dtype=torch.float32).pin_memory()
     o_status = torch.empty(n_pts, dtype=torch.uint8).pin_memory()
-    d1 = torch.empty_like(f1)
-    d2 = torch.empty_like(f2)
-    te = dgf.BatchTracker(spec, prm, dev, lanes=tr.lanes)
-    te.bind([d1], [d2])
+    te = dgf.HostPairTracker(W, H, WORKLOAD["win"], WORKLOAD["step"], prm, dev, lanes=tr.lanes)
 
     def e2e_step():
-        d1.copy_(h1, non_blocking=True)
-        d2.copy_(h2, non_blocking=True)
-        te.run(use_graph=True)
-        o_pts.copy_(te.pts[0], non_blocking=True)
-        o_flow.copy_(te.flow[0], non_blocking=True)
-        o_status.copy_(te.status[0], non_blocking=True)
+        te.run(h1, h2, out=(o_pts, o_flow, o_status))
 
     for _ in range(3):
         e2e_step()
