@@ -792,6 +792,12 @@ def run_cuda(args, rank: int, world: int, local_rank: int):
         line["hbm_context"] = hbm_context(W, H, n_pts, 1e3 * total_s / args.steps)
         if batched is not None:
             line["batched"] = batched
+            dp = batched["detect_pyramid"]
+            # the HBM-bound stages' roofline beside the dominant kernel's
+            line["roofline"]["secondary"] = [{
+                "kernel": "degraf_detect_kernel + pyramid_kernel, 64 mixed pairs (one graph replay)",
+                "bound": "hbm", "achieved": dp["achieved_gbs"], "peak": dp["peak_gbs"], "unit": "GB/s",
+                "frac": dp["frac_of_measured_hbm"], "ms": dp["ms"], "bytes": dp["algorithmic_bytes"]}]
         if not args.no_batched:
             line["small_pair"] = run_small_pair(dgf, torch, dev)
             line["fp16_storage"] = run_fp16(dgf, torch, dev)

@@ -47,9 +47,11 @@ __host__ __device__ constexpr int block_threads()
 
 // Resident blocks the register budget is sized for: 512 threads a SM (128 registers
 // a thread), except at 8 lanes and radius 5, where the bound of 14 one-warp blocks
-// gives the fastest code (128 registers, no spills; measured on the 1242x375 pair
-// with the run layout: 12, 13, 14 and 16 blocks 1.096, 1.080, 1.067 and 1.096 ms),
-// and 12 for the cross-based support there (at 14 its arm scan spills).
+// gives the fastest code (128 registers, so 16 blocks fit; 4 bytes of spills, which
+// the bounds of 15 and 16 avoid, measured 1.055 against 1.064 and 1.073 ms on the
+// 1242x375 pair; before the offset was folded into the interpolation: 12, 13, 14 and
+// 16 blocks 1.096, 1.080, 1.067 and 1.096 ms), and 12 for the cross-based support
+// there (at 14 its arm scan spills).
 template <int G, int RC, bool CROSS>
 __host__ __device__ constexpr int min_blocks()
 {
@@ -224,7 +226,10 @@ struct TapBlock {
         wPb = e ? pw.w11 : pw.w10;
         wQb = e ? pw.w10 : pw.w11;
     }
-    __device__ __forceinline__ float2 pair(int off) const
+    // The interpolated pair plus init (a Gauss-Newton step passes -c, the offset of
+    // the illumination model, so that its residual needs one instruction less; the
+    // level set-up passes 0).
+    __device__ __forceinline__ float2 pair(int off, float2 init = make_float2(0.f, 0.f)) const
     {
         const TS* pu = base_u + off;
         const TS* ps = base_s + off;
@@ -232,7 +237,7 @@ struct TapBlock {
         const float sa = dgf::ld(ps), sb = dgf::ld(ps + pitch);
         const float2 Q = make_float2(e ? sa : u.y, e ? u.x : sa);
         const float2 Qb = make_float2(e ? sb : ub.y, e ? ub.x : sb);
-        float2 J = __fmul2_rn(wP, u);
+        float2 J = __ffma2_rn(wP, u, init);
         J = __ffma2_rn(wQ, Q, J);
         J = __ffma2_rn(wPb, ub, J);
         return __ffma2_rn(wQb, Qb, J);
@@ -250,20 +255,21 @@ struct TapBlock {
         const float s = dgf::ld(ps + k * pitch);
         return Row{u, make_float2(e ? s : u.y, e ? u.x : s)};
     }
-    __device__ __forceinline__ float2 pair_rows(const Row& t, const Row& b) const
+    __device__ __forceinline__ float2 pair_rows(const Row& t, const Row& b, float2 init) const
     {
-        float2 J = __fmul2_rn(wP, t.u);
+        float2 J = __ffma2_rn(wP, t.u, init);
         J = __ffma2_rn(wQ, t.Q, J);
         J = __ffma2_rn(wPb, b.u, J);
         return __ffma2_rn(wQb, b.Q, J);
     }
-    __device__ __forceinline__ float2 generic(int off, int eo0, int eo1, bool vert, const PairWeights& pw) const
+    __device__ __forceinline__ float2 generic(int off, int eo0, int eo1, bool vert, const PairWeights& pw,
+                                              float2 init = make_float2(0.f, 0.f)) const
     {
         const TS* p = base + off;
         const float a0 = dgf::ld(p), a1 = dgf::ld(p + 1), b0 = dgf::ld(p + pitch), b1 = dgf::ld(p + pitch + 1);
         const float e0 = dgf::ld(base + eo0), e1 = dgf::ld(base + eo1);
         const float t0 = vert ? b0 : a1, t1 = vert ? b1 : e0, t2 = vert ? e0 : b1;
-        float2 J = __fmul2_rn(pw.w00, make_float2(a0, t0));
+        float2 J = __ffma2_rn(pw.w00, make_float2(a0, t0), init);
         J = __ffma2_rn(pw.w01, make_float2(a1, t1), J);
         J = __ffma2_rn(pw.w10, make_float2(b0, t2), J);
         return __ffma2_rn(pw.w11, make_float2(b1, e1), J);
@@ -511,19 +517,20 @@ __host__ __device__ constexpr int first_generic_slot()
     return RC ? Layout<RC>::nh / G : SLP;
 }
 
-// Adds one pair's terms at its interpolated frame-2 values J (template of slot j;
-// hci = (c - b)^-1 c of the Hampel weight, or 0 to give the pair weight 0).
+// Adds one pair's terms at its interpolated frame-2 values less the illumination
+// offset, Jc = J - c (template of slot j; hci = (c - b)^-1 c of the Hampel weight,
+// or 0 to give the pair weight 0).
 template <int SLP, int MODEL, int RC, bool CROSS, int FG>
-__device__ __forceinline__ void pair_terms(const Support<SLP>& S, float2 (&acc)[14], int j, float2 J, float2 ng1,
-                                           float2 nc, float ha, float icb, float hci)
+__device__ __forceinline__ void pair_terms(const Support<SLP>& S, float2 (&acc)[14], int j, float2 Jc, float2 ng1,
+                                           float ha, float icb, float hci)
 {
     float2 T, Tx, Ty;
     S.get(j, T, Tx, Ty);
     float2 r;
     if (MODEL == 4)
-        r = __fadd2_rn(__ffma2_rn(ng1, T, J), nc);
+        r = __ffma2_rn(ng1, T, Jc);
     else
-        r = __ffma2_rn(f2(-1.f), T, J);
+        r = __ffma2_rn(f2(-1.f), T, Jc);
     // only a generic slot (and any slot of the runtime layout) can hold a sample
     // past the support
     float2 w = make_float2(hampel_weight(r.x, ha, icb, hci), hampel_weight(r.y, ha, icb, hci));
@@ -565,7 +572,7 @@ __device__ __forceinline__ void run_terms(const Support<SLP>& S, float2 (&acc)[1
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         const typename TapBlock<TS>::Row bot = tb.row(pu, ps, i + 1);
-        pair_terms<SLP, MODEL, RC, CROSS, FG>(S, acc, j0 + i, tb.pair_rows(top, bot), ng1, nc, ha, icb,
+        pair_terms<SLP, MODEL, RC, CROSS, FG>(S, acc, j0 + i, tb.pair_rows(top, bot, nc), ng1, ha, icb,
                                               i >= first_pad ? hci_pad : hc_icb);
         top = bot;
     }
@@ -606,8 +613,9 @@ __device__ __forceinline__ void accumulate(const Support<SLP>& S, float2 (&acc)[
         }
         // the radius-4 run layout's generic slot holds vertical pairs only
         const bool vert = (RunLayout<G, RC>::on && RC == 4) || ((S.vbits >> (j - FG)) & 1u);
-        const float2 J = j >= FG ? tb.generic(S.off[j], S.eo0[j - FG], S.eo1[j - FG], vert, pw) : tb.pair(S.off[j]);
-        pair_terms<SLP, MODEL, RC, CROSS, FG>(S, acc, j, J, ng1, nc, ha, icb, hc_icb);
+        const float2 Jc =
+            j >= FG ? tb.generic(S.off[j], S.eo0[j - FG], S.eo1[j - FG], vert, pw, nc) : tb.pair(S.off[j], nc);
+        pair_terms<SLP, MODEL, RC, CROSS, FG>(S, acc, j, Jc, ng1, ha, icb, hc_icb);
     }
 }
 
