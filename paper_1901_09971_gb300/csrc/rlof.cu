@@ -389,9 +389,10 @@ struct Layout {
 // columns are grouped into vertical runs of pairs in one two-column strip; the
 // pairs of a run share their tap rows, so a run of n pairs reads n + 1 rows of taps
 // instead of 2n. Every lane owns two runs (slots 0 .. la - 1 and la .. la + lb - 1),
-// then generic slots. A pair past the support is a pad: zero template, zero weight
-// (only a run's last pairs can be pads; their taps lie at most one row below the
-// tap block, inside the planes' replicated border).
+// then generic slots. A pair past the support is a pad: zero template, zero weight.
+// Pads are whole runs at radius 5 (reading run 0's taps) and the last pair of a run
+// at radius 4 (reading one row below the tap block, inside the planes' replicated
+// border).
 // * Radius 5 (11 pair rows, five strips), runs of 3: run t = lane + 8k covers strip
 //   t % 5, pair rows 3 (t / 5) .. + 2 (15 runs; lane 7's second run is a pad); the
 //   generic slots hold the pairs of rows 9 and 10 (g = lane + 8 (j - 6) < 10) and
@@ -407,7 +408,7 @@ template <int G, int RC>
 struct RunLayout {
     static constexpr bool on = G == 8 && (RC == 4 || RC == 5);
     static constexpr int la = RC == 5 ? 3 : 2;  // pairs of a lane's first run
-    static constexpr int lb = RC == 5 ? 3 : 3;  // pairs of its second run
+    static constexpr int lb = 3;                // pairs of its second run
     static constexpr int first_generic = la + lb;
     static constexpr int nhg = RC == 5 ? 10 : 0;  // horizontal pairs in generic slots
     static constexpr int ng = nhg + RC + 1;       // generic pairs (then the vertical ones)
