@@ -99,15 +99,16 @@ __device__ __forceinline__ void store2<__half>(__half* p, float a, float b)
 template <int L, bool BULK>
 struct Staged {
     static constexpr int RWP = region_pitch(L);
-    static constexpr unsigned kBulkMis = (unsigned)(-halo(L)) & 15u;
     const unsigned char* raw;
     unsigned mis0, pmod;  // word copies only
     __device__ __forceinline__ const unsigned char* row(int r) const
     {
-        if constexpr (BULK)
+        if constexpr (BULK) {
+            constexpr unsigned kBulkMis = (unsigned)(-halo(L)) & 15u;
             return raw + r * RWP + kBulkMis;
-        else
+        } else {
             return raw + r * RWP + ((mis0 + (unsigned)r * pmod) & 3u);
+        }
     }
 };
 
